@@ -1,0 +1,99 @@
+"""Planted mistakes in the oracle (on the CPU) must be caught by its pins.
+
+Each mutant wraps one oracle function with a plausible error -- a dropped
+sign, a conjugated phase, a window off by one bin, swapped A/B, a flipped
+Roemer delay, a dropped kernel factor -- and the test asserts that the
+matching pin no longer holds.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import fstat_oracle as O
+import tests.test_oracle_pins as P
+
+T = P.T
+
+
+def _brute_force_error(monkeypatch, doppler, df_off):
+    Fa, Fb, Fa_bf, Fb_bf, scale = P._brute_force_case(monkeypatch, doppler, 10.0, df_off,
+                                                      fdot=-1e-9 if doppler else 0.0)
+    return max(abs(Fa - Fa_bf), abs(Fb - Fb_bf)) / scale
+
+
+def _mutant_no_k0_sign(orig):
+    def f(bins_row, k_lo, kh, phase, D):
+        z = orig(bins_row, k_lo, kh, phase, D)
+        return z * (1.0 - 2.0 * (np.floor(kh).astype(np.int64) & 1))
+    return f
+
+
+def _mutant_conj_phase(orig):
+    def f(bins_row, k_lo, kh, phase, D):
+        return orig(bins_row, k_lo, kh, -np.asarray(phase), D)
+    return f
+
+
+def _mutant_window_shift(orig):
+    def f(bins_row, k_lo, kh, phase, D):
+        return orig(bins_row, k_lo + 1, kh, phase, D)
+    return f
+
+
+def _mutant_drop_kernel_factor(orig):
+    def f(bins_row, k_lo, kh, phase, D):
+        kap = np.asarray(kh) - np.floor(kh)
+        z = orig(bins_row, k_lo, kh, phase, D)
+        return np.where(kap < O.KAPPA_LIMIT, z, z / (np.sin(math.pi * kap) / math.pi))
+    return f
+
+
+@pytest.mark.parametrize("mutant", [_mutant_no_k0_sign, _mutant_conj_phase, _mutant_window_shift,
+                                    _mutant_drop_kernel_factor])
+def test_brute_force_pin_catches_sft_term_mutants(monkeypatch, mutant):
+    assert _brute_force_error(monkeypatch, False, 0.3 / T) < 1e-3
+    monkeypatch.setattr(O, "some_calculations", mutant(O.some_calculations))
+    worst = max(_brute_force_error(monkeypatch, False, off) for off in (0.3 / T, 1.37 / T))
+    assert worst > 1e-2
+
+
+def test_doppler_pin_catches_flipped_roemer_delay(monkeypatch):
+    orig = O.sft_timing_antenna
+
+    def flipped(det, T_, alpha, delta, t_ref):
+        dtau, tdot, a, b = orig(det, T_, alpha, delta, t_ref)
+        tm = np.asarray(det.t_start) + 0.5 * T_
+        return 2 * (tm - t_ref) - dtau, 2.0 - tdot, a, b
+
+    monkeypatch.setattr(O, "sft_timing_antenna", flipped)
+    assert _brute_force_error(monkeypatch, True, 0.3 / T) > 1e-1
+
+
+def test_rho2_pin_catches_swapped_combine(monkeypatch):
+    orig = O.normalized
+
+    def swapped(Fa, Fb, A, B, C, D, sigma2=1.0):
+        return orig(Fa, Fb, B, A, C, D, sigma2)
+
+    monkeypatch.setattr(O, "normalized", swapped)
+    with pytest.raises(AssertionError):
+        P.test_large_dterms_recovers_rho2()
+
+
+def test_rho2_pin_catches_dropped_cross_term(monkeypatch):
+    orig = O.normalized
+
+    def dropped(Fa, Fb, A, B, C, D, sigma2=1.0):
+        return orig(Fa, Fb, A, B, 0.0, D, sigma2)
+
+    monkeypatch.setattr(O, "normalized", dropped)
+    with pytest.raises(AssertionError):
+        P.test_large_dterms_recovers_rho2()
+
+
+def test_noise_pin_catches_wrong_normalisation(monkeypatch):
+    orig = O.normalized
+    monkeypatch.setattr(O, "normalized", lambda Fa, Fb, A, B, C, D, s=1.0: orig(Fa, Fb, A, B, C, D, 2.0))
+    with pytest.raises(AssertionError):
+        P.test_noise_mean_matches_finite_dterms_prediction()
