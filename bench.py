@@ -1,0 +1,341 @@
+"""Throughput of the coherent F-statistic on GB300: template.SFT pairs per second.
+
+Default workload (one step = one full pass of the path over one workunit):
+2 detectors x 1200 gapped SFTs (T = 1800 s), 1 Hz band at 100 Hz with 8
+injected signals, templates 10 000 sky x 1800 f x 10 fdot (1.8e8 templates,
+4.32e11 pairs), D = 8, top-1000.  Each step runs the FP64 timing / antenna /
+basis kernel, the Dirichlet kernel with fused 2F, and the toplist selection.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--form c64|f16|bf16]
+  python bench.py --impl reference ...   (the FP64 CPU oracle on a bounded sample)
+
+Multi-GPU (torchrun, one process per GPU): sky points are sharded, each rank
+runs a full workunit-sized step on its shard (weak scaling) and the local
+toplists are merged on rank 0 through one all-gather.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FLOP_PER_PAIR = 100.0          # algorithmic FP32 work of one template.SFT pair
+N_SM = 152
+FP32_LANES = 128
+METRIC = "template·SFT pairs/s (2F) on 1 GB300, chosen vs plain FP32 form at stated 2F error"
+KERNEL_SOURCES = ["dirichlet.cuh", "dirichlet_c64.cu", "dirichlet_f16.cu", "dirichlet_bf16.cu"]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--form", default="c64", choices=["c64", "f16", "bf16"])
+    ap.add_argument("--n-sky", type=int, default=10000)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--compare-forms", action="store_true", help="also time the other storage forms")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+def workload(rank: int, world: int, n_sky: int):
+    from workload import config1, fibonacci_sky
+    sky_all = fibonacci_sky(n_sky * world)
+    return config1(sky=sky_all[rank * n_sky:(rank + 1) * n_sky])
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_0904_1826_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(form: str):
+    """DRAM bytes per launch of the Dirichlet kernel from the committed ncu
+    summary, if it was taken on the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "dirichlet_counters.json")
+    try:
+        with open(p) as fh:
+            d = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    e = d.get(form)
+    if not e or e.get("kernel_hash") != kernel_hash():
+        return None
+    return e.get("dram_bytes_per_full_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.out = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.flush()
+        self.out.seek(0)
+        rows = [r.split(",") for r in self.out.read().strip().splitlines() if r.strip()]
+        os.unlink(self.out.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def cpu_baseline(w, n_fdot_sample=None):
+    """The FP64 oracle as it stands, single process, on one sky point of the
+    workload (all frequencies, all spindowns, all SFTs of both detectors)."""
+    from oracle import fstat_oracle as O
+    from workload import TemplateBank
+    bank = w.bank
+    fd = bank.fdot if n_fdot_sample is None else bank.fdot[:n_fdot_sample]
+    sub = TemplateBank(bank.sky[:1], bank.f0, bank.df, bank.n_f, fd, bank.t_ref)
+    t0 = time.perf_counter()
+    O.compute_fstat_freq_band(w.detectors, w.T, w.k_lo, w.dterms, sub)
+    dt = time.perf_counter() - t0
+    pairs = sub.n_f * sub.n_fdot * w.n_sft_total
+    return pairs / dt, pairs, dt
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    w = workload(0, 1, args.n_sky)
+    # each step: the oracle on 1 sky x 1800 f x 1 fdot x 2400 SFTs (4.3e6 pairs)
+    for _ in range(args.warmup):
+        cpu_baseline(w, n_fdot_sample=1)
+    tot_pairs, tot_t = 0, 0.0
+    for _ in range(args.steps):
+        _, p, t = cpu_baseline(w, n_fdot_sample=1)
+        tot_pairs += p
+        tot_t += t
+    v = tot_pairs / tot_t
+    line = {"metric": METRIC, "value": v, "unit": "pairs/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": "plain workunit: 2 det x 1200 SFT, 10000 sky x 1800 f x 10 fdot, D=8",
+                       "sample": "1 sky x 1800 f x 1 fdot x 2400 SFT per step"},
+            "cpu_baseline": {"value": v, "unit": "pairs/s", "cores": 1, "kind": "oracle",
+                             "sample": "1 sky x 1800 f x 1 fdot x 2400 SFT per step"},
+            "e2e": {"value": v, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    import paper_0904_1826_gb300 as fs
+    from paper_0904_1826_gb300.multi import merge_toplists
+
+    w = workload(rank, world, args.n_sky)
+    n_pairs = w.n_pairs
+    stream = torch.cuda.Stream()
+
+    def make(form):
+        g = fs.FStat(local_rank, dterms=w.dterms, topk=w.topk, bins_form=form)
+        g.load_workload(w)
+        g.inject(w.injections, w.bank.t_ref)
+        return g
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def timed_run(g, steps, warmup, launch_mark=None):
+        for _ in range(warmup):
+            g.compute(stream)
+        torch.cuda.synchronize()
+        g.take_kernel_time()
+        # flush L2 once before the timed region (each step then streams ~5 GB
+        # of bases and 2F through it)
+        junk = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+        junk.fill_(1)
+        del junk
+        barrier()
+        torch.cuda.synchronize()
+        if launch_mark is not None:
+            launch_mark[0] = g.launch_count()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            g.compute(stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms = e0.elapsed_time(e1)
+        kd, kt, nk = g.take_kernel_time()
+        return ms, kd, kt, nk
+
+    g = make(args.form)
+    plan = g.plan()
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    n_launch0 = [0]
+
+    ms, k_dir, k_step, n_k = timed_run(g, args.steps, args.warmup, n_launch0)
+    clocks = sampler.stop()
+    launches = g.launch_count() - n_launch0[0]
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    # the exchange step: merge the local toplists
+    idx, val = g.toplist(w.topk)
+    if world > 1:
+        sky_off = rank * args.n_sky * w.bank.n_fdot * w.bank.n_f
+        local = torch.tensor(np.stack([idx + sky_off, val.view(np.int32).astype(np.int64)], 1), device="cuda")
+        gathered = [torch.empty_like(local) for _ in range(world)]
+        torch.distributed.all_gather(gathered, local)
+        lists = [(x[:, 0].cpu().numpy(), x[:, 1].cpu().numpy().astype(np.int32).view(np.float32)) for x in gathered]
+        idx, val = merge_toplists(lists, w.topk)
+    value = n_pairs * world * args.steps / (ms / 1e3)
+
+    # end to end through the public API with host buffers (pinned), per step:
+    # SFT and template upload, compute, toplist download
+    pinned = []
+    for d in w.detectors:
+        p = torch.empty((d.n_sft, w.n_bins, 2), dtype=torch.float32, pin_memory=True)
+        p.numpy()[:] = d.bins.view(np.float32).reshape(d.n_sft, w.n_bins, 2)
+        pinned.append(p)
+    h2d = sum(p.numel() * 4 for p in pinned) + sum(d.n_sft * 8 for d in w.detectors) + \
+        w.bank.sky.size * 8 + w.bank.fdot.size * 8
+    d2h = w.topk * 12
+    e2e_ms = []
+    for it in range(args.e2e_steps + 1):
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for i, d in enumerate(w.detectors):
+            fs.fstat_set_sfts(g.ctx, i, d.lat, d.lon, d.az, w.T, w.k_lo, d.t_start,
+                              pinned[i].numpy().view(np.complex64).reshape(d.n_sft, w.n_bins))
+        g.set_bank(w.bank)
+        g.compute(stream)
+        g.toplist(w.topk)
+        barrier()
+        if it > 0:
+            e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    e2e_ms_max = max(e2e_ms)
+    if world > 1:
+        t = torch.tensor([e2e_ms_max], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms_max = float(t.item())
+    e2e_value = n_pairs * world / (e2e_ms_max / 1e3)
+
+    forms = {}
+    if args.compare_forms and rank == 0:
+        for f in ("c64", "f16", "bf16"):
+            if f == args.form:
+                continue
+            g2 = make(f)
+            ms2, kd2, _, _ = timed_run(g2, args.steps, 1)
+            forms[f] = {"value": n_pairs * args.steps / (ms2 / 1e3), "dirichlet_ms": kd2}
+            g2.close()
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    clock_mhz = 2070.0
+    peak = N_SM * FP32_LANES * 2 * clock_mhz * 1e6 / 1e12       # TFLOP/s, recipe unit counts, max clock
+    achieved = FLOP_PER_PAIR * n_pairs / (k_dir / 1e3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": ncu_traffic(args.form), "kernel": "dirichlet_kernel",
+                "dirichlet_ms": k_dir, "step_ms_device": k_step,
+                "peak_note": "152 SM x 128 FP32 lanes x 2 flop x 2070 MHz (max SM clock)"}
+    if clocks and clocks.get("sm_mhz"):
+        roofline["frac_at_sampled_clock"] = achieved / (N_SM * FP32_LANES * 2 * clocks["sm_mhz"] * 1e6 / 1e12)
+    line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"c64": "f32", "f16": "f16-storage/f32", "bf16": "bf16-storage/f32"}[args.form],
+            "data": "synthetic",
+            "config": {"workload": "plain workunit: 2 det x 1200 gapped SFT (T=1800 s), 1 Hz band at 100 Hz, "
+                                   "8 injected signals; 10000 sky x 1800 f x 10 fdot, D=8, top-1000",
+                       "form": args.form, "pairs_per_step_per_gpu": n_pairs,
+                       "l2": "per-step working set ~5 GB (bases, 2F array) > 129 MB L2; L2 flushed before timing",
+                       "plan": plan},
+            "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms_max},
+            "roofline": roofline,
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "top": {"2F": float(val[0]), "idx": int(idx[0])}}
+    if forms:
+        line["other_forms"] = forms
+    if world == 1 and not args.no_cpu_baseline:
+        v, p, t = cpu_baseline(w)
+        line["cpu_baseline"] = {"value": v, "unit": "pairs/s", "cores": 1, "kind": "oracle",
+                                "sample": f"1 sky x 1800 f x 10 fdot x 2400 SFT ({p:.3g} pairs, {t:.1f} s)"}
+    g.close()
+    print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,206 @@
+/*
+ * fstat.h -- C ABI of the GB300 coherent F-statistic library (libfstat.so).
+ *
+ * The library computes the multi-detector coherent F-statistic (2F) of a bank
+ * of continuous-wave templates (sky position, frequency, spindown) over short
+ * Fourier transforms (SFTs), and keeps the top-K candidates.  Its calls follow
+ * the paper's statement of the problem: the F-statistic of a frequency band is
+ * a loop over frequencies of a sum over detectors of a sum over SFTs
+ * (Listing 1, Section "Einstein@Home": ComputeFStatFreqBand / ComputeFStat /
+ * ComputeFaFb), fed by flat SFT data arrays with offset arrays instead of a
+ * pointer tree (Section "CUDA", version 2 data structure).
+ *
+ * Per template lambda = (alpha, delta, f, fdot) and SFT alpha of detector d
+ * (start t_a, length T, complex bins X_k at absolute bin k):
+ *   dtau   = t_m - t_ref + n.r_d(t_m)/c,  tdot = 1 + n.v_d(t_m)/c,  t_m = t_a + T/2
+ *   khat   = (f + fdot dtau) tdot T,   k0 = floor(khat),  kappa = khat - k0
+ *   Phi    = 2 pi (f dtau + fdot dtau^2 / 2)
+ *   z      = (-1)^k0 e^{-i Phi} (sin(pi kappa)/pi) sum_{k=k0-D+1}^{k0+D} X_k/(khat - k)
+ *   Fa     = sum a z,  Fb = sum b z  (over all SFTs of all detectors)
+ *   2F     = 2 (B|Fa|^2 + A|Fb|^2 - 2C Re(Fa Fb*)) / (AB - C^2),
+ *            A = sum a^2, B = sum b^2, C = sum ab.
+ * The body of the SFT term is the standard Dirichlet-kernel demodulation that
+ * the paper's pseudo-code abbreviates as some_calculations / normalized.
+ *
+ * Conventions
+ *   - Every call returns an fstat_status (0 = FSTAT_OK); nothing throws.  On
+ *     error, fstat_last_error(ctx) returns a NUL-terminated message owned by
+ *     the context, valid until the next call on it.
+ *   - The library copies every input; callers keep ownership of their buffers
+ *     and may free them when the call returns.  Outputs go to caller-owned
+ *     buffers.  Device memory is owned by the context and released by
+ *     fstat_destroy().
+ *   - Pointer arguments marked "host or device" are device pointers when the
+ *     accompanying `mem` argument is FSTAT_MEM_DEVICE (they must belong to
+ *     the context's device) and host pointers otherwise.
+ *   - A context is bound to one device and one CUDA stream at a time; it is
+ *     not thread-safe.  Separate contexts are independent.
+ *   - Template index of (sky s, spindown d, frequency j):
+ *       idx = ((s * n_fdot) + d) * n_f + j.
+ */
+#ifndef FSTAT_H
+#define FSTAT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fstat_ctx fstat_ctx;
+
+typedef enum {
+    FSTAT_OK = 0,
+    FSTAT_EINVAL = -1,    /* invalid argument (sizes, non-finite data, D < 1 ...) */
+    FSTAT_ENOMEM = -2,    /* device allocation failed */
+    FSTAT_ECUDA = -3,     /* a CUDA runtime call failed */
+    FSTAT_ESTATE = -4,    /* call out of order (e.g. compute before SFTs/templates) */
+    FSTAT_ERANGE = -5,    /* a template's window left the staged SFT range */
+    FSTAT_ETIMEOUT = -6   /* a bounded device wait gave up */
+} fstat_status;
+
+/* Storage of the SFT bins on the device. */
+typedef enum {
+    FSTAT_BINS_C64 = 0,   /* complex64: FP32 re, im */
+    FSTAT_BINS_F16 = 1,   /* FP16 re, im times a per-SFT FP32 scale */
+    FSTAT_BINS_BF16 = 2   /* BF16 re, im times a per-SFT FP32 scale */
+} fstat_bins_form;
+
+typedef enum { FSTAT_MEM_HOST = 0, FSTAT_MEM_DEVICE = 1 } fstat_mem;
+
+typedef struct {
+    int32_t dterms;       /* D >= 1: the SFT term sums 2D bins around khat */
+    int32_t bins_form;    /* fstat_bins_form */
+    int32_t topk;         /* toplist length kept by fstat_compute (0..16384) */
+    int32_t kahan;        /* 1: compensated (Kahan) summation of Fa, Fb over SFTs */
+    int32_t tile_m;       /* templates per thread (0 = chosen by the tuner) */
+    int32_t tile_warps;   /* warps per thread block (0 = chosen by the tuner) */
+    int32_t sft_chunk;    /* SFTs staged per shared-memory round (0 = tuner) */
+    int32_t reserved;
+} fstat_opts;
+
+typedef struct {
+    double lat_rad;       /* geodetic latitude of the vertex */
+    double lon_rad;       /* longitude of the vertex (east positive) */
+    double xarm_az_rad;   /* azimuth of the x-arm from local North, clockwise;
+                             the y-arm points at azimuth + pi/2 */
+} fstat_detector;
+
+/* One continuous-wave signal for fstat_inject (amplitude set by its SNR). */
+typedef struct {
+    double alpha, delta;  /* sky position (equatorial, rad) */
+    double psi;           /* polarisation angle */
+    double cosi;          /* cosine of the inclination */
+    double phi0;          /* initial phase at t_ref */
+    double f, fdot;       /* frequency (Hz) and spindown (Hz/s) at t_ref */
+    double rho;           /* optimal SNR; h0 follows from it and A, B, C */
+} fstat_signal;
+
+/* Library version string, static storage. */
+const char *fstat_version(void);
+
+/* Create a context on CUDA device `device`.  opts == NULL takes the defaults
+ * (D = 8, complex64 storage, topk = 1000, no Kahan, tuned tiles).
+ * Errors: EINVAL (D < 1 or > 64, topk outside 0..16384, unknown form),
+ * ECUDA (device unavailable), ENOMEM. */
+int fstat_create(fstat_ctx **out, int device, const fstat_opts *opts);
+
+/* Release the context and all its device memory.  NULL is ignored. */
+void fstat_destroy(fstat_ctx *ctx);
+
+/* Message of the last failed call on ctx ("" if none; ctx may be NULL). */
+const char *fstat_last_error(const fstat_ctx *ctx);
+
+/* Load the SFTs of detector `det_index` (0 <= det_index < 8).  All detectors
+ * of a context share T, k_lo and n_bins.  Loading a detector again replaces
+ * its SFTs.
+ *   det      geometry of the detector (host)
+ *   Tsft     SFT length in seconds (> 0)
+ *   k_lo     absolute index of the first stored bin (frequency k_lo / Tsft)
+ *   n_bins   stored bins per SFT (>= 2)
+ *   n_sft    number of SFTs (>= 1)
+ *   t_start  [n_sft] SFT start times, host (finite)
+ *   bins     [n_sft][n_bins][2] FP32 (re, im), host or device per `mem`
+ * Bins outside [k_lo, k_lo + n_bins) count as zero in every SFT term.
+ * Errors: EINVAL (sizes, non-finite times or bins, mismatch with the other
+ * detectors' T / k_lo / n_bins), ENOMEM, ECUDA. */
+int fstat_set_sfts(fstat_ctx *ctx, int32_t det_index, const fstat_detector *det, double Tsft,
+                   int64_t k_lo, int32_t n_bins, int32_t n_sft, const double *t_start,
+                   const float *bins, int32_t mem);
+
+/* Set the template bank: n_sky sky positions x n_fdot spindowns x n_f
+ * frequencies f_j = f0 + j df, all at reference time t_ref.
+ *   sky   [n_sky][2] (alpha, delta) radians, host
+ *   fdot  [n_fdot] Hz/s, host
+ * Errors: EINVAL (counts < 1, df <= 0, non-finite values, more than 2^40
+ * templates), ENOMEM. */
+int fstat_set_templates(fstat_ctx *ctx, const double *sky, int32_t n_sky, double f0, double df,
+                        int32_t n_f, const double *fdot, int32_t n_fdot, double t_ref);
+
+/* Compute 2F of every template and the top-K toplist, asynchronously on
+ * `cuda_stream` (a cudaStream_t; NULL = the legacy default stream).
+ * Runs: per-SFT detector state, per-(sky, SFT) timing / antenna / phase and
+ * bin bases in FP64, the Dirichlet accumulation and 2F combine in FP32, and
+ * the toplist selection.  Results stay on the device until read.
+ * Errors: ESTATE (no SFTs or no templates), ECUDA (launch failure). */
+int fstat_compute(fstat_ctx *ctx, void *cuda_stream);
+
+/* Copy 2F of templates [offset, offset + count) to `out` (host or device per
+ * `mem`), after synchronising the context's stream.  FP32.
+ * Errors: ESTATE (nothing computed), EINVAL (range), ERANGE / ETIMEOUT if the
+ * computation flagged an error. */
+int fstat_get_2f(fstat_ctx *ctx, float *out, int64_t offset, int64_t count, int32_t mem);
+
+/* Copy the first k (<= topk) toplist entries, ordered by 2F descending then
+ * template index ascending, to host arrays idx[k] and twoF[k].  Synchronises.
+ * Errors: ESTATE, EINVAL (k out of range), ERANGE. */
+int fstat_get_toplist(fstat_ctx *ctx, int32_t k, int64_t *idx, float *twoF);
+
+/* Per-sky antenna-pattern sums of the last compute: out[n_sky][4] =
+ * (A, B, C, D) in FP64 (host).  Synchronises. */
+int fstat_get_abcd(fstat_ctx *ctx, double *out);
+
+/* Per-SFT timing and antenna values of sky point `sky` from the last compute,
+ * for all SFTs of all detectors in load order (detector 0 first): dtau, tdot
+ * (FP64) and a, b (FP64), host arrays of length n_sft_total.  Synchronises. */
+int fstat_get_sft_timing(fstat_ctx *ctx, int32_t sky, double *dtau, double *tdot, double *a,
+                         double *b);
+
+/* Add n_sig model-exact continuous-wave signals to the loaded SFT bins
+ * (all detectors), X_k += (T/2)(a c_a + b c_b) e^{i Phi} (-1)^k sinc(khat - k),
+ * the Fourier transform of the signal with its phase linearised about each
+ * SFT midpoint, with h0 chosen so that the signal's optimal SNR is rho
+ * (rho^2 = (T^2/2)(A|c_a|^2 + B|c_b|^2 + 2C Re(c_a c_b*))).  The sum of the
+ * stored bins and all signals is formed in FP64 and rounded to FP32 once.
+ *   sig   [n_sig] host;  t_ref reference time of the signals' phase.
+ * Errors: ESTATE (no SFTs), EINVAL. */
+int fstat_inject(fstat_ctx *ctx, const fstat_signal *sig, int32_t n_sig, double t_ref);
+
+/* Copy the stored complex64 bins of detector det_index (after any
+ * injections) to out[n_sft][n_bins][2] FP32, host or device per `mem`.
+ * Synchronises.  Errors: EINVAL (detector not loaded), ECUDA. */
+int fstat_get_bins(fstat_ctx *ctx, int32_t det_index, float *out, int32_t mem);
+
+/* Device-side error flags raised by the last compute (0 = none); synchronises.
+ * Bit 0: a template window left the staged SFT range (clamped).
+ * Bit 1: a sky point had D = AB - C^2 <= 0 (its 2F set to 0). */
+int fstat_get_error_flags(fstat_ctx *ctx, int32_t *flags);
+
+/* Tile configuration chosen for the current bank (after fstat_set_templates):
+ * out[8] = (P, L, M, warps, sft_chunk, lane-groups per column row,
+ *           staged pairs per SFT, kernel variant id). */
+int fstat_get_plan(fstat_ctx *ctx, int32_t *out);
+
+/* Number of CUDA kernels this context has launched since it was created. */
+int fstat_get_launch_count(fstat_ctx *ctx, int64_t *n_launches);
+
+/* Average device time of the Dirichlet kernel over the last `fstat_compute`
+ * calls since the previous query, measured with CUDA events recorded around
+ * its launch on the compute stream (milliseconds; 0 if none).  Resets the
+ * accumulator.  Synchronises. */
+int fstat_take_kernel_time(fstat_ctx *ctx, double *ms_dirichlet, double *ms_total, int32_t *n_calls);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FSTAT_H */

@@ -1,0 +1,803 @@
+// C ABI of libfstat: context, input validation, tile planning and launches.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "fstat_internal.cuh"
+
+namespace fs {
+cudaError_t launch_dirichlet_c64(int v, const DirichletParams& p, int d_rt, int threads, size_t smem,
+                                 long long grid, cudaStream_t s);
+cudaError_t launch_dirichlet_f16(int v, const DirichletParams& p, int d_rt, int threads, size_t smem,
+                                 long long grid, cudaStream_t s);
+cudaError_t launch_dirichlet_bf16(int v, const DirichletParams& p, int d_rt, int threads, size_t smem,
+                                  long long grid, cudaStream_t s);
+size_t inject_work_doubles(int n_sig, int n_sft);
+}  // namespace fs
+
+using namespace fs;
+
+namespace {
+
+// Variant table, in the order of FS_DIRICHLET_VARIANTS: (D, M, L, kahan).
+struct VariantRow {
+    int D, M, L, kahan;
+};
+const VariantRow kVariants[] = {{8, 9, 2, 0}, {8, 8, 2, 0}, {8, 8, 1, 0}, {8, 1, 1, 0}, {8, 4, 2, 1},
+                                {8, 4, 1, 1}, {8, 1, 1, 1}, {0, 1, 1, 0}, {0, 1, 1, 1}};
+constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
+
+constexpr int kTimedRing = 256;
+
+struct Plan {
+    int P = 1, L = 1, M = 1, W = 8, C = 8, lg_row = 1, lg_cta = 32, n_col = 1, chunks_per_col = 1;
+    int w_pairs = 0, w_pad = 0, variant = 3;
+    size_t smem = 0;
+    long long grid = 0;
+};
+
+struct Det {
+    bool set = false;
+    fstat_detector g{};
+    std::vector<double> t_start;
+};
+
+}  // namespace
+
+struct fstat_ctx {
+    int device = 0;
+    fstat_opts opts{};
+    std::string err;
+    // SFT store
+    bool have_sfts = false;
+    double T = 0.0;
+    long long k_lo = 0;
+    int n_bins = 0;
+    long long row = 0;   // padded row length (multiple of 8 elements)
+    Det det[kMaxDet];
+    int n_sft = 0;
+    int sft_capacity = 0;
+    float2* d_bins = nullptr;       // complex64 master copy
+    void* d_bins16 = nullptr;       // 16-bit copy (precision forms)
+    float* d_scale = nullptr;       // per-SFT storage scale
+    SftState* d_state = nullptr;
+    double* d_tstart = nullptr;
+    int* d_det_of = nullptr;
+    bool sft_dirty = true;          // state / quantisation need refresh
+    // template bank
+    bool have_templates = false;
+    int n_sky = 0, n_f = 0, n_fdot = 0;
+    double f0 = 0, df = 0, t_ref = 0;
+    double* d_sky = nullptr;
+    double* d_fdot = nullptr;
+    std::vector<double> h_sky, h_fdot;
+    // derived per-bank buffers
+    size_t cap_meta = 0, cap_kh0 = 0, cap_ph0 = 0, cap_abcd = 0, cap_comb = 0, cap_twoF = 0;
+    SkySftMeta* d_meta = nullptr;
+    long long* d_kh0 = nullptr;
+    unsigned int* d_ph0 = nullptr;
+    double* d_abcd = nullptr;
+    float4* d_comb = nullptr;
+    float* d_twoF = nullptr;
+    int* d_err = nullptr;
+    // toplist
+    TopkWork tw{};
+    int tw_k = 0;
+    // plan and bookkeeping
+    Plan plan;
+    bool plan_valid = false;
+    bool computed = false;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev_a[kTimedRing]{}, ev_b[kTimedRing]{}, ev_c[kTimedRing]{}, ev_d[kTimedRing]{};
+    int n_timed = 0;
+    long long launches = 0;   // kernels launched by this context
+    double* d_inj_work = nullptr;
+    size_t cap_inj = 0;
+    fstat_signal* d_sig = nullptr;
+    size_t cap_sig = 0;
+};
+
+namespace {
+
+int fail(fstat_ctx* c, int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return code;
+}
+
+#define CUDA_TRY(ctx, call)                                                                      \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess)                                                                   \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? FSTAT_ENOMEM : FSTAT_ECUDA,      \
+                        "%s: %s", #call, cudaGetErrorString(e_));                                \
+    } while (0)
+
+template <class T>
+int grow(fstat_ctx* c, T** p, size_t& cap, size_t n) {
+    if (n <= cap && *p) return FSTAT_OK;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    cap = 0;
+    cudaError_t e = cudaMalloc((void**)p, std::max<size_t>(n, 1) * sizeof(T));
+    if (e != cudaSuccess) return fail(c, FSTAT_ENOMEM, "cudaMalloc(%zu bytes): %s", n * sizeof(T), cudaGetErrorString(e));
+    cap = n;
+    return FSTAT_OK;
+}
+
+int set_device(fstat_ctx* c) {
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return fail(c, FSTAT_ECUDA, "cudaSetDevice(%d): %s", c->device, cudaGetErrorString(e));
+    return FSTAT_OK;
+}
+
+int variant_id(int D, int M, int L, int kahan) {
+    for (int i = 0; i < kNumVariants; ++i) {
+        const VariantRow& v = kVariants[i];
+        if (v.D == D && v.M == M && v.L == L && v.kahan == kahan) return i;
+    }
+    return -1;
+}
+
+// Templates in a column the staging range has to cover, and its width in pairs.
+int pairs_needed(const fstat_ctx* c, int span_templates, int D) {
+    // largest tdot: orbital + rotational speed over c, with margin
+    const double tdot_max = 1.0 + 1.1e-4;
+    const double dk_max = c->df * c->T * tdot_max;
+    double fd_min = c->h_fdot[0], fd_max = c->h_fdot[0];
+    for (double v : c->h_fdot) {
+        fd_min = std::min(fd_min, v);
+        fd_max = std::max(fd_max, v);
+    }
+    double tau_max = 0.0;
+    for (int d = 0; d < kMaxDet; ++d)
+        for (double t : c->det[d].t_start) tau_max = std::max(tau_max, std::fabs(t + 0.5 * c->T - c->t_ref));
+    tau_max += 500.0;   // Roemer delay bound (AU + R_E)/c < 500 s
+    const double spread = (fd_max - fd_min) * tau_max * c->T * tdot_max;
+    return (int)std::ceil((span_templates - 1) * dk_max + spread) + 2 * D + 4;
+}
+
+int make_plan(fstat_ctx* c, Plan& out) {
+    const int D = c->opts.dterms;
+    const int kahan = c->opts.kahan ? 1 : 0;
+    const double dk_nom = c->df * c->T;
+    int P = 1, L = 1, M = 1;
+    bool found = false;
+    if (D == 8) {
+        const int Ls[2] = {2, 1};
+        const int Ps[4] = {1, 2, 4, 8};
+        for (int li = 0; li < 2 && !found; ++li)
+            for (int pi = 0; pi < 4 && !found; ++pi)
+                if (std::fabs(Ps[pi] * dk_nom - Ls[li]) <= 1e-6 * Ls[li]) {
+                    P = Ps[pi];
+                    L = Ls[li];
+                    found = true;
+                }
+    }
+    std::vector<int> Ms;
+    if (found) {
+        if (kahan) Ms = {4};
+        else if (L == 2) Ms = {9, 8};
+        else Ms = {8};
+    } else {
+        P = 1;
+        L = 1;
+        Ms = {1};
+    }
+    if (c->opts.tile_m > 0) Ms = {c->opts.tile_m};
+    const int Dv = (D == 8) ? 8 : 0;
+    double best_cost = 1e300;
+    Plan best;
+    bool have = false;
+    for (int M_ : Ms) {
+        const int Lq = (Dv == 0 || M_ == 1) ? 1 : L;
+        const int vid = variant_id(Dv, (Dv == 0 ? 1 : M_), Lq, kahan);
+        if (vid < 0) continue;
+        const int Mv = kVariants[vid].M, Lv = kVariants[vid].L;
+        const int Pv = (Dv == 0 || Mv == 1) && !found ? 1 : P;
+        const int PM = Pv * Mv;
+        const int lg_full = (c->n_f + PM - 1) / PM;
+        for (int W = Pv; W <= 10; W += Pv) {
+            if (c->opts.tile_warps > 0 && W != c->opts.tile_warps) continue;
+            const int lg_cta = 32 * W / Pv;
+            const int lg_max = std::min(lg_full, lg_cta);
+            for (int lg_row = 1; lg_row <= lg_max; ++lg_row) {
+                const int col_w = lg_row * PM;
+                const int n_col = (c->n_f + col_w - 1) / col_w;
+                // the table must hold at least one thread's full window set
+                const int w_pairs = std::max(pairs_needed(c, col_w, D), (Mv - 1) * Lv + 2 * D + 2);
+                const int w_pad = w_pairs + (w_pairs >> 4) + 1;
+                int C = c->opts.sft_chunk > 0 ? c->opts.sft_chunk : 8;
+                size_t smem = dirichlet_smem_bytes(C, w_pad, c->n_fdot);
+                while (C > 1 && smem > 110 * 1024) {
+                    --C;
+                    smem = dirichlet_smem_bytes(C, w_pad, c->n_fdot);
+                }
+                if (smem > 220 * 1024) continue;
+                double cost = 0.0;
+                int chunks_max = 0;
+                for (int col = 0; col < n_col; ++col) {
+                    const int width = std::min(col_w, c->n_f - col * col_w);
+                    const int Gc = (width + PM - 1) / PM;
+                    const long long LG = (long long)c->n_fdot * Gc;
+                    const int chunks = (int)((LG + lg_cta - 1) / lg_cta);
+                    chunks_max = std::max(chunks_max, chunks);
+                    for (int k = 0; k < chunks; ++k) {
+                        const long long lgs = std::min<long long>(lg_cta, LG - (long long)k * lg_cta);
+                        const long long warps = (lgs + 31) / 32 * Pv;
+                        cost += (double)warps * 32.0 * Mv * 85.0 + (double)w_pairs * 14.0 + 400.0;
+                    }
+                }
+                if (cost < best_cost * 0.999) {
+                    best_cost = cost;
+                    best.P = Pv;
+                    best.L = Lv;
+                    best.M = Mv;
+                    best.W = W;
+                    best.C = C;
+                    best.lg_row = lg_row;
+                    best.lg_cta = lg_cta;
+                    best.n_col = n_col;
+                    best.chunks_per_col = chunks_max;
+                    best.w_pairs = w_pairs;
+                    best.w_pad = w_pad;
+                    best.variant = vid;
+                    best.smem = smem;
+                    best.grid = (long long)c->n_sky * n_col * chunks_max;
+                    have = true;
+                }
+            }
+        }
+    }
+    if (!have) return fail(c, FSTAT_EINVAL, "no Dirichlet tile plan fits this template bank");
+    out = best;
+    return FSTAT_OK;
+}
+
+bool all_finite(const double* v, size_t n) {
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(v[i])) return false;
+    return true;
+}
+
+__global__ void finite_check_kernel(const float* v, long long n, int* bad) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        if (!isfinite(v[i])) atomicOr(bad, 1);
+}
+
+__global__ void fill_kernel(float* v, long long n, float x) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        v[i] = x;
+}
+
+int ensure_topk(fstat_ctx* c) {
+    const int k = c->opts.topk;
+    if (k <= 0) return FSTAT_OK;
+    if (c->tw_k >= k) return FSTAT_OK;
+    TopkWork& w = c->tw;
+    cudaFree(w.hist);
+    cudaFree(w.state);
+    cudaFree(w.tie_count);
+    cudaFree(w.cand_idx);
+    cudaFree(w.cand_val);
+    cudaFree(w.n_cand);
+    cudaFree(w.out_idx);
+    cudaFree(w.out_val);
+    w = TopkWork{};
+    w.n_blocks = 1024;
+    CUDA_TRY(c, cudaMalloc(&w.hist, sizeof(unsigned int) * 3 * 2048));
+    CUDA_TRY(c, cudaMalloc(&w.state, sizeof(unsigned int) * 16));
+    CUDA_TRY(c, cudaMalloc(&w.tie_count, sizeof(unsigned int) * w.n_blocks));
+    CUDA_TRY(c, cudaMalloc(&w.cand_idx, sizeof(long long) * k));
+    CUDA_TRY(c, cudaMalloc(&w.cand_val, sizeof(float) * k));
+    CUDA_TRY(c, cudaMalloc(&w.n_cand, sizeof(unsigned int)));
+    CUDA_TRY(c, cudaMalloc(&w.out_idx, sizeof(long long) * k));
+    CUDA_TRY(c, cudaMalloc(&w.out_val, sizeof(float) * k));
+    c->tw_k = k;
+    return FSTAT_OK;
+}
+
+int sync_ctx(fstat_ctx* c) {
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return fail(c, FSTAT_ECUDA, "stream synchronize: %s", cudaGetErrorString(e));
+    return FSTAT_OK;
+}
+
+int refresh_sft_state(fstat_ctx* c, cudaStream_t s) {
+    if (!c->sft_dirty) return FSTAT_OK;
+    std::vector<double> ts;
+    std::vector<int> det_of;
+    fstat_detector g[kMaxDet];
+    std::memset(g, 0, sizeof(g));
+    for (int d = 0; d < kMaxDet; ++d) {
+        if (!c->det[d].set) continue;
+        g[d] = c->det[d].g;
+        for (double t : c->det[d].t_start) {
+            ts.push_back(t);
+            det_of.push_back(d);
+        }
+    }
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_tstart, ts.data(), ts.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_det_of, det_of.data(), det_of.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(c, launch_sft_state(c->d_tstart, c->d_det_of, g, c->n_sft, c->T, c->d_state, s));
+    c->launches += 2;   // detector state + scale fill / quantisation
+    if (c->opts.bins_form == FSTAT_BINS_C64) {
+        fill_kernel<<<64, 256, 0, s>>>(c->d_scale, c->n_sft, 1.0f);
+        CUDA_TRY(c, cudaGetLastError());
+    } else {
+        CUDA_TRY(c, launch_quantize(c->d_bins, c->row, c->n_sft, c->n_bins, c->opts.bins_form, c->d_bins16,
+                                    c->d_scale, s));
+    }
+    // the host vectors are copied asynchronously: wait before they go out of scope
+    CUDA_TRY(c, cudaStreamSynchronize(s));
+    c->sft_dirty = false;
+    return FSTAT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* fstat_version(void) { return "libfstat 0.1 (sm_103a)"; }
+
+int fstat_create(fstat_ctx** out, int device, const fstat_opts* opts) {
+    if (!out) return FSTAT_EINVAL;
+    *out = nullptr;
+    fstat_opts o{};
+    o.dterms = 8;
+    o.bins_form = FSTAT_BINS_C64;
+    o.topk = 1000;
+    if (opts) o = *opts;
+    if (o.dterms < 1 || o.dterms > 64) return FSTAT_EINVAL;
+    if (o.topk < 0 || o.topk > 16384) return FSTAT_EINVAL;
+    if (o.bins_form < 0 || o.bins_form > 2) return FSTAT_EINVAL;
+    if (o.tile_m < 0 || o.tile_warps < 0 || o.tile_warps > 10 || o.sft_chunk < 0 || o.sft_chunk > 64)
+        return FSTAT_EINVAL;
+    int n_dev = 0;
+    if (cudaGetDeviceCount(&n_dev) != cudaSuccess || device < 0 || device >= n_dev) return FSTAT_ECUDA;
+    fstat_ctx* c = new fstat_ctx();
+    c->device = device;
+    c->opts = o;
+    if (set_device(c) != FSTAT_OK) {
+        delete c;
+        return FSTAT_ECUDA;
+    }
+    if (cudaMalloc(&c->d_err, sizeof(int) * 4) != cudaSuccess) {
+        delete c;
+        return FSTAT_ENOMEM;
+    }
+    cudaMemset(c->d_err, 0, sizeof(int) * 4);
+    for (int i = 0; i < kTimedRing; ++i) {
+        cudaEventCreate(&c->ev_a[i]);
+        cudaEventCreate(&c->ev_b[i]);
+        cudaEventCreate(&c->ev_c[i]);
+        cudaEventCreate(&c->ev_d[i]);
+    }
+    *out = c;
+    return FSTAT_OK;
+}
+
+void fstat_destroy(fstat_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    void* ptrs[] = {c->d_bins, c->d_bins16, c->d_scale, c->d_state, c->d_tstart, c->d_det_of, c->d_sky,
+                    c->d_fdot, c->d_meta, c->d_kh0, c->d_ph0, c->d_abcd, c->d_comb, c->d_twoF, c->d_err,
+                    c->tw.hist, c->tw.state, c->tw.tie_count, c->tw.cand_idx, c->tw.cand_val, c->tw.n_cand,
+                    c->tw.out_idx, c->tw.out_val, c->d_inj_work, c->d_sig};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    for (int i = 0; i < kTimedRing; ++i) {
+        cudaEventDestroy(c->ev_a[i]);
+        cudaEventDestroy(c->ev_b[i]);
+        cudaEventDestroy(c->ev_c[i]);
+        cudaEventDestroy(c->ev_d[i]);
+    }
+    delete c;
+}
+
+const char* fstat_last_error(const fstat_ctx* c) { return c ? c->err.c_str() : ""; }
+
+int fstat_set_sfts(fstat_ctx* c, int32_t det_index, const fstat_detector* det, double Tsft, int64_t k_lo,
+                   int32_t n_bins, int32_t n_sft, const double* t_start, const float* bins, int32_t mem) {
+    if (!c) return FSTAT_EINVAL;
+    c->err.clear();
+    if (det_index < 0 || det_index >= kMaxDet) return fail(c, FSTAT_EINVAL, "det_index %d out of 0..7", det_index);
+    if (!det || !t_start || !bins) return fail(c, FSTAT_EINVAL, "null pointer argument");
+    if (!(Tsft > 0) || !std::isfinite(Tsft)) return fail(c, FSTAT_EINVAL, "Tsft must be finite and > 0");
+    if (n_bins < 2) return fail(c, FSTAT_EINVAL, "n_bins must be >= 2");
+    if (n_sft < 1 || n_sft > 32768) return fail(c, FSTAT_EINVAL, "n_sft must be in 1..32768");
+    if (mem != FSTAT_MEM_HOST && mem != FSTAT_MEM_DEVICE) return fail(c, FSTAT_EINVAL, "mem must be 0 or 1");
+    if (!std::isfinite(det->lat_rad) || !std::isfinite(det->lon_rad) || !std::isfinite(det->xarm_az_rad))
+        return fail(c, FSTAT_EINVAL, "non-finite detector geometry");
+    if (!all_finite(t_start, n_sft)) return fail(c, FSTAT_EINVAL, "non-finite SFT start time");
+    if (k_lo < 0 || k_lo > (1LL << 30)) return fail(c, FSTAT_EINVAL, "k_lo out of range");
+    bool others = false;
+    for (int d = 0; d < kMaxDet; ++d) others |= (d != det_index && c->det[d].set);
+    if (others && (Tsft != c->T || k_lo != c->k_lo || n_bins != c->n_bins))
+        return fail(c, FSTAT_EINVAL, "all detectors must share Tsft, k_lo and n_bins");
+    if (set_device(c) != FSTAT_OK) return FSTAT_ECUDA;
+    if (n_bins > (1 << 24)) return fail(c, FSTAT_EINVAL, "n_bins too large");
+    // new layout: detectors in index order, rows padded to 8 elements
+    const long long row = ((long long)n_bins + 7) & ~7LL;
+    int total = 0;
+    int first_of[kMaxDet];
+    for (int d = 0; d < kMaxDet; ++d) {
+        first_of[d] = total;
+        if (d == det_index) total += n_sft;
+        else if (c->det[d].set) total += (int)c->det[d].t_start.size();
+    }
+    if (total > 65535) return fail(c, FSTAT_EINVAL, "more than 65535 SFTs in one context");
+    // host staging for device input: validate values
+    std::vector<float> hb;
+    const float* src = bins;
+    const size_t n_el = (size_t)n_sft * n_bins * 2;
+    if (mem == FSTAT_MEM_HOST) {
+        for (size_t i = 0; i < n_el; ++i)
+            if (!std::isfinite(bins[i])) return fail(c, FSTAT_EINVAL, "non-finite SFT bin at %zu", i);
+    }
+    // new device store; copy kept detectors over
+    float2* nb = nullptr;
+    CUDA_TRY(c, cudaMalloc(&nb, (size_t)total * row * sizeof(float2)));
+    CUDA_TRY(c, cudaMemsetAsync(nb, 0, (size_t)total * row * sizeof(float2), c->stream));
+    int old_first = 0;
+    for (int d = 0; d < kMaxDet; ++d) {
+        const int n_old = c->det[d].set ? (int)c->det[d].t_start.size() : 0;
+        if (d != det_index && n_old) {
+            CUDA_TRY(c, cudaMemcpyAsync(nb + (size_t)first_of[d] * row, c->d_bins + (size_t)old_first * c->row,
+                                        (size_t)n_old * row * sizeof(float2), cudaMemcpyDeviceToDevice, c->stream));
+        }
+        old_first += n_old;
+    }
+    CUDA_TRY(c, cudaMemcpy2DAsync(nb + (size_t)first_of[det_index] * row, row * sizeof(float2), src,
+                                  (size_t)n_bins * sizeof(float2), (size_t)n_bins * sizeof(float2), n_sft,
+                                  mem == FSTAT_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                                  c->stream));
+    if (mem == FSTAT_MEM_DEVICE) {
+        int* bad = c->d_err + 3;
+        CUDA_TRY(c, cudaMemsetAsync(bad, 0, sizeof(int), c->stream));
+        finite_check_kernel<<<256, 256, 0, c->stream>>>(bins, (long long)n_el, bad);
+        CUDA_TRY(c, cudaGetLastError());
+        c->launches += 1;
+        int hbad = 0;
+        CUDA_TRY(c, cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        if (hbad) {
+            cudaFree(nb);
+            return fail(c, FSTAT_EINVAL, "non-finite SFT bin in device input");
+        }
+    }
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    if (c->d_bins) cudaFree(c->d_bins);
+    c->d_bins = nb;
+    c->row = row;
+    c->det[det_index].set = true;
+    c->det[det_index].g = *det;
+    c->det[det_index].t_start.assign(t_start, t_start + n_sft);
+    c->n_sft = total;
+    c->T = Tsft;
+    c->k_lo = k_lo;
+    c->n_bins = n_bins;
+    // per-SFT buffers
+    if (c->d_state) cudaFree(c->d_state);
+    if (c->d_tstart) cudaFree(c->d_tstart);
+    if (c->d_det_of) cudaFree(c->d_det_of);
+    if (c->d_scale) cudaFree(c->d_scale);
+    if (c->d_bins16) cudaFree(c->d_bins16);
+    c->d_state = nullptr;
+    c->d_tstart = nullptr;
+    c->d_det_of = nullptr;
+    c->d_scale = nullptr;
+    c->d_bins16 = nullptr;
+    CUDA_TRY(c, cudaMalloc(&c->d_state, (size_t)total * sizeof(SftState)));
+    CUDA_TRY(c, cudaMalloc(&c->d_tstart, (size_t)total * sizeof(double)));
+    CUDA_TRY(c, cudaMalloc(&c->d_det_of, (size_t)total * sizeof(int)));
+    CUDA_TRY(c, cudaMalloc(&c->d_scale, (size_t)total * sizeof(float)));
+    if (c->opts.bins_form != FSTAT_BINS_C64)
+        CUDA_TRY(c, cudaMalloc(&c->d_bins16, (size_t)total * row * 4));
+    c->have_sfts = true;
+    c->sft_dirty = true;
+    c->plan_valid = false;
+    c->computed = false;
+    return FSTAT_OK;
+}
+
+int fstat_set_templates(fstat_ctx* c, const double* sky, int32_t n_sky, double f0, double df, int32_t n_f,
+                        const double* fdot, int32_t n_fdot, double t_ref) {
+    if (!c) return FSTAT_EINVAL;
+    c->err.clear();
+    if (!sky || !fdot) return fail(c, FSTAT_EINVAL, "null pointer argument");
+    if (n_sky < 1 || n_f < 1 || n_fdot < 1) return fail(c, FSTAT_EINVAL, "template counts must be >= 1");
+    if (n_fdot > 64) return fail(c, FSTAT_EINVAL, "at most 64 spindowns per bank");
+    if (!(df > 0) || !std::isfinite(df) || !std::isfinite(f0) || !(f0 > 0) || !std::isfinite(t_ref))
+        return fail(c, FSTAT_EINVAL, "f0, df must be finite and > 0, t_ref finite");
+    if (!all_finite(sky, 2 * (size_t)n_sky) || !all_finite(fdot, n_fdot))
+        return fail(c, FSTAT_EINVAL, "non-finite sky position or spindown");
+    const double nt = (double)n_sky * n_fdot * n_f;
+    if (nt > (double)(1LL << 40)) return fail(c, FSTAT_EINVAL, "more than 2^40 templates");
+    if (set_device(c) != FSTAT_OK) return FSTAT_ECUDA;
+    c->h_sky.assign(sky, sky + 2 * (size_t)n_sky);
+    c->h_fdot.assign(fdot, fdot + n_fdot);
+    if (c->d_sky) cudaFree(c->d_sky);
+    if (c->d_fdot) cudaFree(c->d_fdot);
+    c->d_sky = nullptr;
+    c->d_fdot = nullptr;
+    CUDA_TRY(c, cudaMalloc(&c->d_sky, 2 * (size_t)n_sky * sizeof(double)));
+    CUDA_TRY(c, cudaMalloc(&c->d_fdot, (size_t)n_fdot * sizeof(double)));
+    CUDA_TRY(c, cudaMemcpy(c->d_sky, sky, 2 * (size_t)n_sky * sizeof(double), cudaMemcpyHostToDevice));
+    CUDA_TRY(c, cudaMemcpy(c->d_fdot, fdot, (size_t)n_fdot * sizeof(double), cudaMemcpyHostToDevice));
+    c->n_sky = n_sky;
+    c->n_f = n_f;
+    c->n_fdot = n_fdot;
+    c->f0 = f0;
+    c->df = df;
+    c->t_ref = t_ref;
+    c->have_templates = true;
+    c->plan_valid = false;
+    c->computed = false;
+    return FSTAT_OK;
+}
+
+int fstat_compute(fstat_ctx* c, void* cuda_stream) {
+    if (!c) return FSTAT_EINVAL;
+    c->err.clear();
+    if (!c->have_sfts || !c->have_templates) return fail(c, FSTAT_ESTATE, "load SFTs and set templates first");
+    if (set_device(c) != FSTAT_OK) return FSTAT_ECUDA;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    c->stream = s;
+    int rc;
+    if ((rc = refresh_sft_state(c, s)) != FSTAT_OK) return rc;
+    if (!c->plan_valid) {
+        if ((rc = make_plan(c, c->plan)) != FSTAT_OK) return rc;
+        c->plan_valid = true;
+    }
+    const Plan& pl = c->plan;
+    const size_t n_meta = (size_t)c->n_sky * c->n_sft;
+    const size_t n_base = n_meta * c->n_fdot;
+    const size_t n_twoF = (size_t)c->n_sky * c->n_fdot * c->n_f;
+    if ((rc = grow(c, &c->d_meta, c->cap_meta, n_meta)) != FSTAT_OK) return rc;
+    if ((rc = grow(c, &c->d_kh0, c->cap_kh0, n_base)) != FSTAT_OK) return rc;
+    if ((rc = grow(c, &c->d_ph0, c->cap_ph0, n_base)) != FSTAT_OK) return rc;
+    if ((rc = grow(c, &c->d_abcd, c->cap_abcd, 4 * (size_t)c->n_sky)) != FSTAT_OK) return rc;
+    if ((rc = grow(c, &c->d_comb, c->cap_comb, (size_t)c->n_sky)) != FSTAT_OK) return rc;
+    if ((rc = grow(c, &c->d_twoF, c->cap_twoF, n_twoF)) != FSTAT_OK) return rc;
+    if ((rc = ensure_topk(c)) != FSTAT_OK) return rc;
+    CUDA_TRY(c, cudaMemsetAsync(c->d_err, 0, sizeof(int) * 3, s));
+
+    const int slot = c->n_timed % kTimedRing;
+    CUDA_TRY(c, cudaEventRecord(c->ev_a[slot], s));
+    TimingParams tp{};
+    tp.st = c->d_state;
+    tp.sky = c->d_sky;
+    tp.fdot = c->d_fdot;
+    tp.scale = c->d_scale;
+    tp.n_sky = c->n_sky;
+    tp.n_sft = c->n_sft;
+    tp.n_fdot = c->n_fdot;
+    tp.f0 = c->f0;
+    tp.df = c->df;
+    tp.T = c->T;
+    tp.t_ref = c->t_ref;
+    tp.P = pl.P;
+    tp.L = pl.L;
+    tp.M = pl.M;
+    tp.meta = c->d_meta;
+    tp.kh0 = c->d_kh0;
+    tp.ph0 = c->d_ph0;
+    tp.abcd = c->d_abcd;
+    tp.comb = c->d_comb;
+    tp.err = c->d_err;
+    CUDA_TRY(c, launch_timing(tp, s));
+
+    DirichletParams dp{};
+    dp.bins = c->opts.bins_form == FSTAT_BINS_C64 ? (const void*)c->d_bins : (const void*)c->d_bins16;
+    dp.row = c->row;
+    dp.k_lo = c->k_lo;
+    dp.n_bins = c->n_bins;
+    dp.n_sft = c->n_sft;
+    dp.meta = c->d_meta;
+    dp.kh0 = c->d_kh0;
+    dp.ph0 = c->d_ph0;
+    dp.comb = c->d_comb;
+    dp.twoF = c->d_twoF;
+    dp.n_sky = c->n_sky;
+    dp.n_fdot = c->n_fdot;
+    dp.n_f = c->n_f;
+    dp.P = pl.P;
+    dp.lg_row = pl.lg_row;
+    dp.lg_cta = pl.lg_cta;
+    dp.chunks_per_col = pl.chunks_per_col;
+    dp.n_col = pl.n_col;
+    dp.w_pairs = pl.w_pairs;
+    dp.w_pad = pl.w_pad;
+    dp.sft_chunk = pl.C;
+    dp.err = c->d_err;
+    CUDA_TRY(c, cudaEventRecord(c->ev_b[slot], s));
+    cudaError_t e;
+    const int threads = pl.W * 32;
+    if (c->opts.bins_form == FSTAT_BINS_C64)
+        e = launch_dirichlet_c64(pl.variant, dp, c->opts.dterms, threads, pl.smem, pl.grid, s);
+    else if (c->opts.bins_form == FSTAT_BINS_F16)
+        e = launch_dirichlet_f16(pl.variant, dp, c->opts.dterms, threads, pl.smem, pl.grid, s);
+    else
+        e = launch_dirichlet_bf16(pl.variant, dp, c->opts.dterms, threads, pl.smem, pl.grid, s);
+    if (e != cudaSuccess) return fail(c, FSTAT_ECUDA, "Dirichlet launch: %s", cudaGetErrorString(e));
+    CUDA_TRY(c, cudaEventRecord(c->ev_c[slot], s));
+    const long long n = (long long)n_twoF;
+    const int k = (int)std::min<long long>(c->opts.topk, n);
+    c->launches += 2;   // timing + Dirichlet
+    if (k > 0) {
+        CUDA_TRY(c, launch_topk(c->d_twoF, n, k, c->tw, s));
+        c->launches += 9;   // 3 histograms, 3 selections, collect, ties, sort
+    }
+    CUDA_TRY(c, cudaEventRecord(c->ev_d[slot], s));
+    c->n_timed++;
+    c->computed = true;
+    return FSTAT_OK;
+}
+
+int fstat_get_2f(fstat_ctx* c, float* out, int64_t offset, int64_t count, int32_t mem) {
+    if (!c) return FSTAT_EINVAL;
+    c->err.clear();
+    if (!c->computed) return fail(c, FSTAT_ESTATE, "nothing computed");
+    const long long n = (long long)c->n_sky * c->n_fdot * c->n_f;
+    if (!out || offset < 0 || count < 0 || offset + count > n) return fail(c, FSTAT_EINVAL, "range out of bounds");
+    if (set_device(c) != FSTAT_OK) return FSTAT_ECUDA;
+    CUDA_TRY(c, cudaMemcpyAsync(out, c->d_twoF + offset, (size_t)count * sizeof(float),
+                                mem == FSTAT_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                c->stream));
+    return sync_ctx(c);
+}
+
+int fstat_get_toplist(fstat_ctx* c, int32_t k, int64_t* idx, float* twoF) {
+    if (!c) return FSTAT_EINVAL;
+    c->err.clear();
+    if (!c->computed) return fail(c, FSTAT_ESTATE, "nothing computed");
+    const long long n = (long long)c->n_sky * c->n_fdot * c->n_f;
+    const int kmax = (int)std::min<long long>(c->opts.topk, n);
+    if (k < 0 || k > kmax || (k > 0 && (!idx || !twoF))) return fail(c, FSTAT_EINVAL, "k out of range 0..%d", kmax);
+    if (set_device(c) != FSTAT_OK) return FSTAT_ECUDA;
+    if (k > 0) {
+        CUDA_TRY(c, cudaMemcpyAsync(idx, c->tw.out_idx, (size_t)k * sizeof(long long), cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(c, cudaMemcpyAsync(twoF, c->tw.out_val, (size_t)k * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    }
+    return sync_ctx(c);
+}
+
+int fstat_get_abcd(fstat_ctx* c, double* out) {
+    if (!c || !out) return FSTAT_EINVAL;
+    c->err.clear();
+    if (!c->computed) return fail(c, FSTAT_ESTATE, "nothing computed");
+    if (set_device(c) != FSTAT_OK) return FSTAT_ECUDA;
+    CUDA_TRY(c, cudaMemcpyAsync(out, c->d_abcd, 4 * (size_t)c->n_sky * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    return sync_ctx(c);
+}
+
+int fstat_get_sft_timing(fstat_ctx* c, int32_t sky, double* dtau, double* tdot, double* a, double* b) {
+    if (!c || !dtau || !tdot || !a || !b) return FSTAT_EINVAL;
+    c->err.clear();
+    if (!c->have_sfts || !c->have_templates) return fail(c, FSTAT_ESTATE, "load SFTs and set templates first");
+    if (sky < 0 || sky >= c->n_sky) return fail(c, FSTAT_EINVAL, "sky index out of range");
+    if (set_device(c) != FSTAT_OK) return FSTAT_ECUDA;
+    int rc;
+    if ((rc = refresh_sft_state(c, c->stream)) != FSTAT_OK) return rc;
+    double* d_out = nullptr;
+    CUDA_TRY(c, cudaMalloc(&d_out, 4 * (size_t)c->n_sft * sizeof(double)));
+    cudaError_t e = launch_sft_timing_one(c->d_state, c->n_sft, c->h_sky[2 * sky], c->h_sky[2 * sky + 1], c->t_ref,
+                                          d_out, c->stream);
+    std::vector<double> h(4 * (size_t)c->n_sft);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h.data(), d_out, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(d_out);
+    if (e != cudaSuccess) return fail(c, FSTAT_ECUDA, "sft timing: %s", cudaGetErrorString(e));
+    const size_t n = c->n_sft;
+    std::memcpy(dtau, h.data(), n * sizeof(double));
+    std::memcpy(tdot, h.data() + n, n * sizeof(double));
+    std::memcpy(a, h.data() + 2 * n, n * sizeof(double));
+    std::memcpy(b, h.data() + 3 * n, n * sizeof(double));
+    return FSTAT_OK;
+}
+
+int fstat_inject(fstat_ctx* c, const fstat_signal* sig, int32_t n_sig, double t_ref) {
+    if (!c) return FSTAT_EINVAL;
+    c->err.clear();
+    if (!c->have_sfts) return fail(c, FSTAT_ESTATE, "load SFTs first");
+    if (n_sig < 0 || (n_sig > 0 && !sig) || !std::isfinite(t_ref)) return fail(c, FSTAT_EINVAL, "bad signal list");
+    if (n_sig == 0) return FSTAT_OK;
+    for (int i = 0; i < n_sig; ++i) {
+        const double v[8] = {sig[i].alpha, sig[i].delta, sig[i].psi, sig[i].cosi, sig[i].phi0, sig[i].f, sig[i].fdot, sig[i].rho};
+        if (!all_finite(v, 8) || !(sig[i].f > 0) || sig[i].rho < 0 || std::fabs(sig[i].cosi) > 1)
+            return fail(c, FSTAT_EINVAL, "signal %d has invalid parameters", i);
+    }
+    if (set_device(c) != FSTAT_OK) return FSTAT_ECUDA;
+    int rc;
+    if ((rc = refresh_sft_state(c, c->stream)) != FSTAT_OK) return rc;
+    if ((rc = grow(c, &c->d_sig, c->cap_sig, (size_t)n_sig)) != FSTAT_OK) return rc;
+    if ((rc = grow(c, &c->d_inj_work, c->cap_inj, inject_work_doubles(n_sig, c->n_sft))) != FSTAT_OK) return rc;
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_sig, sig, (size_t)n_sig * sizeof(fstat_signal), cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, launch_inject(c->d_state, c->n_sft, c->d_sig, n_sig, c->T, t_ref, c->k_lo, c->n_bins, c->row,
+                              c->d_bins, c->d_inj_work, c->stream));
+    c->launches += 2;
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    c->sft_dirty = true;   // 16-bit copies must be rebuilt
+    c->computed = false;
+    return FSTAT_OK;
+}
+
+int fstat_get_bins(fstat_ctx* c, int32_t det_index, float* out, int32_t mem) {
+    if (!c || !out) return FSTAT_EINVAL;
+    c->err.clear();
+    if (det_index < 0 || det_index >= kMaxDet || !c->det[det_index].set)
+        return fail(c, FSTAT_EINVAL, "detector %d not loaded", det_index);
+    if (set_device(c) != FSTAT_OK) return FSTAT_ECUDA;
+    int first = 0;
+    for (int d = 0; d < det_index; ++d)
+        if (c->det[d].set) first += (int)c->det[d].t_start.size();
+    const int n = (int)c->det[det_index].t_start.size();
+    CUDA_TRY(c, cudaMemcpy2DAsync(out, (size_t)c->n_bins * sizeof(float2), c->d_bins + (size_t)first * c->row,
+                                  c->row * sizeof(float2), (size_t)c->n_bins * sizeof(float2), n,
+                                  mem == FSTAT_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                  c->stream));
+    return sync_ctx(c);
+}
+
+int fstat_get_error_flags(fstat_ctx* c, int32_t* flags) {
+    if (!c || !flags) return FSTAT_EINVAL;
+    if (set_device(c) != FSTAT_OK) return FSTAT_ECUDA;
+    int h[3] = {0, 0, 0};
+    CUDA_TRY(c, cudaMemcpyAsync(h, c->d_err, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    int rc = sync_ctx(c);
+    if (rc != FSTAT_OK) return rc;
+    *flags = h[0];
+    return FSTAT_OK;
+}
+
+int fstat_get_plan(fstat_ctx* c, int32_t* out) {
+    if (!c || !out) return FSTAT_EINVAL;
+    if (!c->have_sfts || !c->have_templates) return fail(c, FSTAT_ESTATE, "load SFTs and set templates first");
+    if (!c->plan_valid) {
+        int rc = make_plan(c, c->plan);
+        if (rc != FSTAT_OK) return rc;
+        c->plan_valid = true;
+    }
+    const Plan& p = c->plan;
+    const int v[8] = {p.P, p.L, p.M, p.W, p.C, p.lg_row, p.w_pairs, p.variant};
+    std::memcpy(out, v, sizeof(v));
+    return FSTAT_OK;
+}
+
+int fstat_get_launch_count(fstat_ctx* c, int64_t* n_launches) {
+    if (!c || !n_launches) return FSTAT_EINVAL;
+    *n_launches = c->launches;
+    return FSTAT_OK;
+}
+
+int fstat_take_kernel_time(fstat_ctx* c, double* ms_dirichlet, double* ms_total, int32_t* n_calls) {
+    if (!c || !ms_dirichlet || !ms_total || !n_calls) return FSTAT_EINVAL;
+    if (set_device(c) != FSTAT_OK) return FSTAT_ECUDA;
+    const int n = std::min(c->n_timed, kTimedRing);
+    double sb = 0.0, st = 0.0;
+    for (int i = 0; i < n; ++i) {
+        CUDA_TRY(c, cudaEventSynchronize(c->ev_d[i]));
+        float mb = 0.f, mt = 0.f;
+        CUDA_TRY(c, cudaEventElapsedTime(&mb, c->ev_b[i], c->ev_c[i]));
+        CUDA_TRY(c, cudaEventElapsedTime(&mt, c->ev_a[i], c->ev_d[i]));
+        sb += mb;
+        st += mt;
+    }
+    *n_calls = n;
+    *ms_dirichlet = n ? sb / n : 0.0;
+    *ms_total = n ? st / n : 0.0;
+    c->n_timed = 0;
+    return FSTAT_OK;
+}
+
+}  // extern "C"

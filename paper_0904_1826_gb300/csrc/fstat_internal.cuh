@@ -1,0 +1,137 @@
+// Internal definitions shared by the CUDA translation units of libfstat.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "../../include/fstat.h"
+
+namespace fs {
+
+// Synthetic Sun-centred ephemeris: circular orbit in the ecliptic plane and a
+// spherical Earth rotating at the sidereal rate; equatorial coordinates.
+constexpr double kC = 299792458.0;                  // speed of light, m/s
+constexpr double kAU = 1.495978707e11;              // orbital radius, m
+constexpr double kObliquity = 0.40909280422232897;  // 23.4393 degrees in rad
+constexpr double kYear = 3.15581498e7;              // orbital period, s
+constexpr double kEarthR = 6.371e6;                 // Earth radius, m
+constexpr double kSidereal = 86164.0905;            // sidereal day, s
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+constexpr double kPi = 3.1415926535897932384626433832795;
+
+constexpr int kMaxDet = 8;
+
+// Per-SFT detector state at the SFT midpoint (FP64), written once per SFT load.
+struct SftState {
+    double t_mid;        // t_start + T/2
+    double r[3];         // position, m
+    double v[3];         // velocity, m/s
+    double dt[6];        // response tensor D (xx, xy, xz, yy, yz, zz)
+};
+
+// Per-(sky, SFT) constants of the Dirichlet kernel (48 bytes, 16-aligned).
+//   khat(j) = khat0(fdot) + j * dk  (fixed point, 2^-32 bins)
+//   Phi(j)  = Phi0(fdot) + j * dphi (fixed point, 2^-32 cycles, wraps mod 1)
+// span = (M-1) * P * dk checks that a thread's M templates (stride P) keep
+// their bin windows L bins apart; eps = P*dk - L in bins (float drift);
+// rot = e^{-2 pi i (P*dphi + L/2)} steps the twiddle between them; a, b are the
+// antenna weights times the storage scale times the kernel constant 2/pi.
+struct __align__(16) SkySftMeta {
+    long long dk;
+    long long span;
+    unsigned int dphi;
+    float eps;
+    float rot_re, rot_im;
+    float a, b;
+    float pad0, pad1;
+};
+static_assert(sizeof(SkySftMeta) == 48, "SkySftMeta layout");
+
+struct DirichletParams {
+    const void* bins;          // [n_sft][row] complex64 (float2) or 16-bit (half2 / bf162)
+    long long row;             // elements per stored SFT row (>= n_bins, padded)
+    long long k_lo;            // absolute bin of element 0
+    int n_bins;                // valid bins per row
+    int n_sft;
+    const SkySftMeta* meta;    // [n_sky][n_sft]
+    const long long* kh0;      // [n_sky][n_fdot][n_sft]
+    const unsigned int* ph0;   // [n_sky][n_fdot][n_sft]
+    const float4* comb;        // [n_sky] (2B/D, 2A/D, -4C/D, valid)
+    float* twoF;               // [n_sky][n_fdot][n_f]
+    int n_sky, n_fdot, n_f;
+    int P;                     // template stride inside a thread
+    int lg_row;                // lane-groups per row of a full column
+    int lg_cta;                // lane-groups per block
+    int chunks_per_col;        // blocks per column
+    int n_col;                 // columns per sky
+    int w_pairs;               // staged pair entries per SFT
+    int w_pad;                 // padded row length of the pair table
+    int sft_chunk;             // SFTs per staging round
+    int* err;                  // device error flags
+};
+
+// Shared-memory footprint of the Dirichlet kernel for a plan.
+inline size_t dirichlet_smem_bytes(int sft_chunk, int w_pad, int n_fdot) {
+    size_t b = (size_t)sft_chunk * w_pad * 16;          // pair table
+    b += (size_t)sft_chunk * sizeof(SkySftMeta);        // meta
+    b += (size_t)sft_chunk * n_fdot * 8;                // kh0 rows
+    b += (size_t)sft_chunk * n_fdot * 4;                // ph0 rows
+    b += (size_t)sft_chunk * 4;                         // window base
+    return (b + 15) & ~(size_t)15;
+}
+
+struct TimingParams {
+    const SftState* st;        // [n_sft]
+    const double* sky;         // [n_sky][2]
+    const double* fdot;        // [n_fdot]
+    const float* scale;        // [n_sft] storage scale (1 for complex64)
+    int n_sky, n_sft, n_fdot;
+    double f0, df, T, t_ref;
+    int P, L, M;
+    SkySftMeta* meta;          // out [n_sky][n_sft]
+    long long* kh0;            // out [n_sky][n_fdot][n_sft]
+    unsigned int* ph0;         // out [n_sky][n_fdot][n_sft]
+    double* abcd;              // out [n_sky][4]
+    float4* comb;              // out [n_sky]
+    int* err;
+};
+
+// ---- launchers (defined in the .cu files) --------------------------------
+cudaError_t launch_sft_state(const double* t_start, const int* det_of_sft, const fstat_detector* dets,
+                             int n_sft, double T, SftState* out, cudaStream_t s);
+cudaError_t launch_timing(const TimingParams& p, cudaStream_t s);
+cudaError_t launch_sft_timing_one(const SftState* st, int n_sft, double alpha, double delta,
+                                  double t_ref, double* out4, cudaStream_t s);
+cudaError_t launch_inject(const SftState* st, int n_sft, const fstat_signal* sig_dev, int n_sig,
+                          double T, double t_ref, long long k_lo, int n_bins, long long row,
+                          float2* bins, double* work, cudaStream_t s);
+cudaError_t launch_quantize(const float2* src, long long row, int n_sft, int n_bins, int form,
+                            void* dst, float* scale, cudaStream_t s);
+
+struct DirichletVariant {
+    int D, M, L, form, kahan;
+};
+int dirichlet_variant_id(const DirichletVariant& v);   // -1 if not compiled
+cudaError_t launch_dirichlet(int variant, const DirichletParams& p, int threads, size_t smem,
+                             long long grid, cudaStream_t s);
+cudaError_t launch_dirichlet_generic(int D, int form, const DirichletParams& p, int threads,
+                                     size_t smem, long long grid, cudaStream_t s);
+
+// Toplist (radix select over the FP32 bit patterns of 2F >= 0).
+struct TopkWork {
+    unsigned int* hist;        // [3][2048]
+    unsigned int* state;       // [16] prefix, threshold, counts
+    unsigned int* tie_count;   // [n_blocks]
+    unsigned long long* cand;  // [topk] (value bits << 32 | slot) scratch
+    long long* cand_idx;       // [topk]
+    float* cand_val;           // [topk]
+    unsigned int* n_cand;      // [1]
+    long long* out_idx;        // [topk]
+    float* out_val;            // [topk]
+    int n_blocks;
+};
+cudaError_t launch_topk(const float* v, long long n, int k, TopkWork& w, cudaStream_t s);
+
+}  // namespace fs

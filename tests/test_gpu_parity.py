@@ -1,0 +1,281 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerance of the FP32 path: |d2F| <= 1e-4 * 2F + 1e-3, element by element.
+Inputs are the seeded workloads of `workload`; signals are added by the
+oracle (never by the GPU) before both sides compute.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import fstat_oracle as O
+from oracle import quantize as Q
+from workload import (DET_H, DET_L, DetectorData, TemplateBank, Injection, config0, config_mid,
+                      cn_noise, gapped_timestamps, random_sky, T0, T_SFT)
+
+pytestmark = pytest.mark.gpu
+
+REL, ABS = 1e-4, 1e-3
+
+
+def _dets(w, bins):
+    return [DetectorData(d.lat, d.lon, d.az, d.t_start, b) for d, b in zip(w.detectors, bins)]
+
+
+def _oracle_bins(w):
+    return O.inject(w.detectors, w.T, w.k_lo, w.injections, w.bank.t_ref)
+
+
+def _gpu(lib, w, bins, **opts):
+    opts.setdefault("dterms", w.dterms)
+    opts.setdefault("topk", min(w.topk, w.n_templates))
+    g = lib.FStat(0, **opts)
+    try:
+        g.load_workload(w, bins_override=bins)
+        g.compute()
+        out = dict(twoF=g.twoF(), flags=g.error_flags(), plan=g.plan(), abcd=g.abcd())
+        k = opts["topk"]
+        out["top"] = g.toplist(k) if k > 0 else None
+    finally:
+        g.close()
+    return out
+
+
+def _assert_parity(got, ref, what=""):
+    got = np.asarray(got, dtype=np.float64).ravel()
+    ref = np.asarray(ref, dtype=np.float64).ravel()
+    assert got.shape == ref.shape
+    err = np.abs(got - ref)
+    tol = REL * np.abs(ref) + ABS
+    bad = np.nonzero(err > tol)[0]
+    assert bad.size == 0, (f"{what}: {bad.size}/{ref.size} over tolerance; worst at {bad[np.argmax(err[bad])]}"
+                           f" got {got[bad[np.argmax(err[bad])]]} ref {ref[bad[np.argmax(err[bad])]]}")
+
+
+def _check_toplist(top, gpu_all, ref_all, k):
+    idx, val = top
+    # exact selection on the GPU's own values: (2F desc, index asc)
+    order = np.lexsort((np.arange(gpu_all.size), -gpu_all.astype(np.float64)))[:k]
+    np.testing.assert_array_equal(idx, order)
+    np.testing.assert_array_equal(val, gpu_all[order])
+    # against the oracle: entries clearly above the K-th oracle value must be present,
+    # and every selected entry must be within tolerance of the oracle's K-th value
+    ridx, rval = O.toplist(ref_all, k)
+    vk = rval[-1]
+    tol_k = REL * vk + ABS
+    sure = set(ridx[rval > vk + 2 * tol_k].tolist())
+    assert sure <= set(idx.tolist())
+    assert np.all(ref_all[idx] >= vk - 2 * tol_k)
+    return int(np.sum(np.isin(idx, ridx)))
+
+
+# ---------------------------------------------------------------- kernel (a): timing, antenna, A/B/C/D
+
+def test_sft_timing_and_abcd_match_oracle(lib):
+    w = config_mid()
+    g = lib.FStat(0, dterms=8, topk=10)
+    try:
+        g.load_workload(w)
+        g.compute()
+        abcd = g.abcd()
+        for s in range(w.bank.n_sky):
+            dtau, tdot, a, b = g.sft_timing(s)
+            alpha, delta = w.bank.sky[s]
+            ref = [O.sft_timing_antenna(d, w.T, alpha, delta, w.bank.t_ref) for d in w.detectors]
+            r_dtau = np.concatenate([r[0] for r in ref])
+            r_tdot = np.concatenate([r[1] for r in ref])
+            r_a = np.concatenate([r[2] for r in ref])
+            r_b = np.concatenate([r[3] for r in ref])
+            np.testing.assert_allclose(dtau, r_dtau, rtol=0, atol=1e-9)
+            np.testing.assert_allclose(tdot, r_tdot, rtol=0, atol=1e-14)
+            np.testing.assert_allclose(a, r_a, rtol=0, atol=1e-10)
+            np.testing.assert_allclose(b, r_b, rtol=0, atol=1e-10)
+            A, B, C, D = O.abcd([r[2] for r in ref], [r[3] for r in ref])
+            np.testing.assert_allclose(abcd[s], [A, B, C, D], rtol=1e-9)
+    finally:
+        g.close()
+
+
+# ---------------------------------------------------------------- kernels (b)-(d): 2F and toplist
+
+def test_config0_parity_and_recovery(lib):
+    w = config0()
+    bins = _oracle_bins(w)
+    ref = O.compute_fstat_freq_band(_dets(w, bins), w.T, w.k_lo, w.dterms, w.bank).ravel()
+    out = _gpu(lib, w, bins)
+    assert out["flags"] == 0
+    _assert_parity(out["twoF"], ref, "config0")
+    _check_toplist(out["top"], out["twoF"], ref, w.topk)
+    inj = w.injections[0]
+    assert abs(out["twoF"].max() - 4 - inj.rho ** 2) < 4 * math.sqrt(8 + 4 * inj.rho ** 2)
+
+
+@pytest.mark.parametrize("df_bins,expect", [(1.0, (2, 2)), (0.125, (8, 1)), (2.0, (1, 2)),
+                                            (0.5, (4, 2)), (0.37, (1, 1))])
+def test_mid_parity_grids(lib, df_bins, expect):
+    """Workunit-shaped data: 2 gapped detectors, band edges inside the Doppler
+    excursion (zero-filled windows), several columns and ragged tails, and
+    frequency spacings that select each thread layout (P, L)."""
+    w = config_mid(df_bins=df_bins)
+    bins = _oracle_bins(w)
+    ref = O.compute_fstat_freq_band(_dets(w, bins), w.T, w.k_lo, w.dterms, w.bank).ravel()
+    out = _gpu(lib, w, bins)
+    assert (out["plan"]["P"], out["plan"]["L"]) == expect
+    assert out["flags"] == 0
+    _assert_parity(out["twoF"], ref, f"mid df={df_bins}/T")
+    _check_toplist(out["top"], out["twoF"], ref, w.topk)
+
+
+@pytest.mark.parametrize("tile", [dict(tile_m=8), dict(tile_warps=4), dict(tile_warps=2, sft_chunk=3),
+                                  dict(tile_m=1), dict(sft_chunk=1)])
+def test_tile_overrides_keep_parity(lib, tile):
+    w = config_mid(n_f=97, n_fdot=4, n_sky=3)
+    bins = _oracle_bins(w)
+    ref = O.compute_fstat_freq_band(_dets(w, bins), w.T, w.k_lo, w.dterms, w.bank).ravel()
+    out = _gpu(lib, w, bins, **tile)
+    _assert_parity(out["twoF"], ref, str(tile))
+
+
+@pytest.mark.parametrize("D", [1, 2, 3, 5, 16])
+def test_runtime_dterms(lib, D):
+    w = config_mid(n_f=40, n_fdot=2, n_sky=2, n_bins=160)
+    w.dterms = D
+    bins = _oracle_bins(w)
+    ref = O.compute_fstat_freq_band(_dets(w, bins), w.T, w.k_lo, D, w.bank).ravel()
+    out = _gpu(lib, w, bins)
+    _assert_parity(out["twoF"], ref, f"D={D}")
+
+
+@pytest.mark.parametrize("kahan", [False, True])
+@pytest.mark.parametrize("form", ["f16", "bf16"])
+def test_precision_forms(lib, form, kahan):
+    """16-bit storage: parity with the oracle fed the same dequantised values,
+    and the error against the unquantised data stays at the format's level."""
+    w = config_mid(n_f=120, n_fdot=3, n_sky=3)
+    bins = _oracle_bins(w)
+    deq = []
+    for b in bins:
+        br, bi, sc = Q.quantize(b, form)
+        deq.append(Q.dequantize(br, bi, sc, form))
+    ref_q = O.compute_fstat_freq_band(_dets(w, deq), w.T, w.k_lo, w.dterms, w.bank).ravel()
+    ref = O.compute_fstat_freq_band(_dets(w, bins), w.T, w.k_lo, w.dterms, w.bank).ravel()
+    out = _gpu(lib, w, bins, bins_form=form, kahan=kahan)
+    _assert_parity(out["twoF"], ref_q, f"{form} vs dequantised")
+    rel = np.abs(out["twoF"] - ref) / (ref + 1.0)
+    assert np.max(rel) < (5e-3 if form == "f16" else 4e-2)
+
+
+def test_kahan_fp32_parity(lib):
+    w = config_mid(n_f=60, n_fdot=2, n_sky=2)
+    bins = _oracle_bins(w)
+    ref = O.compute_fstat_freq_band(_dets(w, bins), w.T, w.k_lo, w.dterms, w.bank).ravel()
+    out = _gpu(lib, w, bins, kahan=True)
+    _assert_parity(out["twoF"], ref, "kahan c64")
+
+
+def test_toplist_ties_take_lowest_indices(lib):
+    """Templates whose windows miss the stored band have 2F = 0 exactly; a
+    toplist longer than the nonzero set must take the zero ties in index order."""
+    w = config_mid(n_f=60, n_fdot=2, n_sky=2, n_bins=40)
+    w.bank.f0 = (w.k_lo - 5) / w.T   # first templates' windows are inside, later ones far outside
+    bins = _oracle_bins(w)
+    ref = O.compute_fstat_freq_band(_dets(w, bins), w.T, w.k_lo, w.dterms, w.bank).ravel()
+    n_zero = int(np.sum(ref == 0))
+    assert n_zero > 20
+    k = int(np.sum(ref > 0)) + 15
+    out = _gpu(lib, w, bins, topk=k)
+    assert np.sum(out["twoF"] == 0) == n_zero
+    _assert_parity(out["twoF"], ref, "ties")
+    idx, val = out["top"]
+    zeros = np.nonzero(out["twoF"] == 0)[0][:15]
+    np.testing.assert_array_equal(idx[-15:], zeros)
+    assert np.all(val[-15:] == 0)
+
+
+def test_injection_kernel_matches_oracle(lib):
+    w = config_mid(n_sft=60)
+    ref = _oracle_bins(w)
+    g = lib.FStat(0)
+    try:
+        g.load_workload(w)
+        g.inject(w.injections, w.bank.t_ref)
+        for i, d in enumerate(w.detectors):
+            got = lib.fstat_get_bins(g.ctx, i, d.n_sft, w.n_bins)
+            scale = np.max(np.abs(ref[i]))
+            assert np.max(np.abs(got - ref[i])) <= 4 * 2.0 ** -24 * scale
+    finally:
+        g.close()
+
+
+# ---------------------------------------------------------------- edge cases and errors
+
+def test_edge_single_template_single_sky(lib):
+    w = config_mid(n_f=1, n_fdot=1, n_sky=1)
+    bins = _oracle_bins(w)
+    ref = O.compute_fstat_freq_band(_dets(w, bins), w.T, w.k_lo, w.dterms, w.bank).ravel()
+    out = _gpu(lib, w, bins, topk=1)
+    _assert_parity(out["twoF"], ref, "1 template")
+    assert out["top"][0][0] == 0
+
+
+def test_edge_degenerate_sky_flags_and_zero(lib):
+    """One SFT: a, b are proportional, D = AB - C^2 = 0; 2F is set to 0 and flagged."""
+    T = T_SFT
+    det = DetectorData(DET_H["lat"], 0.0, DET_H["az"], np.array([T0]), cn_noise(3, 1, (1, 64)))
+    g = lib.FStat(0, topk=4)
+    try:
+        lib.fstat_set_sfts(g.ctx, 0, det.lat, det.lon, det.az, T, 180000, det.t_start, det.bins)
+        g.set_bank(TemplateBank(np.array([[1.0, 0.2]]), (180000 + 20) / T, 1 / T, 10, np.zeros(1), T0))
+        g.compute()
+        assert g.error_flags() & 2
+        assert np.all(g.twoF() == 0)
+    finally:
+        g.close()
+
+
+def test_errors_are_reported_not_raised_on_device(lib):
+    g = lib.FStat(0)
+    try:
+        with pytest.raises(lib.FstatError) as e:
+            g.compute()
+        assert e.value.code == lib.FSTAT_ESTATE
+        bad = cn_noise(1, 1, (4, 32))
+        bad[1, 3] = np.nan
+        with pytest.raises(lib.FstatError) as e:
+            lib.fstat_set_sfts(g.ctx, 0, 0.5, 0.0, 0.3, T_SFT, 180000, T0 + T_SFT * np.arange(4), bad)
+        assert e.value.code == lib.FSTAT_EINVAL
+        with pytest.raises(lib.FstatError) as e:
+            lib.fstat_set_sfts(g.ctx, 0, 0.5, 0.0, 0.3, -1.0, 180000, T0 + T_SFT * np.arange(4), bad * 0)
+        assert e.value.code == lib.FSTAT_EINVAL
+        ok = cn_noise(1, 1, (4, 32))
+        lib.fstat_set_sfts(g.ctx, 0, 0.5, 0.0, 0.3, T_SFT, 180000, T0 + T_SFT * np.arange(4), ok)
+        with pytest.raises(lib.FstatError) as e:   # second detector with another band
+            lib.fstat_set_sfts(g.ctx, 1, 0.5, 0.0, 0.3, T_SFT, 180001, T0 + T_SFT * np.arange(4), ok)
+        assert e.value.code == lib.FSTAT_EINVAL
+        with pytest.raises(lib.FstatError) as e:
+            lib.fstat_set_templates(g.ctx, np.zeros((1, 2)), 100.0, -1.0, 10, np.zeros(1), T0)
+        assert e.value.code == lib.FSTAT_EINVAL
+        with pytest.raises(lib.FstatError):
+            lib.fstat_create(0, dterms=0)
+    finally:
+        g.close()
+
+
+def test_device_pointer_input_matches_host(lib):
+    torch = pytest.importorskip("torch")
+    w = config_mid(n_f=50, n_fdot=2, n_sky=2)
+    host = _gpu(lib, w, None)
+    g = lib.FStat(0, topk=10)
+    try:
+        for i, d in enumerate(w.detectors):
+            dev = torch.from_numpy(d.bins.view(np.float32).reshape(d.n_sft, w.n_bins, 2).copy()).cuda()
+            lib.fstat_set_sfts(g.ctx, i, d.lat, d.lon, d.az, w.T, w.k_lo, d.t_start, dev)
+        g.set_bank(w.bank)
+        s = torch.cuda.Stream()
+        g.compute(s)
+        out = torch.empty(g.n_templates, dtype=torch.float32, device="cuda")
+        lib.fstat_get_2f(g.ctx, 0, g.n_templates, out)
+        np.testing.assert_array_equal(out.cpu().numpy(), host["twoF"])
+    finally:
+        g.close()
