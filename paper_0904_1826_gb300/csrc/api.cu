@@ -168,7 +168,7 @@ int make_plan(fstat_ctx* c, Plan& out) {
     const int D = c->opts.dterms;
     const int kahan = c->opts.kahan ? 1 : 0;
     const double dk_nom = c->df * c->T;
-    int P = 1, L = 1, M = 1;
+    int P = 1, L = 1;
     bool found = false;
     if (D == 8) {
         const int Ls[2] = {2, 1};

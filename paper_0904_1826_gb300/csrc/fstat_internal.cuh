@@ -14,7 +14,7 @@ namespace fs {
 // spherical Earth rotating at the sidereal rate; equatorial coordinates.
 constexpr double kC = 299792458.0;                  // speed of light, m/s
 constexpr double kAU = 1.495978707e11;              // orbital radius, m
-constexpr double kObliquity = 0.40909280422232897;  // 23.4393 degrees in rad
+constexpr double kObliquity = 23.4393 * 3.1415926535897932384626433832795 / 180.0;  // rad
 constexpr double kYear = 3.15581498e7;              // orbital period, s
 constexpr double kEarthR = 6.371e6;                 // Earth radius, m
 constexpr double kSidereal = 86164.0905;            // sidereal day, s
@@ -110,21 +110,12 @@ cudaError_t launch_inject(const SftState* st, int n_sft, const fstat_signal* sig
 cudaError_t launch_quantize(const float2* src, long long row, int n_sft, int n_bins, int form,
                             void* dst, float* scale, cudaStream_t s);
 
-struct DirichletVariant {
-    int D, M, L, form, kahan;
-};
-int dirichlet_variant_id(const DirichletVariant& v);   // -1 if not compiled
-cudaError_t launch_dirichlet(int variant, const DirichletParams& p, int threads, size_t smem,
-                             long long grid, cudaStream_t s);
-cudaError_t launch_dirichlet_generic(int D, int form, const DirichletParams& p, int threads,
-                                     size_t smem, long long grid, cudaStream_t s);
 
 // Toplist (radix select over the FP32 bit patterns of 2F >= 0).
 struct TopkWork {
     unsigned int* hist;        // [3][2048]
     unsigned int* state;       // [16] prefix, threshold, counts
     unsigned int* tie_count;   // [n_blocks]
-    unsigned long long* cand;  // [topk] (value bits << 32 | slot) scratch
     long long* cand_idx;       // [topk]
     float* cand_val;           // [topk]
     unsigned int* n_cand;      // [1]

@@ -23,8 +23,8 @@ def test_header_declares_the_boundary():
 
 
 def test_library_builds_and_exports_every_symbol():
-    from paper_0904_1826_gb300 import build as b
-    path = b.build()
+    import __graft_entry__ as ge
+    path = ge._build_module().build()
     lib = ctypes.CDLL(path)
     for n in _declared():
         assert hasattr(lib, n), n
