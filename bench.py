@@ -266,7 +266,7 @@ def main():
         w.bank.sky.size * 8 + w.bank.fdot.size * 8
     d2h = w.topk * 12
     e2e_ms = []
-    for it in range(args.e2e_steps + 1):
+    for it in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):
         torch.cuda.synchronize()
         barrier()
         t0 = time.perf_counter()
@@ -279,12 +279,12 @@ def main():
         barrier()
         if it > 0:
             e2e_ms.append(1e3 * (time.perf_counter() - t0))
-    e2e_ms_max = max(e2e_ms)
-    if world > 1:
+    e2e_ms_max = max(e2e_ms) if e2e_ms else float("nan")
+    if world > 1 and e2e_ms:
         t = torch.tensor([e2e_ms_max], device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         e2e_ms_max = float(t.item())
-    e2e_value = n_pairs * world / (e2e_ms_max / 1e3)
+    e2e_value = n_pairs * world / (e2e_ms_max / 1e3) if e2e_ms else None
 
     forms = {}
     if args.compare_forms and rank == 0:
