@@ -26,15 +26,15 @@ namespace {
 struct VariantRow {
     int D, M, L, kahan;
 };
-const VariantRow kVariants[] = {{8, 9, 2, 0}, {8, 8, 2, 0}, {8, 8, 1, 0}, {8, 1, 1, 0}, {8, 4, 2, 1},
-                                {8, 4, 1, 1}, {8, 1, 1, 1}, {0, 1, 1, 0}, {0, 1, 1, 1}};
+const VariantRow kVariants[] = {{8, 9, 2, 0}, {8, 7, 2, 0}, {8, 5, 2, 0}, {8, 9, 1, 0}, {8, 7, 1, 0}, {8, 1, 1, 0},
+                                {8, 5, 2, 1}, {8, 5, 1, 1}, {8, 1, 1, 1}, {0, 1, 1, 0}, {0, 1, 1, 1}};
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
 constexpr int kTimedRing = 256;
 
 struct Plan {
     int P = 1, L = 1, M = 1, W = 8, C = 8, lg_row = 1, lg_cta = 32, n_col = 1, chunks_per_col = 1;
-    int w_pairs = 0, w_pad = 0, variant = 3;
+    int w_pairs = 0, w_tab = 0, w_raw = 0, variant = 5;
     size_t smem = 0;
     long long grid = 0;
 };
@@ -183,9 +183,10 @@ int make_plan(fstat_ctx* c, Plan& out) {
     }
     std::vector<int> Ms;
     if (found) {
-        if (kahan) Ms = {4};
-        else if (L == 2) Ms = {9, 8};
-        else Ms = {8};
+        // odd M keeps neighbouring threads' pair-table rows on distinct banks
+        if (kahan) Ms = {5};
+        else if (L == 2) Ms = {9, 7, 5};
+        else Ms = {9, 7};
     } else {
         P = 1;
         L = 1;
@@ -213,12 +214,20 @@ int make_plan(fstat_ctx* c, Plan& out) {
                 const int n_col = (c->n_f + col_w - 1) / col_w;
                 // the table must hold at least one thread's full window set
                 const int w_pairs = std::max(pairs_needed(c, col_w, D), (Mv - 1) * Lv + 2 * D + 2);
-                const int w_pad = w_pairs + (w_pairs >> 4) + 1;
+                int w_tab = w_pairs;
+                if (Lv == 2) {   // two parity halves, each offset 4 mod 8 slots from the other
+                    int hf = (w_pairs + 1) / 2;
+                    hf += ((4 - hf % 8) + 8) % 8;
+                    w_tab = 2 * hf;
+                }
+                const int G = (c->opts.bins_form == FSTAT_BINS_C64) ? 2 : 4;
+                const int raw_b = (c->opts.bins_form == FSTAT_BINS_C64) ? 8 : 4;
+                const int w_raw = ((w_pairs + G + G - 1) / G) * G;
                 int C = c->opts.sft_chunk > 0 ? c->opts.sft_chunk : 8;
-                size_t smem = dirichlet_smem_bytes(C, w_pad, c->n_fdot);
+                size_t smem = dirichlet_smem(C, w_tab, w_raw, c->n_fdot, raw_b).total;
                 while (C > 1 && smem > 110 * 1024) {
                     --C;
-                    smem = dirichlet_smem_bytes(C, w_pad, c->n_fdot);
+                    smem = dirichlet_smem(C, w_tab, w_raw, c->n_fdot, raw_b).total;
                 }
                 if (smem > 220 * 1024) continue;
                 double cost = 0.0;
@@ -247,7 +256,8 @@ int make_plan(fstat_ctx* c, Plan& out) {
                     best.n_col = n_col;
                     best.chunks_per_col = chunks_max;
                     best.w_pairs = w_pairs;
-                    best.w_pad = w_pad;
+                    best.w_tab = w_tab;
+                    best.w_raw = w_raw;
                     best.variant = vid;
                     best.smem = smem;
                     best.grid = (long long)c->n_sky * n_col * chunks_max;
@@ -616,7 +626,8 @@ int fstat_compute(fstat_ctx* c, void* cuda_stream) {
     dp.chunks_per_col = pl.chunks_per_col;
     dp.n_col = pl.n_col;
     dp.w_pairs = pl.w_pairs;
-    dp.w_pad = pl.w_pad;
+    dp.w_tab = pl.w_tab;
+    dp.w_raw = pl.w_raw;
     dp.sft_chunk = pl.C;
     dp.err = c->d_err;
     CUDA_TRY(c, cudaEventRecord(c->ev_b[slot], s));

@@ -9,23 +9,28 @@
 //   frequencies j_t + P*q, q = 0..M-1, whose bin windows sit L bins apart
 //   (P * df * T ~= L), so the M windows of a thread overlap and their bins
 //   are read once from shared memory into registers.
-// Per SFT round the block stages, for every SFT of the round, the bin span
-// its templates can touch as a table of adjacent-bin pairs
-//   (X_p + X_{p+1}, X_{p+1} - X_p)
-// so that a pair of Dirichlet terms costs one reciprocal:
+// SFTs are processed in rounds of C.  While a round is being accumulated,
+// cp.async copies bring in the next round's raw bins and the constants of the
+// round after it; at the start of a round the raw bins become a table of
+// adjacent-bin pairs (X_p + X_{p+1}, X_{p+1} - X_p) so that a pair of
+// Dirichlet terms costs one reciprocal:
 //   X_p/(c+1/2) + X_{p+1}/(c-1/2) = 2 (Y Sigma + Delta) / (Y^2 - 1),  Y = 2c,
 // with c = khat - p - 1/2.  The two pairs next to the singular points
 // (kappa -> 0 and kappa -> 1) take their denominators in a cancellation-free
 // product form.
+// Pair-table layout: when windows step by L = 2 bins the table is split by
+// the parity of the pair index, so a thread's pairs are consecutive entries
+// and neighbouring threads (M odd) sit an odd number of 16-byte slots apart:
+// all loads are base + constant and free of bank conflicts.
 #pragma once
 #include "fstat_internal.cuh"
 
 namespace fs {
 
-constexpr int kPadShift = 4;              // one padding entry per 16 pair entries
 constexpr float kKapMin = 5.9604645e-8f;  // 2^-24: below this the kernel is at its limit
 constexpr float kKapMax = 0.99999994f;    // 1 - 2^-24
 constexpr float kPhaseToRad = 1.4629180792671596e-09f;  // 2 pi / 2^32
+constexpr int kMaxThreads = 320;
 
 __device__ __forceinline__ float rcp_approx(float x) {
     float r;
@@ -33,84 +38,86 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return r;
 }
 
-template <int FORM>
-__device__ __forceinline__ float2 load_bin(const void* __restrict__ bins, long long off) {
-    if (FORM == FSTAT_BINS_C64) {
-        return __ldg(reinterpret_cast<const float2*>(bins) + off);
-    } else if (FORM == FSTAT_BINS_F16) {
-        const __half2 h = reinterpret_cast<const __half2*>(bins)[off];
-        return __half22float2(h);
-    } else {
-        const __nv_bfloat162 h = reinterpret_cast<const __nv_bfloat162*>(bins)[off];
-        return __bfloat1622float2(h);
-    }
+__device__ __forceinline__ unsigned int smem_u32(const void* p) {
+    return (unsigned int)__cvta_generic_to_shared(p);
 }
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
-__device__ __forceinline__ int pad_idx(int i) { return i + (i >> kPadShift); }
+// Raw storage element of one complex bin, and bins per 16-byte copy.
+template <int FORM>
+struct RawT;
+template <>
+struct RawT<FSTAT_BINS_C64> {
+    using T = float2;
+    static constexpr int G = 2;
+    static __device__ __forceinline__ float2 f2(T x) { return x; }
+};
+template <>
+struct RawT<FSTAT_BINS_F16> {
+    using T = __half2;
+    static constexpr int G = 4;
+    static __device__ __forceinline__ float2 f2(T x) { return __half22float2(x); }
+};
+template <>
+struct RawT<FSTAT_BINS_BF16> {
+    using T = __nv_bfloat162;
+    static constexpr int G = 4;
+    static __device__ __forceinline__ float2 f2(T x) { return __bfloat1622float2(x); }
+};
+
+// Position of pair index i in the table row (split by parity for L = 2).
+template <int L>
+__device__ __forceinline__ int tab_pos(int i, int half) {
+    return (L == 2) ? ((i & 1) * half + (i >> 1)) : i;
+}
 
 // Denominator of pair gi (bins k0-D+1+2gi, k0-D+2+2gi) times 4: Y^2 - 1 with
 // Y = 2 kappa + 2D - 3 - 4 gi, in product form where it can vanish.
-template <int D>
-__device__ __forceinline__ float pair_den(float Y, float kap, int gi) {
-    if ((D & 1) == 0 && gi == D / 2 - 1) {        // offsets -1, 0: 4 kappa (kappa + 1)
+__device__ __forceinline__ float pair_den(int D, float Y, float kap, int gi) {
+    if ((D & 1) == 0 && gi == D / 2 - 1) {          // offsets -1, 0: 4 kappa (kappa + 1)
         const float k4 = 4.0f * kap;
         return fmaf(k4, kap, k4);
-    } else if ((D & 1) == 0 && gi == D / 2) {     // offsets 1, 2: 4 (kappa-1)(kappa-2)
+    } else if ((D & 1) == 0 && gi == D / 2) {       // offsets 1, 2: 4 (kappa-1)(kappa-2)
         const float u = kap - 1.0f;
         const float u4 = 4.0f * u;
         return fmaf(u4, u, -u4);
-    } else if ((D & 1) == 1 && gi == (D - 1) / 2) {   // offsets 0, 1: 4 kappa (kappa - 1)
+    } else if ((D & 1) == 1 && gi == (D - 1) / 2) { // offsets 0, 1: 4 kappa (kappa - 1)
         const float k4 = 4.0f * kap;
         return fmaf(k4, kap, -k4);
     }
     return fmaf(Y, Y, -1.0f);
 }
 
-__device__ __forceinline__ float pair_den_rt(int D, float Y, float kap, int gi) {
-    if ((D & 1) == 0 && gi == D / 2 - 1) {
-        const float k4 = 4.0f * kap;
-        return fmaf(k4, kap, k4);
-    } else if ((D & 1) == 0 && gi == D / 2) {
-        const float u = kap - 1.0f;
-        const float u4 = 4.0f * u;
-        return fmaf(u4, u, -u4);
-    } else if ((D & 1) == 1 && gi == (D - 1) / 2) {
-        const float k4 = 4.0f * kap;
-        return fmaf(k4, kap, -k4);
-    }
-    return fmaf(Y, Y, -1.0f);
-}
-
-// Sum over the 2D window of one template: Q = sum_pairs (Y Sigma + Delta) / (Y^2 - 1)
-// (the factor 2 of the pair form and 1/pi are folded into a, b).
-template <int D>
-__device__ __forceinline__ void window_sum(const float4* __restrict__ row, int base, float kap,
-                                           float& Qre, float& Qim) {
+// Window sum of one template, Q = sum_pairs (Y Sigma + Delta) / (Y^2 - 1)
+// (the pair form's factor 2 and the 1/pi of the kernel are folded into a, b);
+// consecutive pairs of the window are STRIDE table entries apart.  The
+// complex numerator and accumulator use packed FP32 (f32x2) operations.
+template <int DV, int STRIDE>
+__device__ __forceinline__ float2 window_sum(const float4* __restrict__ pp, float kap, int d_rt) {
+    const int D = DV ? DV : d_rt;
     const float y0 = fmaf(2.0f, kap, (float)(2 * D - 3));
-    Qre = 0.f;
-    Qim = 0.f;
+    float2 Q = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int gi = 0; gi < D; ++gi) {
-        const float4 e = row[pad_idx(base + 2 * gi)];
+    for (int gi = 0; gi < (DV ? DV : 64); ++gi) {
+        if (!DV && gi >= D) break;
+        const float4 e = pp[gi * STRIDE];
         const float Y = y0 - (float)(4 * gi);
-        const float r = rcp_approx(pair_den<D>(Y, kap, gi));
-        Qre = fmaf(fmaf(Y, e.x, e.z), r, Qre);
-        Qim = fmaf(fmaf(Y, e.y, e.w), r, Qim);
+        const float r = rcp_approx(pair_den(D, Y, kap, gi));
+        const float2 S = __ffma2_rn(make_float2(Y, Y), make_float2(e.x, e.y), make_float2(e.z, e.w));
+        Q = __ffma2_rn(S, make_float2(r, r), Q);
     }
-}
-
-__device__ __forceinline__ void window_sum_rt(int D, const float4* __restrict__ row, int base, float kap,
-                                              float& Qre, float& Qim) {
-    const float y0 = fmaf(2.0f, kap, (float)(2 * D - 3));
-    Qre = 0.f;
-    Qim = 0.f;
-    for (int gi = 0; gi < D; ++gi) {
-        const float4 e = row[pad_idx(base + 2 * gi)];
-        const float Y = y0 - (float)(4 * gi);
-        const float r = rcp_approx(pair_den_rt(D, Y, kap, gi));
-        Qre = fmaf(fmaf(Y, e.x, e.z), r, Qre);
-        Qim = fmaf(fmaf(Y, e.y, e.w), r, Qim);
-    }
+    return Q;
 }
 
 // Fixed-point fraction (2^-32 units) to float in [0, 1), truncated to 23 bits.
@@ -136,10 +143,6 @@ __device__ __forceinline__ float sinpi_unit(float x) {
     return p * t;
 }
 
-struct Accum {
-    float re, im;
-};
-
 // Kahan step: t += x with running compensation c.
 __device__ __forceinline__ void kahan_add(float& t, float& c, float x) {
     const float y = __fsub_rn(x, c);
@@ -148,22 +151,33 @@ __device__ __forceinline__ void kahan_add(float& t, float& c, float x) {
     t = s;
 }
 
-constexpr int kMaxThreads = 320;
+// z = tw * sk * Q accumulated into Fa, Fb with weights a, b (packed pairs).
+__device__ __forceinline__ void accumulate(float tw_re, float tw_im, float sk, float2 Q, float2 a2, float2 b2,
+                                           float2& fa, float2& fb) {
+    const float gre = tw_re * sk, gim = tw_im * sk;
+    const float2 z = make_float2(fmaf(gre, Q.x, -gim * Q.y), fmaf(gre, Q.y, gim * Q.x));
+    fa = __ffma2_rn(a2, z, fa);
+    fb = __ffma2_rn(b2, z, fb);
+}
 
-// DV = D (compile time) or 0 (D taken from the runtime argument).
+// DV = D (compile time) or 0 (D taken from the runtime argument, M = 1).
 template <int DV, int M, int L, int FORM, bool KAHAN>
-__global__ void __launch_bounds__(kMaxThreads, 2)
-dirichlet_kernel(const DirichletParams p, const int d_rt) {
-    const int THREADS = blockDim.x;
-    constexpr bool RT = (DV == 0);
-    const int D = RT ? d_rt : DV;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+__global__ void __launch_bounds__(kMaxThreads, 2) dirichlet_kernel(const DirichletParams p, const int d_rt) {
+    using RT = RawT<FORM>;
+    using Raw = typename RT::T;
+    constexpr int G = RT::G;
+    constexpr int STRIDE = (L == 2) ? 1 : 2;
+    const int D = DV ? DV : d_rt;
+    const int NT = blockDim.x;
     const int C = p.sft_chunk;
-    float4* s_pairs = reinterpret_cast<float4*>(smem_raw);
-    SkySftMeta* s_meta = reinterpret_cast<SkySftMeta*>(s_pairs + (size_t)C * p.w_pad);
-    long long* s_kh0 = reinterpret_cast<long long*>(s_meta + C);
-    unsigned int* s_ph0 = reinterpret_cast<unsigned int*>(s_kh0 + (size_t)C * p.n_fdot);
-    int* s_lo = reinterpret_cast<int*>(s_ph0 + (size_t)C * p.n_fdot);
+    extern __shared__ __align__(16) unsigned char smem[];
+    const DirSmem lay = dirichlet_smem(C, p.w_tab, p.w_raw, p.n_fdot, (int)sizeof(Raw));
+    float4* s_tab = reinterpret_cast<float4*>(smem + lay.pairs);            // [C][w_tab]
+    Raw* s_raw = reinterpret_cast<Raw*>(smem + lay.raw);                    // [2][C][w_raw]
+    SkySftMeta* s_meta = reinterpret_cast<SkySftMeta*>(smem + lay.meta);    // [3][C]
+    long long* s_kh0 = reinterpret_cast<long long*>(smem + lay.kh0);        // [3][C][n_fdot]
+    unsigned int* s_ph0 = reinterpret_cast<unsigned int*>(smem + lay.ph0);  // [3][C][n_fdot]
+    int* s_lo = reinterpret_cast<int*>(smem + lay.lo);                      // [2][C][2]: window base, raw start
 
     long long bid = blockIdx.x;
     const int chunk = (int)(bid % p.chunks_per_col);
@@ -194,93 +208,124 @@ dirichlet_kernel(const DirichletParams p, const int d_rt) {
     const int j_t = j_col0 + g * PM + r;
     const int row_i = drow - d_lo;
     const bool warp_live = __any_sync(0xffffffffu, active);
+    const int half = p.w_tab >> 1;
 
-    Accum fa[M], fb[M];
-    Accum ca[M], cb[M];   // Kahan compensation (KAHAN only)
-    Accum ta[M], tb[M];   // Kahan totals (KAHAN only)
-#pragma unroll
-    for (int q = 0; q < M; ++q) {
-        fa[q] = {0.f, 0.f};
-        fb[q] = {0.f, 0.f};
-        ca[q] = {0.f, 0.f};
-        cb[q] = {0.f, 0.f};
-        ta[q] = {0.f, 0.f};
-        tb[q] = {0.f, 0.f};
-    }
     const size_t meta0 = (size_t)sky * p.n_sft;
     const size_t base0 = (size_t)sky * p.n_fdot * p.n_sft;
+    const int n_rounds = (p.n_sft + C - 1) / C;
+
+    // ---- staging helpers -------------------------------------------------
+    auto issue_consts = [&](int rd) {
+        const int a0 = rd * C, slot = rd % 3;
+        const int nc = min(C, p.n_sft - a0);
+        const char* msrc = reinterpret_cast<const char*>(p.meta + meta0 + a0);
+        char* mdst = reinterpret_cast<char*>(s_meta + slot * C);
+        for (int t = threadIdx.x; t < nc * 3; t += NT) cp_async16(mdst + 16 * t, msrc + 16 * t, 16);
+        for (int t = threadIdx.x; t < nc * n_rows; t += NT) {
+            const int c = t / n_rows, rr = t - c * n_rows;
+            const size_t o = base0 + (size_t)(d_lo + rr) * p.n_sft + a0 + c;
+            cp_async8(s_kh0 + (slot * C + c) * p.n_fdot + rr, p.kh0 + o);
+            cp_async4(s_ph0 + (slot * C + c) * p.n_fdot + rr, p.ph0 + o);
+        }
+    };
+    auto compute_lo = [&](int rd) {
+        const int a0 = rd * C, cslot = rd % 3, lslot = rd & 1;
+        const int nc = min(C, p.n_sft - a0);
+        for (int c = threadIdx.x; c < nc; c += NT) {
+            const SkySftMeta& m = s_meta[cslot * C + c];
+            const long long kb = m.khmin + (long long)j_col0 * m.dk;
+            const int lo_rel = (int)((kb >> 32) - p.k_lo) - (D - 1);
+            const int raw_rel = (lo_rel >= 0) ? (lo_rel / G) * G : -((-lo_rel + G - 1) / G) * G;
+            s_lo[(lslot * C + c) * 2] = lo_rel;
+            s_lo[(lslot * C + c) * 2 + 1] = raw_rel;
+        }
+    };
+    auto issue_raw = [&](int rd) {
+        const int a0 = rd * C, slot = rd & 1;
+        const int nc = min(C, p.n_sft - a0);
+        const int gpr = p.w_raw / G;
+        const Raw* bins = reinterpret_cast<const Raw*>(p.bins);
+        for (int t = threadIdx.x; t < nc * gpr; t += NT) {
+            const int c = t / gpr, gi = t - c * gpr;
+            const long long x = (long long)s_lo[(slot * C + c) * 2 + 1] + (long long)gi * G;
+            const bool in = (x >= 0) && (x < p.row);
+            const Raw* src = bins + (size_t)(a0 + c) * p.row + (in ? x : 0);
+            cp_async16(s_raw + ((size_t)slot * C + c) * p.w_raw + gi * G, src, in ? 16 : 0);
+        }
+    };
+    auto build_pairs = [&](int rd) {
+        const int a0 = rd * C, slot = rd & 1;
+        const int nc = min(C, p.n_sft - a0);
+        for (int e = threadIdx.x; e < nc * p.w_pairs; e += NT) {
+            const int c = e / p.w_pairs, i = e - c * p.w_pairs;
+            const int ri = s_lo[(slot * C + c) * 2] - s_lo[(slot * C + c) * 2 + 1] + i;
+            const Raw* rw = s_raw + ((size_t)slot * C + c) * p.w_raw;
+            const float2 x0 = RT::f2(rw[ri]), x1 = RT::f2(rw[ri + 1]);
+            s_tab[(size_t)c * p.w_tab + tab_pos<L>(i, half)] =
+                make_float4(x0.x + x1.x, x0.y + x1.y, x1.x - x0.x, x1.y - x0.y);
+        }
+    };
+
+    float2 fa[M], fb[M];
+    float2 ca[M], cb[M];   // Kahan compensation (KAHAN only)
+    float2 ta[M], tb[M];   // Kahan totals (KAHAN only)
+#pragma unroll
+    for (int q = 0; q < M; ++q) {
+        fa[q] = fb[q] = ca[q] = cb[q] = ta[q] = tb[q] = make_float2(0.f, 0.f);
+    }
     int bad = 0;
 
-    for (int a0 = 0; a0 < p.n_sft; a0 += C) {
+    // ---- prologue: constants of rounds 0 and 1, raw bins of round 0
+    issue_consts(0);
+    if (n_rounds > 1) issue_consts(1);
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncthreads();
+    compute_lo(0);
+    __syncthreads();
+    issue_raw(0);
+    cp_async_commit();
+
+    for (int rd = 0; rd < n_rounds; ++rd) {
+        const int a0 = rd * C;
         const int nc = min(C, p.n_sft - a0);
-        __syncthreads();   // the previous round's readers are done
-        // ---- stage per-SFT constants and the window base of this block
-        for (int i = threadIdx.x; i < nc; i += THREADS) {
-            const SkySftMeta m = p.meta[meta0 + a0 + i];
-            s_meta[i] = m;
-            // lowest window start over the block's spindown rows (any order)
-            long long kmin = p.kh0[base0 + (size_t)d_lo * p.n_sft + a0 + i];
-            for (int rr = d_lo + 1; rr <= d_hi; ++rr) {
-                const long long k = p.kh0[base0 + (size_t)rr * p.n_sft + a0 + i];
-                kmin = k < kmin ? k : kmin;
-            }
-            s_lo[i] = (int)((kmin + (long long)j_col0 * m.dk) >> 32) - (D - 1);
-        }
-        for (int i = threadIdx.x; i < nc * n_rows; i += THREADS) {
-            const int c = i / n_rows, rr = i - c * n_rows;
-            const size_t o = base0 + (size_t)(d_lo + rr) * p.n_sft + a0 + c;
-            s_kh0[c * p.n_fdot + rr] = p.kh0[o];
-            s_ph0[c * p.n_fdot + rr] = p.ph0[o];
-        }
-        __syncthreads();
-        // ---- pair table of the bins this block can touch (zero outside the band)
-        for (int e = threadIdx.x; e < nc * p.w_pairs; e += THREADS) {
-            const int c = e / p.w_pairs;
-            const int i = e - c * p.w_pairs;
-            const long long off = (long long)s_lo[c] + i - p.k_lo;
-            const long long rowoff = (long long)(a0 + c) * p.row;
-            float2 x0 = make_float2(0.f, 0.f), x1 = make_float2(0.f, 0.f);
-            if (off >= 0 && off < p.n_bins) x0 = load_bin<FORM>(p.bins, rowoff + off);
-            if (off + 1 >= 0 && off + 1 < p.n_bins) x1 = load_bin<FORM>(p.bins, rowoff + off + 1);
-            s_pairs[(size_t)c * p.w_pad + pad_idx(i)] = make_float4(x0.x + x1.x, x0.y + x1.y, x1.x - x0.x, x1.y - x0.y);
-        }
-        __syncthreads();
-        // ---- accumulate this round's SFTs (warps without templates only stage)
+        const int cslot = rd % 3, lslot = rd & 1;
+        cp_async_wait_all();
+        __syncthreads();   // raw(rd), consts(rd+1) visible; everyone done with round rd-1
+        build_pairs(rd);
+        if (rd + 1 < n_rounds) compute_lo(rd + 1);
+        __syncthreads();   // pair table and next window bases ready
+        if (rd + 1 < n_rounds) issue_raw(rd + 1);
+        if (rd + 2 < n_rounds) issue_consts(rd + 2);
+        cp_async_commit();
+
         for (int c = 0; c < (warp_live ? nc : 0); ++c) {
-            const SkySftMeta m = s_meta[c];
-            const long long kh = s_kh0[c * p.n_fdot + row_i] + (long long)j_t * m.dk;
+            const SkySftMeta m = s_meta[cslot * C + c];
+            const long long kh = s_kh0[(cslot * C + c) * p.n_fdot + row_i] + (long long)j_t * m.dk;
             const int k0 = (int)(kh >> 32);
-            const unsigned int ph = s_ph0[c * p.n_fdot + row_i] + (unsigned int)j_t * m.dphi + ((unsigned int)k0 << 31);
-            const float4* prow = s_pairs + (size_t)c * p.w_pad;
-            const int lo = s_lo[c];
+            const unsigned int ph0 = s_ph0[(cslot * C + c) * p.n_fdot + row_i];
+            const int lo_rel = s_lo[(lslot * C + c) * 2];
+            const int b = (k0 - (int)p.k_lo) - (D - 1) - lo_rel;   // first pair of template 0
+            const float4* tab = s_tab + (size_t)c * p.w_tab;
+            const float2 a2 = make_float2(m.a, m.a), b2 = make_float2(m.b, m.b);
             const bool fast = ((int)((kh + m.span) >> 32) == k0 + (M - 1) * L);
-            float sn, cs;
-            __sincosf((float)(int)ph * kPhaseToRad, &sn, &cs);
-            float tw_re = cs, tw_im = -sn;
             if (fast) {
-                int base = k0 - (D - 1) - lo;
-                const int last = base + (M - 1) * L + 2 * (D - 1);
-                if (base < 0 || last >= p.w_pairs) {
+                int bb = b;
+                if (bb < 0 || bb + (M - 1) * L + 2 * (D - 1) >= p.w_pairs) {
                     bad = 1;
-                    base = max(0, min(base, p.w_pairs - 1 - (M - 1) * L - 2 * (D - 1)));
+                    bb = max(0, min(bb, p.w_pairs - 1 - (M - 1) * L - 2 * (D - 1)));
                 }
+                const float4* pp = tab + tab_pos<L>(bb, half);
+                const unsigned int ph = ph0 + (unsigned int)j_t * m.dphi + ((unsigned int)k0 << 31);
+                float sn, cs;
+                __sincosf((float)(int)ph * kPhaseToRad, &sn, &cs);
+                float tw_re = cs, tw_im = -sn;
                 const float kap0 = frac_to_float((unsigned int)kh);
 #pragma unroll
                 for (int q = 0; q < M; ++q) {
                     const float kap = clamp_kappa(fmaf((float)q, m.eps, kap0));
-                    float Qre, Qim;
-                    if (RT)
-                        window_sum_rt(D, prow, base + q * L, kap, Qre, Qim);
-                    else
-                        window_sum<(RT ? 8 : DV)>(prow, base + q * L, kap, Qre, Qim);
-                    const float sk = sinpi_unit(kap);
-                    const float gre = tw_re * sk, gim = tw_im * sk;
-                    const float zre = fmaf(gre, Qre, -gim * Qim);
-                    const float zim = fmaf(gre, Qim, gim * Qre);
-                    fa[q].re = fmaf(m.a, zre, fa[q].re);
-                    fa[q].im = fmaf(m.a, zim, fa[q].im);
-                    fb[q].re = fmaf(m.b, zre, fb[q].re);
-                    fb[q].im = fmaf(m.b, zim, fb[q].im);
+                    const float2 Q = window_sum<DV, STRIDE>(pp + q, kap, d_rt);
+                    accumulate(tw_re, tw_im, sinpi_unit(kap), Q, a2, b2, fa[q], fb[q]);
                     if (q + 1 < M) {
                         const float t = fmaf(tw_re, m.rot_re, -tw_im * m.rot_im);
                         tw_im = fmaf(tw_re, m.rot_im, tw_im * m.rot_re);
@@ -289,35 +334,21 @@ dirichlet_kernel(const DirichletParams p, const int d_rt) {
                 }
             } else {
                 const long long pdk = (long long)p.P * m.dk;
-                const unsigned int pdphi = (unsigned int)p.P * m.dphi;
 #pragma unroll
                 for (int q = 0; q < M; ++q) {
                     const long long khq = kh + (long long)q * pdk;
                     const int k0q = (int)(khq >> 32);
                     const float kap = clamp_kappa(frac_to_float((unsigned int)khq));
-                    const unsigned int phq = s_ph0[c * p.n_fdot + row_i] + (unsigned int)(j_t + q * p.P) * m.dphi +
-                                             ((unsigned int)k0q << 31);
-                    (void)pdphi;
+                    const unsigned int phq = ph0 + (unsigned int)(j_t + q * p.P) * m.dphi + ((unsigned int)k0q << 31);
                     float s2, c2;
                     __sincosf((float)(int)phq * kPhaseToRad, &s2, &c2);
-                    int base = k0q - (D - 1) - lo;
-                    if (base < 0 || base + 2 * (D - 1) >= p.w_pairs) {
+                    int bq = (k0q - (int)p.k_lo) - (D - 1) - lo_rel;
+                    if (bq < 0 || bq + 2 * (D - 1) >= p.w_pairs) {
                         bad = 1;
-                        base = max(0, min(base, p.w_pairs - 1 - 2 * (D - 1)));
+                        bq = max(0, min(bq, p.w_pairs - 1 - 2 * (D - 1)));
                     }
-                    float Qre, Qim;
-                    if (RT)
-                        window_sum_rt(D, prow, base, kap, Qre, Qim);
-                    else
-                        window_sum<(RT ? 8 : DV)>(prow, base, kap, Qre, Qim);
-                    const float sk = sinpi_unit(kap);
-                    const float gre = c2 * sk, gim = -s2 * sk;
-                    const float zre = fmaf(gre, Qre, -gim * Qim);
-                    const float zim = fmaf(gre, Qim, gim * Qre);
-                    fa[q].re = fmaf(m.a, zre, fa[q].re);
-                    fa[q].im = fmaf(m.a, zim, fa[q].im);
-                    fb[q].re = fmaf(m.b, zre, fb[q].re);
-                    fb[q].im = fmaf(m.b, zim, fb[q].im);
+                    const float2 Q = window_sum<DV, STRIDE>(tab + tab_pos<L>(bq, half), kap, d_rt);
+                    accumulate(c2, -s2, sinpi_unit(kap), Q, a2, b2, fa[q], fb[q]);
                 }
             }
         }
@@ -325,12 +356,11 @@ dirichlet_kernel(const DirichletParams p, const int d_rt) {
             // compensated addition of this round's partial sums into the totals
 #pragma unroll
             for (int q = 0; q < M; ++q) {
-                kahan_add(ta[q].re, ca[q].re, fa[q].re);
-                kahan_add(ta[q].im, ca[q].im, fa[q].im);
-                kahan_add(tb[q].re, cb[q].re, fb[q].re);
-                kahan_add(tb[q].im, cb[q].im, fb[q].im);
-                fa[q] = {0.f, 0.f};
-                fb[q] = {0.f, 0.f};
+                kahan_add(ta[q].x, ca[q].x, fa[q].x);
+                kahan_add(ta[q].y, ca[q].y, fa[q].y);
+                kahan_add(tb[q].x, cb[q].x, fb[q].x);
+                kahan_add(tb[q].y, cb[q].y, fb[q].y);
+                fa[q] = fb[q] = make_float2(0.f, 0.f);
             }
         }
     }
@@ -344,40 +374,40 @@ dirichlet_kernel(const DirichletParams p, const int d_rt) {
     for (int q = 0; q < M; ++q) {
         const int j = j_t + q * p.P;
         if (j < j_end) {
-            const Accum A_ = KAHAN ? ta[q] : fa[q];
-            const Accum B_ = KAHAN ? tb[q] : fb[q];
-            float v = cm.x * fmaf(A_.re, A_.re, A_.im * A_.im) + cm.y * fmaf(B_.re, B_.re, B_.im * B_.im) +
-                      cm.z * fmaf(A_.re, B_.re, A_.im * B_.im);
+            const float2 A_ = KAHAN ? ta[q] : fa[q];
+            const float2 B_ = KAHAN ? tb[q] : fb[q];
+            const float v = cm.x * fmaf(A_.x, A_.x, A_.y * A_.y) + cm.y * fmaf(B_.x, B_.x, B_.y * B_.y) +
+                            cm.z * fmaf(A_.x, B_.x, A_.y * B_.y);
             out[j] = fmaxf(v, 0.0f);
         }
     }
 }
 
-// Compiled variants: (D, M, L, KAHAN); D = 0 takes D at run time.
+// Compiled variants: (ID, D, M, L, KAHAN); D = 0 takes D at run time.
 #define FS_DIRICHLET_VARIANTS(X) \
     X(0, 8, 9, 2, false)          \
-    X(1, 8, 8, 2, false)          \
-    X(2, 8, 8, 1, false)          \
-    X(3, 8, 1, 1, false)          \
-    X(4, 8, 4, 2, true)           \
-    X(5, 8, 4, 1, true)           \
-    X(6, 8, 1, 1, true)           \
-    X(7, 0, 1, 1, false)          \
-    X(8, 0, 1, 1, true)
-
-constexpr int kNumDirichletVariants = 9;
+    X(1, 8, 7, 2, false)          \
+    X(2, 8, 5, 2, false)          \
+    X(3, 8, 9, 1, false)          \
+    X(4, 8, 7, 1, false)          \
+    X(5, 8, 1, 1, false)          \
+    X(6, 8, 5, 2, true)           \
+    X(7, 8, 5, 1, true)           \
+    X(8, 8, 1, 1, true)           \
+    X(9, 0, 1, 1, false)          \
+    X(10, 0, 1, 1, true)
 
 template <int FORM>
 cudaError_t launch_dirichlet_form(int v, const DirichletParams& p, int d_rt, int threads, size_t smem,
                                   long long grid, cudaStream_t s) {
     switch (v) {
-#define FS_CASE(ID, D_, M_, L_, K_)                                                                  \
-    case ID: {                                                                                       \
-        auto fn = dirichlet_kernel<D_, M_, L_, FORM, K_>;                                            \
+#define FS_CASE(ID, D_, M_, L_, K_)                                                                       \
+    case ID: {                                                                                            \
+        auto fn = dirichlet_kernel<D_, M_, L_, FORM, K_>;                                                 \
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
-        if (e != cudaSuccess) return e;                                                              \
-        fn<<<(unsigned)grid, threads, smem, s>>>(p, d_rt);                                           \
-        return cudaGetLastError();                                                                   \
+        if (e != cudaSuccess) return e;                                                                   \
+        fn<<<(unsigned)grid, threads, smem, s>>>(p, d_rt);                                                \
+        return cudaGetLastError();                                                                        \
     }
         FS_DIRICHLET_VARIANTS(FS_CASE)
 #undef FS_CASE

@@ -172,17 +172,19 @@ __global__ void __launch_bounds__(kTimingBlock) timing_kernel(const TimingParams
         const double sc = (double)p.scale[i] * kconst;
         m.a = (float)(a * sc);
         m.b = (float)(b * sc);
-        m.pad0 = 0.f;
-        m.pad1 = 0.f;
-        p.meta[(size_t)sky * p.n_sft + i] = m;
+        long long khmin = 0x7fffffffffffffffLL;
         for (int d = 0; d < p.n_fdot; ++d) {
             const double fd = p.fdot[d];
             const double khat0 = (p.f0 + fd * dtau) * tdot * p.T;
             const double cyc0 = p.f0 * dtau + 0.5 * fd * dtau * dtau;
             const size_t o = ((size_t)sky * p.n_fdot + d) * p.n_sft + i;
-            p.kh0[o] = bin_fx(khat0);
+            const long long kfx = bin_fx(khat0);
+            p.kh0[o] = kfx;
             p.ph0[o] = frac_fx32(cyc0);
+            khmin = kfx < khmin ? kfx : khmin;
         }
+        m.khmin = khmin;
+        p.meta[(size_t)sky * p.n_sft + i] = m;
     }
     const double A = block_sum<kTimingBlock>(sAA, red[0]);
     const double B = block_sum<kTimingBlock>(sBB, red[1]);

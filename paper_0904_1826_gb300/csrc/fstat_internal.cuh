@@ -37,7 +37,8 @@ struct SftState {
 // span = (M-1) * P * dk checks that a thread's M templates (stride P) keep
 // their bin windows L bins apart; eps = P*dk - L in bins (float drift);
 // rot = e^{-2 pi i (P*dphi + L/2)} steps the twiddle between them; a, b are the
-// antenna weights times the storage scale times the kernel constant 2/pi.
+// antenna weights times the storage scale times the kernel constant 2/pi;
+// khmin = min over the spindowns of khat0 (lower bound of every window base).
 struct __align__(16) SkySftMeta {
     long long dk;
     long long span;
@@ -45,7 +46,7 @@ struct __align__(16) SkySftMeta {
     float eps;
     float rot_re, rot_im;
     float a, b;
-    float pad0, pad1;
+    long long khmin;
 };
 static_assert(sizeof(SkySftMeta) == 48, "SkySftMeta layout");
 
@@ -67,19 +68,29 @@ struct DirichletParams {
     int chunks_per_col;        // blocks per column
     int n_col;                 // columns per sky
     int w_pairs;               // staged pair entries per SFT
-    int w_pad;                 // padded row length of the pair table
+    int w_tab;                 // pair-table row length (entries, >= w_pairs)
+    int w_raw;                 // raw staging row length (bins, multiple of 4)
     int sft_chunk;             // SFTs per staging round
     int* err;                  // device error flags
 };
 
-// Shared-memory footprint of the Dirichlet kernel for a plan.
-inline size_t dirichlet_smem_bytes(int sft_chunk, int w_pad, int n_fdot) {
-    size_t b = (size_t)sft_chunk * w_pad * 16;          // pair table
-    b += (size_t)sft_chunk * sizeof(SkySftMeta);        // meta
-    b += (size_t)sft_chunk * n_fdot * 8;                // kh0 rows
-    b += (size_t)sft_chunk * n_fdot * 4;                // ph0 rows
-    b += (size_t)sft_chunk * 4;                         // window base
-    return (b + 15) & ~(size_t)15;
+// Shared-memory layout of the Dirichlet kernel (offsets in bytes).
+struct DirSmem {
+    size_t pairs, raw, meta, kh0, ph0, lo, total;
+};
+__host__ __device__ inline size_t smem_align16(size_t x) { return (x + 15) & ~(size_t)15; }
+__host__ __device__ inline DirSmem dirichlet_smem(int sft_chunk, int w_tab, int w_raw, int n_fdot,
+                                                  int raw_elem_bytes) {
+    DirSmem m;
+    const size_t C = (size_t)sft_chunk;
+    m.pairs = 0;                                                           // float4 pair table [C][w_tab]
+    m.raw = smem_align16(m.pairs + C * w_tab * 16);                        // [2][C][w_raw] raw bins
+    m.meta = smem_align16(m.raw + 2 * C * w_raw * raw_elem_bytes);         // [3][C] constants
+    m.kh0 = smem_align16(m.meta + 3 * C * sizeof(SkySftMeta));             // [3][C][n_fdot]
+    m.ph0 = smem_align16(m.kh0 + 3 * C * n_fdot * 8);                      // [3][C][n_fdot]
+    m.lo = smem_align16(m.ph0 + 3 * C * n_fdot * 4);                       // [2][C][2]
+    m.total = smem_align16(m.lo + 2 * C * 8);
+    return m;
 }
 
 struct TimingParams {
