@@ -127,7 +127,7 @@ def test_mid_parity_grids(lib, df_bins, expect):
     _check_toplist(out["top"], out["twoF"], ref, w.topk)
 
 
-@pytest.mark.parametrize("tile", [dict(tile_m=8), dict(tile_warps=4), dict(tile_warps=2, sft_chunk=3),
+@pytest.mark.parametrize("tile", [dict(tile_m=7), dict(tile_m=5, tile_warps=4), dict(tile_warps=2, sft_chunk=3),
                                   dict(tile_m=1), dict(sft_chunk=1)])
 def test_tile_overrides_keep_parity(lib, tile):
     w = config_mid(n_f=97, n_fdot=4, n_sky=3)
