@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--compare-forms", action="store_true", help="also time the other storage forms")
+    ap.add_argument("--tile-m", type=int, default=0, help="templates per thread (0 = planner)")
+    ap.add_argument("--tile-warps", type=int, default=0, help="warps per block (0 = planner)")
+    ap.add_argument("--sft-chunk", type=int, default=0, help="SFTs per staging round (0 = planner)")
     return ap.parse_args()
 
 
@@ -196,7 +199,8 @@ def main():
     stream = torch.cuda.Stream()
 
     def make(form):
-        g = fs.FStat(local_rank, dterms=w.dterms, topk=w.topk, bins_form=form)
+        g = fs.FStat(local_rank, dterms=w.dterms, topk=w.topk, bins_form=form, tile_m=args.tile_m,
+                     tile_warps=args.tile_warps, sft_chunk=args.sft_chunk)
         g.load_workload(w)
         g.inject(w.injections, w.bank.t_ref)
         return g

@@ -241,7 +241,10 @@ int make_plan(fstat_ctx* c, Plan& out) {
                     for (int k = 0; k < chunks; ++k) {
                         const long long lgs = std::min<long long>(lg_cta, LG - (long long)k * lg_cta);
                         const long long warps = (lgs + 31) / 32 * Pv;
-                        cost += (double)warps * 32.0 * Mv * 85.0 + (double)w_pairs * 14.0 + 400.0;
+                        // per thread and SFT: ~40 instructions of set-up and M + 7 table loads,
+                        // then ~75 per template; staging ~14 per staged pair; round overhead
+                        const double per_thread = 40.0 + (Mv + 7) + 75.0 * Mv;
+                        cost += (double)warps * 32.0 * per_thread + (double)w_pairs * 14.0 + 400.0;
                     }
                 }
                 if (cost < best_cost * 0.999) {
