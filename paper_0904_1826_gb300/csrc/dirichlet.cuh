@@ -107,14 +107,16 @@ template <int DV, int STRIDE>
 __device__ __forceinline__ float2 window_sum(const float4* __restrict__ pp, float kap, int d_rt) {
     const int D = DV ? DV : d_rt;
     const float y0 = fmaf(2.0f, kap, (float)(2 * D - 3));
+    const float2 y02 = make_float2(y0, y0);
     float2 Q = make_float2(0.f, 0.f);
 #pragma unroll
     for (int gi = 0; gi < (DV ? DV : 64); ++gi) {
         if (!DV && gi >= D) break;
         const float4 e = pp[gi * STRIDE];
-        const float Y = y0 - (float)(4 * gi);
-        const float r = rcp_approx(pair_den(D, Y, kap, gi));
-        const float2 S = __ffma2_rn(make_float2(Y, Y), make_float2(e.x, e.y), make_float2(e.z, e.w));
+        const float c = (float)(-4 * gi);
+        const float2 Y2 = __fadd2_rn(y02, make_float2(c, c));   // Y in both halves
+        const float r = rcp_approx(pair_den(D, Y2.x, kap, gi));
+        const float2 S = __ffma2_rn(Y2, make_float2(e.x, e.y), make_float2(e.z, e.w));
         Q = __ffma2_rn(S, make_float2(r, r), Q);
     }
     return Q;
@@ -299,7 +301,10 @@ __global__ void __launch_bounds__(kMaxThreads, 2) dirichlet_kernel(const Dirichl
         if (rd + 2 < n_rounds) issue_consts(rd + 2);
         cp_async_commit();
 
-        for (int c = 0; c < (warp_live ? nc : 0); ++c) {
+        // warps walk the round's SFTs from different starting points so that
+        // their reciprocal-heavy and multiply-add-heavy phases interleave
+        int c = warp % nc;
+        for (int cc = 0; cc < (warp_live ? nc : 0); ++cc, c = (c + 1 == nc) ? 0 : c + 1) {
             const SkySftMeta m = s_meta[cslot * C + c];
             const long long kh = s_kh0[(cslot * C + c) * p.n_fdot + row_i] + (long long)j_t * m.dk;
             const int k0 = (int)(kh >> 32);
@@ -325,7 +330,8 @@ __global__ void __launch_bounds__(kMaxThreads, 2) dirichlet_kernel(const Dirichl
                 for (int q = 0; q < M; ++q) {
                     const float kap = clamp_kappa(fmaf((float)q, m.eps, kap0));
                     const float2 Q = window_sum<DV, STRIDE>(pp + q, kap, d_rt);
-                    accumulate(tw_re, tw_im, sinpi_unit(kap), Q, a2, b2, fa[q], fb[q]);
+                    const float sk = sinpi_unit(kap);
+                    accumulate(tw_re, tw_im, sk, Q, a2, b2, fa[q], fb[q]);
                     if (q + 1 < M) {
                         const float t = fmaf(tw_re, m.rot_re, -tw_im * m.rot_im);
                         tw_im = fmaf(tw_re, m.rot_im, tw_im * m.rot_re);
