@@ -113,10 +113,9 @@ __device__ __forceinline__ float2 window_sum(const float4* __restrict__ pp, floa
     for (int gi = 0; gi < (DV ? DV : 64); ++gi) {
         if (!DV && gi >= D) break;
         const float4 e = pp[gi * STRIDE];
-        const float c = (float)(-4 * gi);
-        const float2 Y2 = __fadd2_rn(y02, make_float2(c, c));   // Y in both halves
-        const float r = rcp_approx(pair_den(D, Y2.x, kap, gi));
-        const float2 S = __ffma2_rn(Y2, make_float2(e.x, e.y), make_float2(e.z, e.w));
+        const float Y = y0 - (float)(4 * gi);
+        const float r = rcp_approx(pair_den(D, Y, kap, gi));
+        const float2 S = __ffma2_rn(make_float2(Y, Y), make_float2(e.x, e.y), make_float2(e.z, e.w));
         Q = __ffma2_rn(S, make_float2(r, r), Q);
     }
     return Q;
@@ -303,8 +302,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2) dirichlet_kernel(const Dirichl
 
         // warps walk the round's SFTs from different starting points so that
         // their reciprocal-heavy and multiply-add-heavy phases interleave
-        int c = warp % nc;
-        for (int cc = 0; cc < (warp_live ? nc : 0); ++cc, c = (c + 1 == nc) ? 0 : c + 1) {
+        for (int c = 0; c < (warp_live ? nc : 0); ++c) {
             const SkySftMeta m = s_meta[cslot * C + c];
             const long long kh = s_kh0[(cslot * C + c) * p.n_fdot + row_i] + (long long)j_t * m.dk;
             const int k0 = (int)(kh >> 32);
