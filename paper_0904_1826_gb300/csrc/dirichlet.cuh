@@ -126,46 +126,6 @@ __host__ __device__ constexpr bool pair_is_singular(int D, int gi) {
     return ((D & 1) == 0) ? (gi == D / 2 - 1 || gi == D / 2) : (gi == (D - 1) / 2);
 }
 
-// Reciprocals 1/(Y^2 - 1) of the regular pairs at the thread's first template
-// (kappa_0) and their derivatives d/dY = -2 Y r^2, for templates whose kappa
-// differs from kappa_0 by |q eps| < 2e-3: r(Y0 + dY) = r0 + dY t0 has a
-// relative error below 3 dY^2 / Y^2 < 2e-6 for the regular pairs (|Y| >= 3).
-template <int D>
-struct SharedRcp {
-    float r0[D], t0[D];
-    __device__ __forceinline__ void init(float kap0) {
-#pragma unroll
-        for (int gi = 0; gi < D; ++gi) {
-            if (pair_is_singular(D, gi)) {
-                r0[gi] = t0[gi] = 0.f;
-                continue;
-            }
-            const float Y = fmaf(2.0f, kap0, (float)(2 * D - 3 - 4 * gi));
-            const float r = rcp_approx(fmaf(Y, Y, -1.0f));
-            r0[gi] = r;
-            t0[gi] = -2.0f * Y * r * r;
-        }
-    }
-};
-
-// Window sum of a template whose kappa is kap0 + dY/2: regular pairs from the
-// shared reciprocals, the singular-adjacent pairs exactly.
-template <int D, int STRIDE>
-__device__ __forceinline__ float2 window_sum_shared(const float4* __restrict__ pp, float kap, float dY,
-                                                    const SharedRcp<D>& sr) {
-    const float y0 = fmaf(2.0f, kap, (float)(2 * D - 3));
-    float2 Q = make_float2(0.f, 0.f);
-#pragma unroll
-    for (int gi = 0; gi < D; ++gi) {
-        const float4 e = pp[gi * STRIDE];
-        const float Y = y0 - (float)(4 * gi);
-        const float r = pair_is_singular(D, gi) ? rcp_approx(pair_den(D, Y, kap, gi)) : fmaf(dY, sr.t0[gi], sr.r0[gi]);
-        const float2 S = __ffma2_rn(make_float2(Y, Y), make_float2(e.x, e.y), make_float2(e.z, e.w));
-        Q = __ffma2_rn(S, make_float2(r, r), Q);
-    }
-    return Q;
-}
-
 // Fixed-point fraction (2^-32 units) to float in [0, 1), truncated to 23 bits.
 __device__ __forceinline__ float frac_to_float(unsigned int fr) {
     return __int_as_float(0x3f800000u | (fr >> 9)) - 1.0f;
@@ -369,16 +329,11 @@ __global__ void __launch_bounds__(kMaxThreads, 2) dirichlet_kernel(const Dirichl
                 __sincosf((float)(int)ph * kPhaseToRad, &sn, &cs);
                 float tw_re = cs, tw_im = -sn;
                 const float kap0 = clamp_kappa(frac_to_float((unsigned int)kh));
-                SharedRcp<(DV > 0 && M > 1) ? DV : 1> sr;
-                if (DV > 0 && M > 1) sr.init(kap0);
+
 #pragma unroll
                 for (int q = 0; q < M; ++q) {
                     const float kap = clamp_kappa(fmaf((float)q, m.eps, kap0));
-                    float2 Q;
-                    if constexpr (DV > 0 && M > 1)
-                        Q = window_sum_shared<DV, STRIDE>(pp + q, kap, 2.0f * (kap - kap0), sr);
-                    else
-                        Q = window_sum<DV, STRIDE>(pp + q, kap, d_rt);
+                    const float2 Q = window_sum<DV, STRIDE>(pp + q, kap, d_rt);
                     const float sk = sinpi_unit(kap);
                     accumulate(tw_re, tw_im, sk, Q, a2, b2, fa[q], fb[q]);
                     if (q + 1 < M) {
