@@ -200,6 +200,77 @@ int fstat_get_launch_count(fstat_ctx *ctx, int64_t *n_launches);
  * accumulator.  Synchronises. */
 int fstat_take_kernel_time(fstat_ctx *ctx, double *ms_dirichlet, double *ms_total, int32_t *n_calls);
 
+/* ---- Measured tile autotuner ------------------------------------------------
+ * Time the Dirichlet kernel for candidate tilings (templates per thread M,
+ * SFTs per staging round) on a slice of the current bank (the first sky
+ * points, a few waves of blocks) and keep the fastest as the context's tile
+ * choice for later computes.  out[4] (host, may be NULL) receives
+ * (M, sft_chunk, warps, best kernel time on the slice in microseconds).
+ * Synchronises.  Errors: ESTATE (no SFTs or templates). */
+int fstat_autotune(fstat_ctx *ctx, void *cuda_stream, int32_t *out);
+
+/* ---- Batched form: many workunits, one persistent launch ----------------------
+ * A workunit is a full problem of its own: SFTs of 1..8 detectors sharing T,
+ * k_lo and n_bins, and a template bank.  fstat_batch_compute runs, for all
+ * workunits added to the context, the per-(sky, SFT) FP64 kernel of each, one
+ * persistent Dirichlet kernel per group of workunits with the same kernel
+ * variant (its blocks pull (workunit, sky, column, chunk) items from a device
+ * queue until every item of every workunit is done), and the toplist of each
+ * workunit; the sequence is captured into a CUDA graph on the first call and
+ * replayed on later calls (re-captured when workunits are added).  The
+ * context's own single-bank state (fstat_set_sfts / fstat_set_templates) is
+ * separate and unaffected. */
+typedef struct {
+    int32_t n_det;                 /* 1..8 */
+    const fstat_detector *det;     /* [n_det] host */
+    const int32_t *n_sft;          /* [n_det] host */
+    const double *const *t_start;  /* [n_det] host pointers to [n_sft[d]] start times */
+    const float *const *bins;      /* [n_det] host pointers to [n_sft[d]][n_bins][2] FP32 */
+    double Tsft;
+    int64_t k_lo;
+    int32_t n_bins;
+    const double *sky;             /* [n_sky][2] host */
+    int32_t n_sky;
+    double f0, df;
+    int32_t n_f;
+    const double *fdot;            /* [n_fdot] host */
+    int32_t n_fdot;
+    double t_ref;
+} fstat_workunit;
+
+/* Add a workunit (inputs copied, host memory); *wu_id receives its index.
+ * Errors: as fstat_set_sfts / fstat_set_templates. */
+int fstat_batch_add(fstat_ctx *ctx, const fstat_workunit *wu, int32_t *wu_id);
+
+/* Add model-exact signals to workunit wu's SFTs (see fstat_inject). */
+int fstat_batch_inject(fstat_ctx *ctx, int32_t wu, const fstat_signal *sig, int32_t n_sig, double t_ref);
+
+/* Remove all workunits and release their memory. */
+int fstat_batch_clear(fstat_ctx *ctx);
+
+/* Number of workunits in the batch. */
+int fstat_batch_size(fstat_ctx *ctx, int32_t *n_wu);
+
+/* Run the whole batch asynchronously on cuda_stream (see above).
+ * Errors: ESTATE (empty batch), ECUDA. */
+int fstat_batch_compute(fstat_ctx *ctx, void *cuda_stream);
+
+/* Compute workunit wu alone with the ordinary (one launch per bank) path,
+ * asynchronously on cuda_stream; results are read with the calls below.
+ * This is the one-launch-per-workunit reference the batch is compared with. */
+int fstat_batch_compute_one(fstat_ctx *ctx, int32_t wu, void *cuda_stream);
+
+/* Toplist / 2F of workunit wu after fstat_batch_compute (synchronise); same
+ * contracts as fstat_get_toplist / fstat_get_2f. */
+int fstat_batch_get_toplist(fstat_ctx *ctx, int32_t wu, int32_t k, int64_t *idx, float *twoF);
+int fstat_batch_get_2f(fstat_ctx *ctx, int32_t wu, float *out, int64_t offset, int64_t count, int32_t mem);
+
+/* Timing of the last batch compute: wu_done_ms[n_wu] (host, may be NULL) =
+ * device time from the start of the batch to the completion of each
+ * workunit's last Dirichlet item; *total_ms = start to end of the batch
+ * (CUDA events on the stream).  Synchronises. */
+int fstat_batch_get_times(fstat_ctx *ctx, double *wu_done_ms, double *total_ms);
+
 #ifdef __cplusplus
 }
 #endif

@@ -45,6 +45,15 @@ class fstat_signal(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in ("alpha", "delta", "psi", "cosi", "phi0", "f", "fdot", "rho")]
 
 
+class fstat_workunit(ctypes.Structure):
+    _fields_ = [("n_det", ctypes.c_int32), ("det", ctypes.POINTER(fstat_detector)),
+                ("n_sft", ctypes.POINTER(ctypes.c_int32)), ("t_start", ctypes.POINTER(ctypes.c_void_p)),
+                ("bins", ctypes.POINTER(ctypes.c_void_p)), ("Tsft", ctypes.c_double), ("k_lo", ctypes.c_int64),
+                ("n_bins", ctypes.c_int32), ("sky", ctypes.c_void_p), ("n_sky", ctypes.c_int32),
+                ("f0", ctypes.c_double), ("df", ctypes.c_double), ("n_f", ctypes.c_int32),
+                ("fdot", ctypes.c_void_p), ("n_fdot", ctypes.c_int32), ("t_ref", ctypes.c_double)]
+
+
 _P = ctypes.c_void_p
 _I32 = ctypes.c_int32
 _I64 = ctypes.c_int64
@@ -69,6 +78,16 @@ SIGNATURES = {
     "fstat_get_plan": (ctypes.c_int, [_P, _P]),
     "fstat_get_launch_count": (ctypes.c_int, [_P, ctypes.POINTER(_I64)]),
     "fstat_take_kernel_time": (ctypes.c_int, [_P, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_I32)]),
+    "fstat_autotune": (ctypes.c_int, [_P, _P, _P]),
+    "fstat_batch_add": (ctypes.c_int, [_P, ctypes.POINTER(fstat_workunit), ctypes.POINTER(_I32)]),
+    "fstat_batch_inject": (ctypes.c_int, [_P, _I32, ctypes.POINTER(fstat_signal), _I32, _D]),
+    "fstat_batch_clear": (ctypes.c_int, [_P]),
+    "fstat_batch_size": (ctypes.c_int, [_P, ctypes.POINTER(_I32)]),
+    "fstat_batch_compute": (ctypes.c_int, [_P, _P]),
+    "fstat_batch_compute_one": (ctypes.c_int, [_P, _I32, _P]),
+    "fstat_batch_get_toplist": (ctypes.c_int, [_P, _I32, _I32, _P, _P]),
+    "fstat_batch_get_2f": (ctypes.c_int, [_P, _I32, _P, _I64, _I64, _I32]),
+    "fstat_batch_get_times": (ctypes.c_int, [_P, _P, ctypes.POINTER(_D)]),
 }
 
 
@@ -225,6 +244,90 @@ def fstat_get_launch_count(ctx) -> int:
     return int(n.value)
 
 
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    h = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    return ctypes.c_void_p(h) if h else None
+
+
+def fstat_autotune(ctx, stream=None) -> dict:
+    out = np.zeros(4, dtype=np.int32)
+    _check(ctx, _lib.fstat_autotune(ctx, _stream_handle(stream), _host_ptr(out)))
+    return {"M": int(out[0]), "sft_chunk": int(out[1]), "warps": int(out[2]), "slice_us": int(out[3])}
+
+
+def fstat_batch_add(ctx, w, bins_override=None) -> int:
+    """Add a workload.generate.Workload (its detectors' SFTs and bank) to the batch."""
+    dets = w.detectors
+    n = len(dets)
+    keep = []
+    det_arr = (fstat_detector * n)(*[fstat_detector(d.lat, d.lon, d.az) for d in dets])
+    n_sft = (ctypes.c_int32 * n)(*[d.n_sft for d in dets])
+    tps, bps = (ctypes.c_void_p * n)(), (ctypes.c_void_p * n)()
+    for i, d in enumerate(dets):
+        t = np.ascontiguousarray(d.t_start, dtype=np.float64)
+        b = np.ascontiguousarray(d.bins if bins_override is None else bins_override[i], dtype=np.complex64)
+        keep += [t, b]
+        tps[i] = t.ctypes.data
+        bps[i] = b.ctypes.data
+    sky = np.ascontiguousarray(w.bank.sky, dtype=np.float64)
+    fd = np.ascontiguousarray(w.bank.fdot, dtype=np.float64)
+    wu = fstat_workunit(n, det_arr, n_sft, tps, bps, w.T, int(w.k_lo), int(w.n_bins), sky.ctypes.data,
+                        w.bank.n_sky, w.bank.f0, w.bank.df, w.bank.n_f, fd.ctypes.data, w.bank.n_fdot,
+                        w.bank.t_ref)
+    wid = _I32()
+    _check(ctx, _lib.fstat_batch_add(ctx, ctypes.byref(wu), ctypes.byref(wid)))
+    del keep
+    return int(wid.value)
+
+
+def fstat_batch_inject(ctx, wu: int, signals, t_ref: float) -> None:
+    sig = list(signals)
+    arr = (fstat_signal * max(len(sig), 1))()
+    for i, s in enumerate(sig):
+        arr[i] = fstat_signal(s.alpha, s.delta, s.psi, s.cosi, s.phi0, s.f, s.fdot, s.rho)
+    _check(ctx, _lib.fstat_batch_inject(ctx, wu, arr, len(sig), t_ref))
+
+
+def fstat_batch_clear(ctx) -> None:
+    _check(ctx, _lib.fstat_batch_clear(ctx))
+
+
+def fstat_batch_size(ctx) -> int:
+    n = _I32()
+    _check(ctx, _lib.fstat_batch_size(ctx, ctypes.byref(n)))
+    return int(n.value)
+
+
+def fstat_batch_compute(ctx, stream=None) -> None:
+    _check(ctx, _lib.fstat_batch_compute(ctx, _stream_handle(stream)))
+
+
+def fstat_batch_compute_one(ctx, wu: int, stream=None) -> None:
+    _check(ctx, _lib.fstat_batch_compute_one(ctx, wu, _stream_handle(stream)))
+
+
+def fstat_batch_get_toplist(ctx, wu: int, k: int):
+    idx = np.empty(k, dtype=np.int64)
+    val = np.empty(k, dtype=np.float32)
+    _check(ctx, _lib.fstat_batch_get_toplist(ctx, wu, k, _host_ptr(idx), _host_ptr(val)))
+    return idx, val
+
+
+def fstat_batch_get_2f(ctx, wu: int, offset: int, count: int):
+    out = np.empty(count, dtype=np.float32)
+    _check(ctx, _lib.fstat_batch_get_2f(ctx, wu, _host_ptr(out), offset, count, FSTAT_MEM_HOST))
+    return out
+
+
+def fstat_batch_get_times(ctx, n_wu: int):
+    done = np.zeros(n_wu, dtype=np.float64)
+    tot = _D()
+    _check(ctx, _lib.fstat_batch_get_times(ctx, _host_ptr(done), ctypes.byref(tot)))
+    return done, float(tot.value)
+
+
 def fstat_take_kernel_time(ctx):
     mb, mt, n = _D(), _D(), _I32()
     _check(ctx, _lib.fstat_take_kernel_time(ctx, ctypes.byref(mb), ctypes.byref(mt), ctypes.byref(n)))
@@ -300,3 +403,6 @@ class FStat:
 
     def launch_count(self) -> int:
         return fstat_get_launch_count(self.ctx)
+
+    def autotune(self, stream=None) -> dict:
+        return fstat_autotune(self.ctx, stream)

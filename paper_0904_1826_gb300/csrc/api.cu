@@ -2,6 +2,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -15,6 +16,15 @@ cudaError_t launch_dirichlet_f16(int v, const DirichletParams& p, int d_rt, int 
                                  long long grid, cudaStream_t s);
 cudaError_t launch_dirichlet_bf16(int v, const DirichletParams& p, int d_rt, int threads, size_t smem,
                                   long long grid, cudaStream_t s);
+cudaError_t launch_dirichlet_batch_c64(int v, const DirichletBatch& b, int d_rt, int threads, size_t smem,
+                                     int grid, cudaStream_t s);
+cudaError_t launch_dirichlet_batch_f16(int v, const DirichletBatch& b, int d_rt, int threads, size_t smem,
+                                     int grid, cudaStream_t s);
+cudaError_t launch_dirichlet_batch_bf16(int v, const DirichletBatch& b, int d_rt, int threads, size_t smem,
+                                      int grid, cudaStream_t s);
+cudaError_t dirichlet_occupancy_c64(int v, int threads, size_t smem, int* blocks_per_sm);
+cudaError_t dirichlet_occupancy_f16(int v, int threads, size_t smem, int* blocks_per_sm);
+cudaError_t dirichlet_occupancy_bf16(int v, int threads, size_t smem, int* blocks_per_sm);
 size_t inject_work_doubles(int n_sig, int n_sft);
 }  // namespace fs
 
@@ -98,6 +108,23 @@ struct fstat_ctx {
     size_t cap_inj = 0;
     fstat_signal* d_sig = nullptr;
     size_t cap_sig = 0;
+    // batched form: child contexts, one per workunit
+    std::vector<fstat_ctx*> wus;
+    bool batch_ran = false;           // first batch compute done (buffers and attributes set)
+    bool graph_valid = false;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    DirichletParams* d_banks = nullptr;
+    long long* d_prefix = nullptr;
+    int* d_rem_init = nullptr;
+    int* d_rem = nullptr;
+    unsigned long long* d_queue = nullptr;
+    unsigned long long* d_done = nullptr;   // [n_wu + 1], last = batch start
+    int n_groups = 0;
+    cudaEvent_t bev0 = nullptr, bev1 = nullptr;
+    long long launches_per_graph = 0;
+    std::vector<int> batch_order;     // grouped position -> workunit index
 };
 
 namespace {
@@ -398,10 +425,16 @@ int fstat_create(fstat_ctx** out, int device, const fstat_opts* opts) {
     return FSTAT_OK;
 }
 
+int fstat_batch_clear(fstat_ctx* c);
+
 void fstat_destroy(fstat_ctx* c) {
     if (!c) return;
     cudaSetDevice(c->device);
     cudaDeviceSynchronize();
+    fstat_batch_clear(c);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->bev0) cudaEventDestroy(c->bev0);
+    if (c->bev1) cudaEventDestroy(c->bev1);
     void* ptrs[] = {c->d_bins, c->d_bins16, c->d_scale, c->d_state, c->d_tstart, c->d_det_of, c->d_sky,
                     c->d_fdot, c->d_meta, c->d_kh0, c->d_ph0, c->d_abcd, c->d_comb, c->d_twoF, c->d_err,
                     c->tw.hist, c->tw.state, c->tw.tie_count, c->tw.cand_idx, c->tw.cand_val, c->tw.n_cand,
@@ -559,20 +592,16 @@ int fstat_set_templates(fstat_ctx* c, const double* sky, int32_t n_sky, double f
     return FSTAT_OK;
 }
 
-int fstat_compute(fstat_ctx* c, void* cuda_stream) {
-    if (!c) return FSTAT_EINVAL;
-    c->err.clear();
-    if (!c->have_sfts || !c->have_templates) return fail(c, FSTAT_ESTATE, "load SFTs and set templates first");
-    if (set_device(c) != FSTAT_OK) return FSTAT_ECUDA;
-    cudaStream_t s = (cudaStream_t)cuda_stream;
-    c->stream = s;
+namespace {
+
+// Refresh the per-SFT state, plan the tiles and size every buffer of one bank.
+int prepare(fstat_ctx* c, cudaStream_t s) {
     int rc;
     if ((rc = refresh_sft_state(c, s)) != FSTAT_OK) return rc;
     if (!c->plan_valid) {
         if ((rc = make_plan(c, c->plan)) != FSTAT_OK) return rc;
         c->plan_valid = true;
     }
-    const Plan& pl = c->plan;
     const size_t n_meta = (size_t)c->n_sky * c->n_sft;
     const size_t n_base = n_meta * c->n_fdot;
     const size_t n_twoF = (size_t)c->n_sky * c->n_fdot * c->n_f;
@@ -583,33 +612,36 @@ int fstat_compute(fstat_ctx* c, void* cuda_stream) {
     if ((rc = grow(c, &c->d_comb, c->cap_comb, (size_t)c->n_sky)) != FSTAT_OK) return rc;
     if ((rc = grow(c, &c->d_twoF, c->cap_twoF, n_twoF)) != FSTAT_OK) return rc;
     if ((rc = ensure_topk(c)) != FSTAT_OK) return rc;
-    CUDA_TRY(c, cudaMemsetAsync(c->d_err, 0, sizeof(int) * 3, s));
+    return FSTAT_OK;
+}
 
-    const int slot = c->n_timed % kTimedRing;
-    CUDA_TRY(c, cudaEventRecord(c->ev_a[slot], s));
+TimingParams timing_params(const fstat_ctx* c, int n_sky) {
     TimingParams tp{};
     tp.st = c->d_state;
     tp.sky = c->d_sky;
     tp.fdot = c->d_fdot;
     tp.scale = c->d_scale;
-    tp.n_sky = c->n_sky;
+    tp.n_sky = n_sky;
     tp.n_sft = c->n_sft;
     tp.n_fdot = c->n_fdot;
     tp.f0 = c->f0;
     tp.df = c->df;
     tp.T = c->T;
     tp.t_ref = c->t_ref;
-    tp.P = pl.P;
-    tp.L = pl.L;
-    tp.M = pl.M;
+    tp.P = c->plan.P;
+    tp.L = c->plan.L;
+    tp.M = c->plan.M;
     tp.meta = c->d_meta;
     tp.kh0 = c->d_kh0;
     tp.ph0 = c->d_ph0;
     tp.abcd = c->d_abcd;
     tp.comb = c->d_comb;
     tp.err = c->d_err;
-    CUDA_TRY(c, launch_timing(tp, s));
+    return tp;
+}
 
+DirichletParams dirichlet_params(const fstat_ctx* c) {
+    const Plan& pl = c->plan;
     DirichletParams dp{};
     dp.bins = c->opts.bins_form == FSTAT_BINS_C64 ? (const void*)c->d_bins : (const void*)c->d_bins16;
     dp.row = c->row;
@@ -634,24 +666,50 @@ int fstat_compute(fstat_ctx* c, void* cuda_stream) {
     dp.w_raw = pl.w_raw;
     dp.sft_chunk = pl.C;
     dp.err = c->d_err;
-    CUDA_TRY(c, cudaEventRecord(c->ev_b[slot], s));
-    cudaError_t e;
+    return dp;
+}
+
+cudaError_t launch_dir(const fstat_ctx* c, const DirichletParams& dp, long long grid, cudaStream_t s) {
+    const Plan& pl = c->plan;
     const int threads = pl.W * 32;
     if (c->opts.bins_form == FSTAT_BINS_C64)
-        e = launch_dirichlet_c64(pl.variant, dp, c->opts.dterms, threads, pl.smem, pl.grid, s);
-    else if (c->opts.bins_form == FSTAT_BINS_F16)
-        e = launch_dirichlet_f16(pl.variant, dp, c->opts.dterms, threads, pl.smem, pl.grid, s);
-    else
-        e = launch_dirichlet_bf16(pl.variant, dp, c->opts.dterms, threads, pl.smem, pl.grid, s);
-    if (e != cudaSuccess) return fail(c, FSTAT_ECUDA, "Dirichlet launch: %s", cudaGetErrorString(e));
-    CUDA_TRY(c, cudaEventRecord(c->ev_c[slot], s));
-    const long long n = (long long)n_twoF;
+        return launch_dirichlet_c64(pl.variant, dp, c->opts.dterms, threads, pl.smem, grid, s);
+    if (c->opts.bins_form == FSTAT_BINS_F16)
+        return launch_dirichlet_f16(pl.variant, dp, c->opts.dterms, threads, pl.smem, grid, s);
+    return launch_dirichlet_bf16(pl.variant, dp, c->opts.dterms, threads, pl.smem, grid, s);
+}
+
+int enqueue_topk(fstat_ctx* c, cudaStream_t s) {
+    const long long n = (long long)c->n_sky * c->n_fdot * c->n_f;
     const int k = (int)std::min<long long>(c->opts.topk, n);
-    c->launches += 2;   // timing + Dirichlet
     if (k > 0) {
         CUDA_TRY(c, launch_topk(c->d_twoF, n, k, c->tw, s));
         c->launches += 9;   // 3 histograms, 3 selections, collect, ties, sort
     }
+    return FSTAT_OK;
+}
+
+}  // namespace
+
+int fstat_compute(fstat_ctx* c, void* cuda_stream) {
+    if (!c) return FSTAT_EINVAL;
+    c->err.clear();
+    if (!c->have_sfts || !c->have_templates) return fail(c, FSTAT_ESTATE, "load SFTs and set templates first");
+    if (set_device(c) != FSTAT_OK) return FSTAT_ECUDA;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    c->stream = s;
+    int rc;
+    if ((rc = prepare(c, s)) != FSTAT_OK) return rc;
+    CUDA_TRY(c, cudaMemsetAsync(c->d_err, 0, sizeof(int) * 3, s));
+    const int slot = c->n_timed % kTimedRing;
+    CUDA_TRY(c, cudaEventRecord(c->ev_a[slot], s));
+    CUDA_TRY(c, launch_timing(timing_params(c, c->n_sky), s));
+    CUDA_TRY(c, cudaEventRecord(c->ev_b[slot], s));
+    cudaError_t e = launch_dir(c, dirichlet_params(c), c->plan.grid, s);
+    if (e != cudaSuccess) return fail(c, FSTAT_ECUDA, "Dirichlet launch: %s", cudaGetErrorString(e));
+    CUDA_TRY(c, cudaEventRecord(c->ev_c[slot], s));
+    c->launches += 2;   // timing + Dirichlet
+    if ((rc = enqueue_topk(c, s)) != FSTAT_OK) return rc;
     CUDA_TRY(c, cudaEventRecord(c->ev_d[slot], s));
     c->n_timed++;
     c->computed = true;
@@ -812,6 +870,380 @@ int fstat_take_kernel_time(fstat_ctx* c, double* ms_dirichlet, double* ms_total,
     *ms_dirichlet = n ? sb / n : 0.0;
     *ms_total = n ? st / n : 0.0;
     c->n_timed = 0;
+    return FSTAT_OK;
+}
+
+
+int fstat_autotune(fstat_ctx* c, void* cuda_stream, int32_t* out) {
+    if (!c) return FSTAT_EINVAL;
+    c->err.clear();
+    // a context holding only workunits tunes on its largest one and applies the choice to all
+    if ((!c->have_sfts || !c->have_templates) && !c->wus.empty()) {
+        fstat_ctx* big = c->wus[0];
+        for (fstat_ctx* w : c->wus)
+            if ((double)w->n_sky * w->n_f * w->n_fdot * w->n_sft > (double)big->n_sky * big->n_f * big->n_fdot * big->n_sft)
+                big = w;
+        int32_t o[4];
+        int rc = fstat_autotune(big, cuda_stream, o);
+        if (rc != FSTAT_OK) return fail(c, rc, "autotune: %s", big->err.c_str());
+        for (fstat_ctx* w : c->wus) {
+            w->opts.tile_m = o[0];
+            w->opts.sft_chunk = o[1];
+            w->plan_valid = false;
+        }
+        c->opts.tile_m = o[0];
+        c->opts.sft_chunk = o[1];
+        c->graph_valid = false;
+        if (out) std::memcpy(out, o, sizeof(o));
+        return FSTAT_OK;
+    }
+    if (!c->have_sfts || !c->have_templates) return fail(c, FSTAT_ESTATE, "load SFTs and set templates first");
+    if (set_device(c) != FSTAT_OK) return FSTAT_ECUDA;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    c->stream = s;
+    const fstat_opts saved = c->opts;
+    // candidate (M, SFT round) pairs for this bank's thread layout
+    c->opts.tile_m = 0;
+    c->opts.sft_chunk = 0;
+    c->plan_valid = false;
+    int rc = prepare(c, s);
+    if (rc != FSTAT_OK) {
+        c->opts = saved;
+        return rc;
+    }
+    std::vector<int> Ms;
+    if (c->plan.M == 1) Ms = {1};
+    else if (c->opts.kahan) Ms = {5};
+    else if (c->plan.L == 2) Ms = {5, 7, 9};
+    else Ms = {7, 9};
+    const int Cs[3] = {6, 8, 10};
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    int bestM = c->plan.M, bestC = c->plan.C, bestW = c->plan.W;
+    for (int M : Ms) {
+        for (int C : Cs) {
+            c->opts.tile_m = M;
+            c->opts.sft_chunk = C;
+            c->plan_valid = false;
+            if (make_plan(c, c->plan) != FSTAT_OK) continue;
+            c->plan_valid = true;
+            if (c->plan.C != C) continue;   // round size capped by shared memory
+            // a slice of the bank: the first sky points, about four waves of blocks
+            const long long per_sky = (long long)c->plan.n_col * c->plan.chunks_per_col;
+            int occ = 2;
+            const long long want = 4LL * occ * 152;
+            const int n_sky_sub = (int)std::min<long long>(c->n_sky, std::max<long long>(1, (want + per_sky - 1) / per_sky));
+            if (launch_timing(timing_params(c, n_sky_sub), s) != cudaSuccess) continue;
+            const DirichletParams dp = dirichlet_params(c);
+            const long long grid = (long long)n_sky_sub * per_sky;
+            float t = 1e30f;
+            for (int rep = 0; rep < 3; ++rep) {
+                cudaEventRecord(e0, s);
+                cudaError_t e = launch_dir(c, dp, grid, s);
+                cudaEventRecord(e1, s);
+                if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) break;
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0) t = std::min(t, ms);   // first run warms up
+            }
+            c->launches += 4;
+            if (t < best) {
+                best = t;
+                bestM = M;
+                bestC = C;
+                bestW = c->plan.W;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->opts = saved;
+    c->opts.tile_m = bestM;
+    c->opts.sft_chunk = bestC;
+    c->plan_valid = false;
+    c->computed = false;
+    if (out) {
+        out[0] = bestM;
+        out[1] = bestC;
+        out[2] = bestW;
+        out[3] = (int32_t)std::min(best * 1000.f, 2.0e9f);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(c, FSTAT_ECUDA, "autotune: %s", cudaGetErrorString(e));
+    return FSTAT_OK;
+}
+
+int fstat_batch_add(fstat_ctx* c, const fstat_workunit* wu, int32_t* wu_id) {
+    if (!c || !wu) return FSTAT_EINVAL;
+    c->err.clear();
+    if (wu->n_det < 1 || wu->n_det > kMaxDet || !wu->det || !wu->n_sft || !wu->t_start || !wu->bins)
+        return fail(c, FSTAT_EINVAL, "workunit needs 1..8 detectors with SFTs");
+    fstat_ctx* w = nullptr;
+    int rc = fstat_create(&w, c->device, &c->opts);
+    if (rc != FSTAT_OK) return fail(c, rc, "workunit context creation failed");
+    for (int d = 0; d < wu->n_det; ++d) {
+        rc = fstat_set_sfts(w, d, &wu->det[d], wu->Tsft, wu->k_lo, wu->n_bins, wu->n_sft[d], wu->t_start[d],
+                            wu->bins[d], FSTAT_MEM_HOST);
+        if (rc != FSTAT_OK) {
+            fail(c, rc, "workunit detector %d: %s", d, w->err.c_str());
+            fstat_destroy(w);
+            return rc;
+        }
+    }
+    rc = fstat_set_templates(w, wu->sky, wu->n_sky, wu->f0, wu->df, wu->n_f, wu->fdot, wu->n_fdot, wu->t_ref);
+    if (rc != FSTAT_OK) {
+        fail(c, rc, "workunit bank: %s", w->err.c_str());
+        fstat_destroy(w);
+        return rc;
+    }
+    c->wus.push_back(w);
+    c->graph_valid = false;
+    c->batch_ran = false;
+    if (wu_id) *wu_id = (int32_t)c->wus.size() - 1;
+    return FSTAT_OK;
+}
+
+int fstat_batch_inject(fstat_ctx* c, int32_t wu, const fstat_signal* sig, int32_t n_sig, double t_ref) {
+    if (!c) return FSTAT_EINVAL;
+    if (wu < 0 || wu >= (int)c->wus.size()) return fail(c, FSTAT_EINVAL, "no workunit %d", wu);
+    int rc = fstat_inject(c->wus[wu], sig, n_sig, t_ref);
+    if (rc != FSTAT_OK) return fail(c, rc, "%s", c->wus[wu]->err.c_str());
+    c->graph_valid = false;
+    c->batch_ran = false;
+    return FSTAT_OK;
+}
+
+int fstat_batch_clear(fstat_ctx* c) {
+    if (!c) return FSTAT_EINVAL;
+    cudaSetDevice(c->device);
+    if (!c->wus.empty()) cudaDeviceSynchronize();
+    for (fstat_ctx* w : c->wus) fstat_destroy(w);
+    c->wus.clear();
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    c->graph_exec = nullptr;
+    c->graph = nullptr;
+    void* ptrs[] = {c->d_banks, c->d_prefix, c->d_rem_init, c->d_rem, c->d_queue, c->d_done};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    c->d_banks = nullptr;
+    c->d_prefix = nullptr;
+    c->d_rem_init = nullptr;
+    c->d_rem = nullptr;
+    c->d_queue = nullptr;
+    c->d_done = nullptr;
+    c->graph_valid = false;
+    c->batch_ran = false;
+    return FSTAT_OK;
+}
+
+int fstat_batch_size(fstat_ctx* c, int32_t* n_wu) {
+    if (!c || !n_wu) return FSTAT_EINVAL;
+    *n_wu = (int32_t)c->wus.size();
+    return FSTAT_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+__global__ void stamp_kernel(unsigned long long* t) {
+    unsigned long long v;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(v));
+    *t = v;
+}
+
+// Groups of workunits sharing a kernel variant and block size.
+struct BatchGroup {
+    int variant, W, form;
+    size_t smem;
+    int first, count;   // range in the sorted workunit order
+};
+
+// Enqueue the whole batch on stream s (also used inside graph capture).
+int enqueue_batch(fstat_ctx* c, const std::vector<int>& order, const std::vector<BatchGroup>& groups,
+                  cudaStream_t s) {
+    const int n = (int)c->wus.size();
+    stamp_kernel<<<1, 1, 0, s>>>(c->d_done + n);
+    CUDA_TRY(c, cudaGetLastError());
+    c->launches += 1;
+    for (fstat_ctx* w : c->wus) {
+        CUDA_TRY(c, cudaMemsetAsync(w->d_err, 0, sizeof(int) * 3, s));
+        CUDA_TRY(c, launch_timing(timing_params(w, w->n_sky), s));
+        w->launches += 1;
+    }
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_rem, c->d_rem_init, sizeof(int) * n, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(c, cudaMemsetAsync(c->d_queue, 0, sizeof(unsigned long long) * groups.size(), s));
+    int dev_sms = 152;
+    cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, c->device);
+    for (size_t g = 0; g < groups.size(); ++g) {
+        const BatchGroup& G = groups[g];
+        DirichletBatch b{};
+        b.banks = c->d_banks + G.first;
+        b.item_prefix = c->d_prefix + G.first + g;   // each group's prefix has count + 1 entries
+        b.n_wu = G.count;
+        b.queue = c->d_queue + g;
+        b.remaining = c->d_rem + G.first;
+        b.done_ns = c->d_done + G.first;
+        int occ = 1;
+        cudaError_t e;
+        if (G.form == FSTAT_BINS_C64) e = dirichlet_occupancy_c64(G.variant, G.W * 32, G.smem, &occ);
+        else if (G.form == FSTAT_BINS_F16) e = dirichlet_occupancy_f16(G.variant, G.W * 32, G.smem, &occ);
+        else e = dirichlet_occupancy_bf16(G.variant, G.W * 32, G.smem, &occ);
+        if (e != cudaSuccess) return fail(c, FSTAT_ECUDA, "occupancy: %s", cudaGetErrorString(e));
+        const int grid = std::max(1, occ) * dev_sms;
+        if (G.form == FSTAT_BINS_C64) e = launch_dirichlet_batch_c64(G.variant, b, c->opts.dterms, G.W * 32, G.smem, grid, s);
+        else if (G.form == FSTAT_BINS_F16) e = launch_dirichlet_batch_f16(G.variant, b, c->opts.dterms, G.W * 32, G.smem, grid, s);
+        else e = launch_dirichlet_batch_bf16(G.variant, b, c->opts.dterms, G.W * 32, G.smem, grid, s);
+        if (e != cudaSuccess) return fail(c, FSTAT_ECUDA, "batch Dirichlet launch: %s", cudaGetErrorString(e));
+        c->launches += 1;
+    }
+    for (fstat_ctx* w : c->wus) {
+        int rc = enqueue_topk(w, s);
+        if (rc != FSTAT_OK) return fail(c, rc, "%s", w->err.c_str());
+    }
+    (void)order;
+    return FSTAT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fstat_batch_compute(fstat_ctx* c, void* cuda_stream) {
+    if (!c) return FSTAT_EINVAL;
+    c->err.clear();
+    if (c->wus.empty()) return fail(c, FSTAT_ESTATE, "no workunits in the batch");
+    if (set_device(c) != FSTAT_OK) return FSTAT_ECUDA;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    c->stream = s;
+    const int n = (int)c->wus.size();
+    for (fstat_ctx* w : c->wus) {
+        w->stream = s;
+        int rc = prepare(w, s);
+        if (rc != FSTAT_OK) return fail(c, rc, "workunit: %s", w->err.c_str());
+    }
+    if (!c->bev0) {
+        cudaEventCreate(&c->bev0);
+        cudaEventCreate(&c->bev1);
+    }
+    // group workunits by kernel variant and block size (usually one group)
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    auto key = [&](int i) { return c->wus[i]->plan.variant * 64 + c->wus[i]->plan.W; };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return key(a) < key(b); });
+    if (!c->graph_valid) {
+        // device tables in grouped order
+        std::vector<BatchGroup> groups;
+        std::vector<DirichletParams> banks(n);
+        std::vector<long long> prefix;
+        std::vector<int> rem(n);
+        for (int k = 0; k < n; ++k) {
+            fstat_ctx* w = c->wus[order[k]];
+            if (groups.empty() || key(order[groups.back().first]) != key(order[k])) {
+                groups.push_back(BatchGroup{w->plan.variant, w->plan.W, w->opts.bins_form, 0, k, 0});
+                prefix.push_back(0);
+            }
+            BatchGroup& G = groups.back();
+            G.count++;
+            G.smem = std::max(G.smem, w->plan.smem);
+            banks[k] = dirichlet_params(w);
+            rem[k] = (int)w->plan.grid;
+            prefix.push_back(prefix.back() + w->plan.grid);
+        }
+        if (c->d_banks) cudaFree(c->d_banks);
+        if (c->d_prefix) cudaFree(c->d_prefix);
+        if (c->d_rem_init) cudaFree(c->d_rem_init);
+        if (c->d_rem) cudaFree(c->d_rem);
+        if (c->d_queue) cudaFree(c->d_queue);
+        if (c->d_done) cudaFree(c->d_done);
+        CUDA_TRY(c, cudaMalloc(&c->d_banks, sizeof(DirichletParams) * n));
+        CUDA_TRY(c, cudaMalloc(&c->d_prefix, sizeof(long long) * prefix.size()));
+        CUDA_TRY(c, cudaMalloc(&c->d_rem_init, sizeof(int) * n));
+        CUDA_TRY(c, cudaMalloc(&c->d_rem, sizeof(int) * n));
+        CUDA_TRY(c, cudaMalloc(&c->d_queue, sizeof(unsigned long long) * groups.size()));
+        CUDA_TRY(c, cudaMalloc(&c->d_done, sizeof(unsigned long long) * (n + 1)));
+        CUDA_TRY(c, cudaMemcpy(c->d_banks, banks.data(), sizeof(DirichletParams) * n, cudaMemcpyHostToDevice));
+        CUDA_TRY(c, cudaMemcpy(c->d_prefix, prefix.data(), sizeof(long long) * prefix.size(), cudaMemcpyHostToDevice));
+        CUDA_TRY(c, cudaMemcpy(c->d_rem_init, rem.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
+        CUDA_TRY(c, cudaMemset(c->d_done, 0, sizeof(unsigned long long) * (n + 1)));
+        // first run without a graph (sets kernel attributes), then capture the same sequence
+        CUDA_TRY(c, cudaEventRecord(c->bev0, s));
+        int rc = enqueue_batch(c, order, groups, s);
+        if (rc != FSTAT_OK) return rc;
+        CUDA_TRY(c, cudaEventRecord(c->bev1, s));
+        CUDA_TRY(c, cudaStreamSynchronize(s));
+        if (!c->cap_stream) CUDA_TRY(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+        if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+        if (c->graph) cudaGraphDestroy(c->graph);
+        c->graph_exec = nullptr;
+        c->graph = nullptr;
+        const long long launches_before = c->launches;
+        CUDA_TRY(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeRelaxed));
+        rc = enqueue_batch(c, order, groups, c->cap_stream);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+        if (rc != FSTAT_OK) return rc;
+        if (e != cudaSuccess) return fail(c, FSTAT_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+        c->graph = g;
+        CUDA_TRY(c, cudaGraphInstantiate(&c->graph_exec, g, 0));
+        c->launches_per_graph = c->launches - launches_before;
+        c->batch_order = order;
+        c->launches = launches_before;
+        c->graph_valid = true;
+    } else {
+        CUDA_TRY(c, cudaEventRecord(c->bev0, s));
+        CUDA_TRY(c, cudaGraphLaunch(c->graph_exec, s));
+        CUDA_TRY(c, cudaEventRecord(c->bev1, s));
+        c->launches += c->launches_per_graph;
+    }
+    for (fstat_ctx* w : c->wus) w->computed = true;
+    return FSTAT_OK;
+}
+
+int fstat_batch_compute_one(fstat_ctx* c, int32_t wu, void* cuda_stream) {
+    if (!c) return FSTAT_EINVAL;
+    if (wu < 0 || wu >= (int)c->wus.size()) return fail(c, FSTAT_EINVAL, "no workunit %d", wu);
+    int rc = fstat_compute(c->wus[wu], cuda_stream);
+    if (rc != FSTAT_OK) return fail(c, rc, "%s", c->wus[wu]->err.c_str());
+    return FSTAT_OK;
+}
+
+int fstat_batch_get_toplist(fstat_ctx* c, int32_t wu, int32_t k, int64_t* idx, float* twoF) {
+    if (!c) return FSTAT_EINVAL;
+    if (wu < 0 || wu >= (int)c->wus.size()) return fail(c, FSTAT_EINVAL, "no workunit %d", wu);
+    int rc = fstat_get_toplist(c->wus[wu], k, idx, twoF);
+    if (rc != FSTAT_OK) return fail(c, rc, "%s", c->wus[wu]->err.c_str());
+    return FSTAT_OK;
+}
+
+int fstat_batch_get_2f(fstat_ctx* c, int32_t wu, float* out, int64_t offset, int64_t count, int32_t mem) {
+    if (!c) return FSTAT_EINVAL;
+    if (wu < 0 || wu >= (int)c->wus.size()) return fail(c, FSTAT_EINVAL, "no workunit %d", wu);
+    int rc = fstat_get_2f(c->wus[wu], out, offset, count, mem);
+    if (rc != FSTAT_OK) return fail(c, rc, "%s", c->wus[wu]->err.c_str());
+    return FSTAT_OK;
+}
+
+int fstat_batch_get_times(fstat_ctx* c, double* wu_done_ms, double* total_ms) {
+    if (!c || !total_ms) return FSTAT_EINVAL;
+    if (c->wus.empty() || !c->bev1) return fail(c, FSTAT_ESTATE, "no batch computed");
+    if (set_device(c) != FSTAT_OK) return FSTAT_ECUDA;
+    CUDA_TRY(c, cudaEventSynchronize(c->bev1));
+    float ms = 0.f;
+    CUDA_TRY(c, cudaEventElapsedTime(&ms, c->bev0, c->bev1));
+    *total_ms = ms;
+    if (wu_done_ms) {
+        const int n = (int)c->wus.size();
+        std::vector<unsigned long long> t(n + 1);
+        CUDA_TRY(c, cudaMemcpy(t.data(), c->d_done, sizeof(unsigned long long) * (n + 1), cudaMemcpyDeviceToHost));
+        for (int k = 0; k < n; ++k) {
+            const int i = k < (int)c->batch_order.size() ? c->batch_order[k] : k;
+            wu_done_ms[i] = t[k] >= t[n] ? (double)(t[k] - t[n]) * 1e-6 : 0.0;
+        }
+    }
     return FSTAT_OK;
 }
 

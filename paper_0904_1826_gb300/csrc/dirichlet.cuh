@@ -166,9 +166,13 @@ __device__ __forceinline__ void accumulate(float tw_re, float tw_im, float sk, f
     fb = __ffma2_rn(b2, z, fb);
 }
 
-// DV = D (compile time) or 0 (D taken from the runtime argument, M = 1).
+// One thread block's work item: block index `bid` of the grid that covers
+// (sky, column, chunk) of one template bank.  DV = D (compile time) or 0 (D
+// taken from the runtime argument, M = 1).  Every exit is block-uniform
+// except the final per-thread epilogue, so callers may loop over items.
 template <int DV, int M, int L, int FORM, bool KAHAN>
-__global__ void __launch_bounds__(kMaxThreads, 2) dirichlet_kernel(const DirichletParams p, const int d_rt) {
+__device__ __forceinline__ void dirichlet_block(const DirichletParams& p, const int d_rt, long long bid,
+                                                unsigned char* smem) {
     using RT = RawT<FORM>;
     using Raw = typename RT::T;
     constexpr int G = RT::G;
@@ -176,7 +180,6 @@ __global__ void __launch_bounds__(kMaxThreads, 2) dirichlet_kernel(const Dirichl
     const int D = DV ? DV : d_rt;
     const int NT = blockDim.x;
     const int C = p.sft_chunk;
-    extern __shared__ __align__(16) unsigned char smem[];
     const DirSmem lay = dirichlet_smem(C, p.w_tab, p.w_raw, p.n_fdot, (int)sizeof(Raw));
     float4* s_tab = reinterpret_cast<float4*>(smem + lay.pairs);            // [C][w_tab]
     Raw* s_raw = reinterpret_cast<Raw*>(smem + lay.raw);                    // [2][C][w_raw]
@@ -185,7 +188,6 @@ __global__ void __launch_bounds__(kMaxThreads, 2) dirichlet_kernel(const Dirichl
     unsigned int* s_ph0 = reinterpret_cast<unsigned int*>(smem + lay.ph0);  // [3][C][n_fdot]
     int* s_lo = reinterpret_cast<int*>(smem + lay.lo);                      // [2][C][2]: window base, raw start
 
-    long long bid = blockIdx.x;
     const int chunk = (int)(bid % p.chunks_per_col);
     bid /= p.chunks_per_col;
     const int col = (int)(bid % p.n_col);
@@ -393,6 +395,57 @@ __global__ void __launch_bounds__(kMaxThreads, 2) dirichlet_kernel(const Dirichl
     }
 }
 
+template <int DV, int M, int L, int FORM, bool KAHAN>
+__global__ void __launch_bounds__(kMaxThreads, 2) dirichlet_kernel(const DirichletParams p, const int d_rt) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    dirichlet_block<DV, M, L, FORM, KAHAN>(p, d_rt, (long long)blockIdx.x, smem);
+}
+
+// Persistent form over many template banks (workunits): every block takes
+// the next item from a device queue until all items of all banks are done.
+// item_prefix[w] is the first item of bank w (item_prefix[n_wu] = total);
+// the block that completes a bank's last item stamps its completion time.
+// The loop ends after at most `total` items per block; nothing waits on
+// another block.
+template <int DV, int M, int L, int FORM, bool KAHAN>
+__global__ void __launch_bounds__(kMaxThreads, 2)
+    dirichlet_batch_kernel(const DirichletParams* __restrict__ banks, const long long* __restrict__ item_prefix,
+                           int n_wu, unsigned long long* __restrict__ queue, int* __restrict__ remaining,
+                           unsigned long long* __restrict__ done_ns, const int d_rt) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ long long s_item;
+    __shared__ int s_wu;
+    const long long total = item_prefix[n_wu];
+    for (long long guard = 0; guard <= total; ++guard) {
+        __syncthreads();   // previous item fully consumed (shared memory free)
+        if (threadIdx.x == 0) {
+            const long long it = (long long)atomicAdd(queue, 1ULL);
+            int lo = 0, hi = n_wu;   // last bank with item_prefix <= it
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (item_prefix[mid] <= it) lo = mid; else hi = mid;
+            }
+            s_item = it;
+            s_wu = lo;
+        }
+        __syncthreads();
+        const long long it = s_item;
+        if (it >= total) break;
+        const int w = s_wu;
+        const DirichletParams p = banks[w];
+        dirichlet_block<DV, M, L, FORM, KAHAN>(p, d_rt, it - item_prefix[w], smem);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            if (atomicSub(&remaining[w], 1) == 1) {
+                unsigned long long t;
+                asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+                done_ns[w] = t;
+            }
+        }
+    }
+}
+
 // Compiled variants: (ID, D, M, L, KAHAN); D = 0 takes D at run time.
 #define FS_DIRICHLET_VARIANTS(X) \
     X(0, 8, 9, 2, false)          \
@@ -406,6 +459,43 @@ __global__ void __launch_bounds__(kMaxThreads, 2) dirichlet_kernel(const Dirichl
     X(8, 8, 1, 1, true)           \
     X(9, 0, 1, 1, false)          \
     X(10, 0, 1, 1, true)
+
+template <int FORM>
+cudaError_t launch_dirichlet_batch_form(int v, const DirichletBatch& b, int d_rt, int threads, size_t smem,
+                                        int grid, cudaStream_t s) {
+    switch (v) {
+#define FS_BCASE(ID, D_, M_, L_, K_)                                                                      \
+    case ID: {                                                                                            \
+        auto fn = dirichlet_batch_kernel<D_, M_, L_, FORM, K_>;                                           \
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        if (e != cudaSuccess) return e;                                                                   \
+        fn<<<grid, threads, smem, s>>>(b.banks, b.item_prefix, b.n_wu, b.queue, b.remaining, b.done_ns,   \
+                                       d_rt);                                                             \
+        return cudaGetLastError();                                                                        \
+    }
+        FS_DIRICHLET_VARIANTS(FS_BCASE)
+#undef FS_BCASE
+        default:
+            return cudaErrorInvalidValue;
+    }
+}
+
+template <int FORM>
+cudaError_t dirichlet_occupancy_form(int v, int threads, size_t smem, int* blocks_per_sm) {
+    switch (v) {
+#define FS_OCASE(ID, D_, M_, L_, K_)                                                                          \
+    case ID: {                                                                                                \
+        auto fn = dirichlet_batch_kernel<D_, M_, L_, FORM, K_>;                                               \
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);     \
+        if (e != cudaSuccess) return e;                                                                       \
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, threads, smem);               \
+    }
+        FS_DIRICHLET_VARIANTS(FS_OCASE)
+#undef FS_OCASE
+        default:
+            return cudaErrorInvalidValue;
+    }
+}
 
 template <int FORM>
 cudaError_t launch_dirichlet_form(int v, const DirichletParams& p, int d_rt, int threads, size_t smem,

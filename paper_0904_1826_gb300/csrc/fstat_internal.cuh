@@ -93,6 +93,16 @@ __host__ __device__ inline DirSmem dirichlet_smem(int sft_chunk, int w_tab, int 
     return m;
 }
 
+// Device-side description of a batch of template banks for the persistent kernel.
+struct DirichletBatch {
+    const DirichletParams* banks;     // [n_wu]
+    const long long* item_prefix;     // [n_wu + 1]
+    int n_wu;
+    unsigned long long* queue;        // work counter (zeroed per launch)
+    int* remaining;                   // [n_wu] items left per bank
+    unsigned long long* done_ns;      // [n_wu] completion time (globaltimer)
+};
+
 struct TimingParams {
     const SftState* st;        // [n_sft]
     const double* sky;         // [n_sky][2]
