@@ -84,9 +84,13 @@ struct fstat_ctx {
     double* d_sky = nullptr;
     double* d_fdot = nullptr;
     std::vector<double> h_sky, h_fdot;
+    bool fdot_uniform = true;         // spindowns fdot_0 + d * dfdot (compact bases)
+    double dfdot = 0.0;
     // derived per-bank buffers
     size_t cap_meta = 0, cap_kh0 = 0, cap_ph0 = 0, cap_abcd = 0, cap_comb = 0, cap_twoF = 0;
     SkySftMeta* d_meta = nullptr;
+    SkySftBase* d_base = nullptr;
+    size_t cap_base = 0;
     long long* d_kh0 = nullptr;
     unsigned int* d_ph0 = nullptr;
     double* d_abcd = nullptr;
@@ -435,7 +439,7 @@ void fstat_destroy(fstat_ctx* c) {
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->bev0) cudaEventDestroy(c->bev0);
     if (c->bev1) cudaEventDestroy(c->bev1);
-    void* ptrs[] = {c->d_bins, c->d_bins16, c->d_scale, c->d_state, c->d_tstart, c->d_det_of, c->d_sky,
+    void* ptrs[] = {c->d_base, c->d_bins, c->d_bins16, c->d_scale, c->d_state, c->d_tstart, c->d_det_of, c->d_sky,
                     c->d_fdot, c->d_meta, c->d_kh0, c->d_ph0, c->d_abcd, c->d_comb, c->d_twoF, c->d_err,
                     c->tw.hist, c->tw.state, c->tw.tie_count, c->tw.cand_idx, c->tw.cand_val, c->tw.n_cand,
                     c->tw.out_idx, c->tw.out_val, c->d_inj_work, c->d_sig};
@@ -583,6 +587,13 @@ int fstat_set_templates(fstat_ctx* c, const double* sky, int32_t n_sky, double f
     c->n_sky = n_sky;
     c->n_f = n_f;
     c->n_fdot = n_fdot;
+    // a uniform spindown grid gets compact per-(sky, SFT) bases
+    c->dfdot = n_fdot > 1 ? (fdot[n_fdot - 1] - fdot[0]) / (n_fdot - 1) : 0.0;
+    c->fdot_uniform = true;
+    double fmax = 0.0;
+    for (int d = 0; d < n_fdot; ++d) fmax = std::max(fmax, std::fabs(fdot[d]));
+    for (int d = 0; d < n_fdot; ++d)
+        if (std::fabs(fdot[d] - (fdot[0] + d * c->dfdot)) > 1e-12 * fmax) c->fdot_uniform = false;
     c->f0 = f0;
     c->df = df;
     c->t_ref = t_ref;
@@ -606,8 +617,12 @@ int prepare(fstat_ctx* c, cudaStream_t s) {
     const size_t n_base = n_meta * c->n_fdot;
     const size_t n_twoF = (size_t)c->n_sky * c->n_fdot * c->n_f;
     if ((rc = grow(c, &c->d_meta, c->cap_meta, n_meta)) != FSTAT_OK) return rc;
-    if ((rc = grow(c, &c->d_kh0, c->cap_kh0, n_base)) != FSTAT_OK) return rc;
-    if ((rc = grow(c, &c->d_ph0, c->cap_ph0, n_base)) != FSTAT_OK) return rc;
+    if (c->fdot_uniform) {
+        if ((rc = grow(c, &c->d_base, c->cap_base, n_meta)) != FSTAT_OK) return rc;
+    } else {
+        if ((rc = grow(c, &c->d_kh0, c->cap_kh0, n_base)) != FSTAT_OK) return rc;
+        if ((rc = grow(c, &c->d_ph0, c->cap_ph0, n_base)) != FSTAT_OK) return rc;
+    }
     if ((rc = grow(c, &c->d_abcd, c->cap_abcd, 4 * (size_t)c->n_sky)) != FSTAT_OK) return rc;
     if ((rc = grow(c, &c->d_comb, c->cap_comb, (size_t)c->n_sky)) != FSTAT_OK) return rc;
     if ((rc = grow(c, &c->d_twoF, c->cap_twoF, n_twoF)) != FSTAT_OK) return rc;
@@ -631,9 +646,12 @@ TimingParams timing_params(const fstat_ctx* c, int n_sky) {
     tp.P = c->plan.P;
     tp.L = c->plan.L;
     tp.M = c->plan.M;
+    tp.uniform = c->fdot_uniform ? 1 : 0;
+    tp.dfdot = c->dfdot;
     tp.meta = c->d_meta;
-    tp.kh0 = c->d_kh0;
-    tp.ph0 = c->d_ph0;
+    tp.base = c->fdot_uniform ? c->d_base : nullptr;
+    tp.kh0 = c->fdot_uniform ? nullptr : c->d_kh0;
+    tp.ph0 = c->fdot_uniform ? nullptr : c->d_ph0;
     tp.abcd = c->d_abcd;
     tp.comb = c->d_comb;
     tp.err = c->d_err;
@@ -649,8 +667,9 @@ DirichletParams dirichlet_params(const fstat_ctx* c) {
     dp.n_bins = c->n_bins;
     dp.n_sft = c->n_sft;
     dp.meta = c->d_meta;
-    dp.kh0 = c->d_kh0;
-    dp.ph0 = c->d_ph0;
+    dp.base = c->fdot_uniform ? c->d_base : nullptr;
+    dp.kh0 = c->fdot_uniform ? nullptr : c->d_kh0;
+    dp.ph0 = c->fdot_uniform ? nullptr : c->d_ph0;
     dp.comb = c->d_comb;
     dp.twoF = c->d_twoF;
     dp.n_sky = c->n_sky;

@@ -184,6 +184,7 @@ __device__ __forceinline__ void dirichlet_block(const DirichletParams& p, const 
     float4* s_tab = reinterpret_cast<float4*>(smem + lay.pairs);            // [C][w_tab]
     Raw* s_raw = reinterpret_cast<Raw*>(smem + lay.raw);                    // [2][C][w_raw]
     SkySftMeta* s_meta = reinterpret_cast<SkySftMeta*>(smem + lay.meta);    // [3][C]
+    SkySftBase* s_base = reinterpret_cast<SkySftBase*>(smem + lay.base);    // [3][C]
     long long* s_kh0 = reinterpret_cast<long long*>(smem + lay.kh0);        // [3][C][n_fdot]
     unsigned int* s_ph0 = reinterpret_cast<unsigned int*>(smem + lay.ph0);  // [3][C][n_fdot]
     int* s_lo = reinterpret_cast<int*>(smem + lay.lo);                      // [2][C][2]: window base, raw start
@@ -229,6 +230,12 @@ __device__ __forceinline__ void dirichlet_block(const DirichletParams& p, const 
         const char* msrc = reinterpret_cast<const char*>(p.meta + meta0 + a0);
         char* mdst = reinterpret_cast<char*>(s_meta + slot * C);
         for (int t = threadIdx.x; t < nc * 3; t += NT) cp_async16(mdst + 16 * t, msrc + 16 * t, 16);
+        if (p.base) {   // uniform spindown grid: two 16-byte halves per SFT
+            const char* bsrc = reinterpret_cast<const char*>(p.base + meta0 + a0);
+            char* bdst = reinterpret_cast<char*>(s_base + slot * C);
+            for (int t = threadIdx.x; t < nc * 2; t += NT) cp_async16(bdst + 16 * t, bsrc + 16 * t, 16);
+            return;
+        }
         for (int t = threadIdx.x; t < nc * n_rows; t += NT) {
             const int c = t / n_rows, rr = t - c * n_rows;
             const size_t o = base0 + (size_t)(d_lo + rr) * p.n_sft + a0 + c;
@@ -311,9 +318,18 @@ __device__ __forceinline__ void dirichlet_block(const DirichletParams& p, const 
         // their reciprocal-heavy and multiply-add-heavy phases interleave
         for (int c = 0; c < (warp_live ? nc : 0); ++c) {
             const SkySftMeta m = s_meta[cslot * C + c];
-            const long long kh = s_kh0[(cslot * C + c) * p.n_fdot + row_i] + (long long)j_t * m.dk;
+            long long kh_row;
+            unsigned int ph0;
+            if (p.base) {
+                const SkySftBase bs = s_base[cslot * C + c];
+                kh_row = bs.kh0 + (long long)drow * bs.dkh;
+                ph0 = bs.ph0 + (unsigned int)drow * bs.dph;
+            } else {
+                kh_row = s_kh0[(cslot * C + c) * p.n_fdot + row_i];
+                ph0 = s_ph0[(cslot * C + c) * p.n_fdot + row_i];
+            }
+            const long long kh = kh_row + (long long)j_t * m.dk;
             const int k0 = (int)(kh >> 32);
-            const unsigned int ph0 = s_ph0[(cslot * C + c) * p.n_fdot + row_i];
             const int lo_rel = s_lo[(lslot * C + c) * 2];
             const int b = (k0 - (int)p.k_lo) - (D - 1) - lo_rel;   // first pair of template 0
             const float4* tab = s_tab + (size_t)c * p.w_tab;

@@ -173,15 +173,28 @@ __global__ void __launch_bounds__(kTimingBlock) timing_kernel(const TimingParams
         m.a = (float)(a * sc);
         m.b = (float)(b * sc);
         long long khmin = 0x7fffffffffffffffLL;
-        for (int d = 0; d < p.n_fdot; ++d) {
-            const double fd = p.fdot[d];
-            const double khat0 = (p.f0 + fd * dtau) * tdot * p.T;
-            const double cyc0 = p.f0 * dtau + 0.5 * fd * dtau * dtau;
-            const size_t o = ((size_t)sky * p.n_fdot + d) * p.n_sft + i;
-            const long long kfx = bin_fx(khat0);
-            p.kh0[o] = kfx;
-            p.ph0[o] = frac_fx32(cyc0);
-            khmin = kfx < khmin ? kfx : khmin;
+        if (p.uniform) {
+            const double fd = p.fdot[0];
+            SkySftBase bs;
+            bs.kh0 = bin_fx((p.f0 + fd * dtau) * tdot * p.T);
+            bs.dkh = llrint(p.dfdot * dtau * tdot * p.T * kTwo32);
+            bs.ph0 = frac_fx32(p.f0 * dtau + 0.5 * fd * dtau * dtau);
+            bs.dph = frac_fx32(0.5 * p.dfdot * dtau * dtau);
+            bs.pad0 = bs.pad1 = 0u;
+            p.base[(size_t)sky * p.n_sft + i] = bs;
+            const long long last = bs.kh0 + (long long)(p.n_fdot - 1) * bs.dkh;
+            khmin = bs.kh0 < last ? bs.kh0 : last;
+        } else {
+            for (int d = 0; d < p.n_fdot; ++d) {
+                const double fd = p.fdot[d];
+                const double khat0 = (p.f0 + fd * dtau) * tdot * p.T;
+                const double cyc0 = p.f0 * dtau + 0.5 * fd * dtau * dtau;
+                const size_t o = ((size_t)sky * p.n_fdot + d) * p.n_sft + i;
+                const long long kfx = bin_fx(khat0);
+                p.kh0[o] = kfx;
+                p.ph0[o] = frac_fx32(cyc0);
+                khmin = kfx < khmin ? kfx : khmin;
+            }
         }
         m.khmin = khmin;
         p.meta[(size_t)sky * p.n_sft + i] = m;

@@ -50,6 +50,16 @@ struct __align__(16) SkySftMeta {
 };
 static_assert(sizeof(SkySftMeta) == 48, "SkySftMeta layout");
 
+// Bases of a uniform spindown grid fdot_d = fdot_0 + d * dfdot, per (sky, SFT):
+//   khat0(d) = kh0 + d * dkh   (32.32 fixed-point bins)
+//   Phi0(d)  = ph0 + d * dph   (0.32 fixed-point cycles, wraps mod 1)
+struct __align__(16) SkySftBase {
+    long long kh0, dkh;
+    unsigned int ph0, dph;
+    unsigned int pad0, pad1;
+};
+static_assert(sizeof(SkySftBase) == 32, "SkySftBase layout");
+
 struct DirichletParams {
     const void* bins;          // [n_sft][row] complex64 (float2) or 16-bit (half2 / bf162)
     long long row;             // elements per stored SFT row (>= n_bins, padded)
@@ -57,8 +67,9 @@ struct DirichletParams {
     int n_bins;                // valid bins per row
     int n_sft;
     const SkySftMeta* meta;    // [n_sky][n_sft]
-    const long long* kh0;      // [n_sky][n_fdot][n_sft]
-    const unsigned int* ph0;   // [n_sky][n_fdot][n_sft]
+    const long long* kh0;      // [n_sky][n_fdot][n_sft] (any spindown list) or null
+    const unsigned int* ph0;   // [n_sky][n_fdot][n_sft] or null
+    const SkySftBase* base;    // [n_sky][n_sft] (uniform spindown grid) or null
     const float4* comb;        // [n_sky] (2B/D, 2A/D, -4C/D, valid)
     float* twoF;               // [n_sky][n_fdot][n_f]
     int n_sky, n_fdot, n_f;
@@ -76,7 +87,7 @@ struct DirichletParams {
 
 // Shared-memory layout of the Dirichlet kernel (offsets in bytes).
 struct DirSmem {
-    size_t pairs, raw, meta, kh0, ph0, lo, total;
+    size_t pairs, raw, meta, base, kh0, ph0, lo, total;
 };
 __host__ __device__ inline size_t smem_align16(size_t x) { return (x + 15) & ~(size_t)15; }
 __host__ __device__ inline DirSmem dirichlet_smem(int sft_chunk, int w_tab, int w_raw, int n_fdot,
@@ -86,7 +97,8 @@ __host__ __device__ inline DirSmem dirichlet_smem(int sft_chunk, int w_tab, int 
     m.pairs = 0;                                                           // float4 pair table [C][w_tab]
     m.raw = smem_align16(m.pairs + C * w_tab * 16);                        // [2][C][w_raw] raw bins
     m.meta = smem_align16(m.raw + 2 * C * w_raw * raw_elem_bytes);         // [3][C] constants
-    m.kh0 = smem_align16(m.meta + 3 * C * sizeof(SkySftMeta));             // [3][C][n_fdot]
+    m.base = smem_align16(m.meta + 3 * C * sizeof(SkySftMeta));            // [3][C] uniform-grid bases
+    m.kh0 = smem_align16(m.base + 3 * C * sizeof(SkySftBase));             // [3][C][n_fdot]
     m.ph0 = smem_align16(m.kh0 + 3 * C * n_fdot * 8);                      // [3][C][n_fdot]
     m.lo = smem_align16(m.ph0 + 3 * C * n_fdot * 4);                       // [2][C][2]
     m.total = smem_align16(m.lo + 2 * C * 8);
@@ -111,9 +123,12 @@ struct TimingParams {
     int n_sky, n_sft, n_fdot;
     double f0, df, T, t_ref;
     int P, L, M;
+    int uniform;               // spindowns fdot_0 + d * dfdot: write `base`, else kh0 / ph0
+    double dfdot;
     SkySftMeta* meta;          // out [n_sky][n_sft]
-    long long* kh0;            // out [n_sky][n_fdot][n_sft]
-    unsigned int* ph0;         // out [n_sky][n_fdot][n_sft]
+    SkySftBase* base;          // out [n_sky][n_sft] (uniform)
+    long long* kh0;            // out [n_sky][n_fdot][n_sft] (not uniform)
+    unsigned int* ph0;         // out [n_sky][n_fdot][n_sft] (not uniform)
     double* abcd;              // out [n_sky][4]
     float4* comb;              // out [n_sky]
     int* err;

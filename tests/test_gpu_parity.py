@@ -279,3 +279,15 @@ def test_device_pointer_input_matches_host(lib):
         np.testing.assert_array_equal(out.cpu().numpy(), host["twoF"])
     finally:
         g.close()
+
+
+def test_nonuniform_unsorted_spindowns(lib):
+    """A spindown list that is not an arithmetic grid (and not sorted) takes the
+    per-(sky, spindown, SFT) bases; a uniform one the compact per-(sky, SFT) bases."""
+    w = config_mid(n_f=80, n_fdot=3, n_sky=3)
+    w.bank.fdot = np.array([-7e-10, 0.0, -2e-10])
+    bins = _oracle_bins(w)
+    ref = O.compute_fstat_freq_band(_dets(w, bins), w.T, w.k_lo, w.dterms, w.bank).ravel()
+    out = _gpu(lib, w, bins)
+    assert out["flags"] == 0
+    _assert_parity(out["twoF"], ref, "non-uniform fdot")
