@@ -14,3 +14,5 @@ Pinned functions (see tests/test_oracle_pins.py):
   * the MLP forward/backward                       -- central finite differences.
 """
 from . import fstat_oracle  # noqa: F401
+from . import mlp_oracle  # noqa: F401
+from . import quantize  # noqa: F401
