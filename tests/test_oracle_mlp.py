@@ -24,7 +24,7 @@ def test_gradients_match_central_finite_differences():
     checked = 0
     for k in MO.NAMES:
         flat = p[k].reshape(-1)
-        for i in rng.choice(flat.size, size=min(flat.size, 25), replace=False):
+        for i in rng.choice(flat.size, size=min(flat.size, 30), replace=False):
             old = flat[i]
             flat[i] = old + h
             lp = MO.loss(p, X, y, 3.0)
