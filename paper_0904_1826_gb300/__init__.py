@@ -88,6 +88,17 @@ SIGNATURES = {
     "fstat_batch_get_toplist": (ctypes.c_int, [_P, _I32, _I32, _P, _P]),
     "fstat_batch_get_2f": (ctypes.c_int, [_P, _I32, _P, _I64, _I64, _I32]),
     "fstat_batch_get_times": (ctypes.c_int, [_P, _P, ctypes.POINTER(_D)]),
+    "fstat_extract_patches": (ctypes.c_int, [_P, _I32, _I32, _I32, _I32, _I32, _P, _I32, ctypes.c_float,
+                                             ctypes.c_float, _P]),
+    # include/fstat_mlp.h
+    "fstat_mlp_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, _I32, _I32, _I32]),
+    "fstat_mlp_destroy": (None, [_P]),
+    "fstat_mlp_last_error": (ctypes.c_char_p, [_P]),
+    "fstat_mlp_set_params": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
+    "fstat_mlp_get_params": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
+    "fstat_mlp_forward": (ctypes.c_int, [_P, _P, _I32, _P, _I32, _P]),
+    "fstat_mlp_train_step": (ctypes.c_int, [_P, _P, _P, _I32, ctypes.c_float, ctypes.c_float, _P, _I32, _P]),
+    "fstat_mlp_get_grads": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
 }
 
 
@@ -326,6 +337,92 @@ def fstat_batch_get_times(ctx, n_wu: int):
     tot = _D()
     _check(ctx, _lib.fstat_batch_get_times(ctx, _host_ptr(done), ctypes.byref(tot)))
     return done, float(tot.value)
+
+
+def fstat_extract_patches(ctx, n_a: int, n_d: int, s_a: int, s_d: int, n_fp: int, f_start, shift: float,
+                          scale: float, out) -> None:
+    """out: torch CUDA tensor (int16/uint16/bfloat16) of [n_patches, s_a*s_d*n_fp] elements."""
+    fst = np.ascontiguousarray(f_start, dtype=np.int32)
+    _check(ctx, _lib.fstat_extract_patches(ctx, n_a, n_d, s_a, s_d, n_fp, _host_ptr(fst), fst.size, shift, scale,
+                                           ctypes.c_void_p(out.data_ptr())))
+
+
+MLP_NAMES = ("W1", "b1", "W2", "b2", "w3", "b3")
+
+
+def _mlp_check(m, rc):
+    if rc != FSTAT_OK:
+        raise FstatError(rc, (_lib.fstat_mlp_last_error(m) or b"").decode())
+
+
+class MLP:
+    """The patch-scoring network (include/fstat_mlp.h)."""
+
+    def __init__(self, n_in: int, n_hidden: int, max_batch: int, device: int = 0):
+        self.n_in, self.H, self.max_batch = n_in, n_hidden, max_batch
+        h = _P()
+        _check(None, _lib.fstat_mlp_create(ctypes.byref(h), device, n_in, n_hidden, max_batch))
+        self.h = h
+
+    def close(self):
+        if self.h:
+            _lib.fstat_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _shapes(self):
+        I, H = self.n_in, self.H
+        return {"W1": (I, H), "b1": (H,), "W2": (H, H), "b2": (H,), "w3": (H,), "b3": (1,)}
+
+    def set_params(self, p: dict) -> None:
+        arrs = [np.ascontiguousarray(np.asarray(p[k], dtype=np.float32).reshape(self._shapes()[k])) for k in MLP_NAMES]
+        _mlp_check(self.h, _lib.fstat_mlp_set_params(self.h, *[_host_ptr(a) for a in arrs]))
+
+    def get_params(self) -> dict:
+        out = {k: np.empty(s, dtype=np.float32) for k, s in self._shapes().items()}
+        _mlp_check(self.h, _lib.fstat_mlp_get_params(self.h, *[_host_ptr(out[k]) for k in MLP_NAMES]))
+        return out
+
+    def get_grads(self) -> dict:
+        out = {k: np.empty(s, dtype=np.float32) for k, s in self._shapes().items()}
+        _mlp_check(self.h, _lib.fstat_mlp_get_grads(self.h, *[_host_ptr(out[k]) for k in MLP_NAMES]))
+        return out
+
+    def forward(self, X, stream=None):
+        """X: numpy uint16 (BF16 bits) [B, n_in] or a torch CUDA tensor (16-bit) -> logits."""
+        if _is_cuda_tensor(X):
+            import torch
+            B = int(X.shape[0])
+            out = torch.empty(B, dtype=torch.float32, device=X.device)
+            _mlp_check(self.h, _lib.fstat_mlp_forward(self.h, ctypes.c_void_p(X.data_ptr()), B,
+                                                      ctypes.c_void_p(out.data_ptr()), FSTAT_MEM_DEVICE,
+                                                      _stream_handle(stream)))
+            return out
+        Xh = np.ascontiguousarray(X, dtype=np.uint16)
+        out = np.empty(Xh.shape[0], dtype=np.float32)
+        _mlp_check(self.h, _lib.fstat_mlp_forward(self.h, _host_ptr(Xh), Xh.shape[0], _host_ptr(out),
+                                                  FSTAT_MEM_HOST, _stream_handle(stream)))
+        return out
+
+    def train_step(self, X, y, pos_weight: float, lr: float, stream=None, want_loss: bool = True):
+        lv = ctypes.c_float()
+        lp = ctypes.byref(lv) if want_loss else None
+        if _is_cuda_tensor(X):
+            _mlp_check(self.h, _lib.fstat_mlp_train_step(self.h, ctypes.c_void_p(X.data_ptr()),
+                                                         ctypes.c_void_p(y.data_ptr()), int(X.shape[0]),
+                                                         pos_weight, lr, lp, FSTAT_MEM_DEVICE,
+                                                         _stream_handle(stream)))
+        else:
+            Xh = np.ascontiguousarray(X, dtype=np.uint16)
+            yh = np.ascontiguousarray(y, dtype=np.float32)
+            _mlp_check(self.h, _lib.fstat_mlp_train_step(self.h, _host_ptr(Xh), _host_ptr(yh), Xh.shape[0],
+                                                         pos_weight, lr, lp, FSTAT_MEM_HOST, _stream_handle(stream)))
+        return float(lv.value) if want_loss else None
 
 
 def fstat_take_kernel_time(ctx):

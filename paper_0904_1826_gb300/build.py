@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfstat.so")
-SOURCES = ["api.cu", "ephemeris.cu", "toplist.cu", "dirichlet_c64.cu", "dirichlet_f16.cu", "dirichlet_bf16.cu"]
+SOURCES = ["api.cu", "ephemeris.cu", "toplist.cu", "mlp.cu", "dirichlet_c64.cu", "dirichlet_f16.cu", "dirichlet_bf16.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 
@@ -25,7 +25,8 @@ def nvcc() -> str:
 
 def _deps_mtime() -> float:
     paths = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
-    paths.append(os.path.join(os.path.dirname(HERE), "include", "fstat.h"))
+    inc = os.path.join(os.path.dirname(HERE), "include")
+    paths += [os.path.join(inc, f) for f in os.listdir(inc)]
     return max(os.path.getmtime(p) for p in paths)
 
 

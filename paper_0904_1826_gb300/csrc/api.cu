@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "fstat_internal.cuh"
+#include "../../include/fstat_mlp.h"
 
 namespace fs {
 cudaError_t launch_dirichlet_c64(int v, const DirichletParams& p, int d_rt, int threads, size_t smem,
@@ -129,6 +130,8 @@ struct fstat_ctx {
     cudaEvent_t bev0 = nullptr, bev1 = nullptr;
     long long launches_per_graph = 0;
     std::vector<int> batch_order;     // grouped position -> workunit index
+    int* d_fstart = nullptr;          // patch frequency starts
+    size_t cap_fstart = 0;
 };
 
 namespace {
@@ -439,7 +442,7 @@ void fstat_destroy(fstat_ctx* c) {
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->bev0) cudaEventDestroy(c->bev0);
     if (c->bev1) cudaEventDestroy(c->bev1);
-    void* ptrs[] = {c->d_base, c->d_bins, c->d_bins16, c->d_scale, c->d_state, c->d_tstart, c->d_det_of, c->d_sky,
+    void* ptrs[] = {c->d_fstart, c->d_base, c->d_bins, c->d_bins16, c->d_scale, c->d_state, c->d_tstart, c->d_det_of, c->d_sky,
                     c->d_fdot, c->d_meta, c->d_kh0, c->d_ph0, c->d_abcd, c->d_comb, c->d_twoF, c->d_err,
                     c->tw.hist, c->tw.state, c->tw.tie_count, c->tw.cand_idx, c->tw.cand_val, c->tw.n_cand,
                     c->tw.out_idx, c->tw.out_val, c->d_inj_work, c->d_sig};
@@ -1263,6 +1266,31 @@ int fstat_batch_get_times(fstat_ctx* c, double* wu_done_ms, double* total_ms) {
             wu_done_ms[i] = t[k] >= t[n] ? (double)(t[k] - t[n]) * 1e-6 : 0.0;
         }
     }
+    return FSTAT_OK;
+}
+
+
+int fstat_extract_patches(fstat_ctx* c, int32_t n_a, int32_t n_d, int32_t s_a, int32_t s_d, int32_t n_fp,
+                          const int32_t* f_start, int32_t n_q, float shift, float scale, uint16_t* out) {
+    if (!c || !f_start || !out) return FSTAT_EINVAL;
+    c->err.clear();
+    if (!c->computed) return fail(c, FSTAT_ESTATE, "nothing computed");
+    if (c->n_fdot != 1) return fail(c, FSTAT_EINVAL, "patches need a bank with one spindown");
+    if (n_a < 1 || n_d < 1 || s_a < 1 || s_d < 1 || n_a % s_a || n_d % s_d || (long long)n_a * n_d != c->n_sky)
+        return fail(c, FSTAT_EINVAL, "sky grid %d x %d does not tile the bank's %d sky points", n_a, n_d, c->n_sky);
+    if (n_fp < 1 || n_q < 1) return fail(c, FSTAT_EINVAL, "empty patch");
+    for (int q = 0; q < n_q; ++q)
+        if (f_start[q] < 0 || f_start[q] + n_fp > c->n_f) return fail(c, FSTAT_EINVAL, "frequency patch %d outside the band", q);
+    if (set_device(c) != FSTAT_OK) return FSTAT_ECUDA;
+    int rc = grow(c, &c->d_fstart, c->cap_fstart, (size_t)n_q);
+    if (rc != FSTAT_OK) return rc;
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_fstart, f_start, sizeof(int) * n_q, cudaMemcpyHostToDevice, c->stream));
+    const int n_pd = n_d / s_d;
+    const int n_patches = (n_a / s_a) * n_pd * n_q;
+    CUDA_TRY(c, launch_patches(c->d_twoF, c->n_f, n_d, s_a, s_d, n_fp, c->d_fstart, n_q, n_patches, n_pd, shift, scale,
+                               out, c->stream));
+    c->launches += 1;
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));   // f_start is a caller buffer
     return FSTAT_OK;
 }
 

@@ -1,0 +1,514 @@
+// Patch-scoring network of the learned-proposal search: BF16 tensor-core
+// matrix products (mma.sync m16n8k16, FP32 accumulation) for the two hidden
+// layers forward and backward, FP32 output layer, loss and Adam.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/fstat_mlp.h"
+#include "fstat_internal.cuh"
+
+using bf16 = __nv_bfloat16;
+
+namespace fs {
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 32, KPAD = 8;
+
+__device__ __forceinline__ unsigned int ld_pair(const bf16* p) { return *reinterpret_cast<const unsigned int*>(p); }
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned int (&a)[4], const unsigned int (&b)[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+enum { EPI_F32 = 0, EPI_RELU = 1, EPI_MASK = 2 };
+
+// C(m, n) = sum_k A(m, k) B(k, n) (+ bias(n)), A(m, k) = TA ? A[k lda + m] : A[m lda + k],
+// B(k, n) = TB ? B[n ldb + k] : B[k ldb + n]; K, lda, ldb multiples of 8.
+// EPI_F32: Cf = C.  EPI_RELU: Cf = C (pre-activation), Cb = bf16(max(C, 0)).
+// EPI_MASK: C *= (zref > 0); Cf = C, Cb = bf16(C).
+template <bool TA, bool TB, int EPI>
+__global__ void __launch_bounds__(128) gemm_bf16_kernel(int M, int N, int K, const bf16* __restrict__ A, int lda,
+                                                        const bf16* __restrict__ B, int ldb,
+                                                        const float* __restrict__ bias, float* __restrict__ Cf,
+                                                        bf16* __restrict__ Cb, const float* __restrict__ zref,
+                                                        int ldc) {
+    __shared__ __align__(16) bf16 As[BM][BK + KPAD];
+    __shared__ __align__(16) bf16 Bs[BN][BK + KPAD];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+    const int g = lane >> 2, t = lane & 3;
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
+    const bf16 zero = __float2bfloat16(0.f);
+    for (int k0 = 0; k0 < K; k0 += BK) {
+        // A tile, 8-element vectors along the contiguous axis
+        for (int v = tid; v < BM * BK / 8; v += 128) {
+            if (!TA) {
+                const int mm = v / (BK / 8), kk = (v % (BK / 8)) * 8;
+                const int gm = m0 + mm, gk = k0 + kk;
+                uint4 q = make_uint4(0, 0, 0, 0);
+                if (gm < M && gk < K) q = *reinterpret_cast<const uint4*>(A + (size_t)gm * lda + gk);
+                *reinterpret_cast<uint4*>(&As[mm][kk]) = q;
+            } else {
+                const int kk = v / (BM / 8), mm = (v % (BM / 8)) * 8;
+                const int gm = m0 + mm, gk = k0 + kk;
+                bf16 e[8];
+                if (gk < K && gm + 7 < M) {
+                    *reinterpret_cast<uint4*>(e) = *reinterpret_cast<const uint4*>(A + (size_t)gk * lda + gm);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) e[i] = (gk < K && gm + i < M) ? A[(size_t)gk * lda + gm + i] : zero;
+                }
+#pragma unroll
+                for (int i = 0; i < 8; ++i) As[mm + i][kk] = e[i];
+            }
+        }
+        for (int v = tid; v < BN * BK / 8; v += 128) {
+            if (TB) {
+                const int nn = v / (BK / 8), kk = (v % (BK / 8)) * 8;
+                const int gn = n0 + nn, gk = k0 + kk;
+                uint4 q = make_uint4(0, 0, 0, 0);
+                if (gn < N && gk < K) q = *reinterpret_cast<const uint4*>(B + (size_t)gn * ldb + gk);
+                *reinterpret_cast<uint4*>(&Bs[nn][kk]) = q;
+            } else {
+                const int kk = v / (BN / 8), nn = (v % (BN / 8)) * 8;
+                const int gn = n0 + nn, gk = k0 + kk;
+                bf16 e[8];
+                if (gk < K && gn + 7 < N) {
+                    *reinterpret_cast<uint4*>(e) = *reinterpret_cast<const uint4*>(B + (size_t)gk * ldb + gn);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) e[i] = (gk < K && gn + i < N) ? B[(size_t)gk * ldb + gn + i] : zero;
+                }
+#pragma unroll
+                for (int i = 0; i < 8; ++i) Bs[nn + i][kk] = e[i];
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; kk += 16) {
+            unsigned int a[2][4], b[4][2];
+#pragma unroll
+            for (int im = 0; im < 2; ++im) {
+                const int r = wm + im * 16 + g;
+                a[im][0] = ld_pair(&As[r][kk + 2 * t]);
+                a[im][1] = ld_pair(&As[r + 8][kk + 2 * t]);
+                a[im][2] = ld_pair(&As[r][kk + 8 + 2 * t]);
+                a[im][3] = ld_pair(&As[r + 8][kk + 8 + 2 * t]);
+            }
+#pragma unroll
+            for (int in = 0; in < 4; ++in) {
+                const int c = wn + in * 8 + g;
+                b[in][0] = ld_pair(&Bs[c][kk + 2 * t]);
+                b[in][1] = ld_pair(&Bs[c][kk + 8 + 2 * t]);
+            }
+#pragma unroll
+            for (int im = 0; im < 2; ++im)
+#pragma unroll
+                for (int in = 0; in < 4; ++in) mma_bf16(acc[im][in], a[im], b[in]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int im = 0; im < 2; ++im)
+#pragma unroll
+        for (int in = 0; in < 4; ++in)
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const int row = m0 + wm + im * 16 + g + 8 * h;
+                    const int col = n0 + wn + in * 8 + 2 * t + j;
+                    if (row >= M || col >= N) continue;
+                    float v = acc[im][in][2 * h + j];
+                    if (bias) v += bias[col];
+                    const size_t o = (size_t)row * ldc + col;
+                    if (EPI == EPI_F32) {
+                        Cf[o] = v;
+                    } else if (EPI == EPI_RELU) {
+                        Cf[o] = v;
+                        Cb[o] = __float2bfloat16_rn(fmaxf(v, 0.f));
+                    } else {
+                        v = zref[o] > 0.f ? v : 0.f;
+                        Cf[o] = v;
+                        Cb[o] = __float2bfloat16_rn(v);
+                    }
+                }
+}
+
+// Output layer and loss, one warp per row: s = relu(z2) . w3 + b3;
+// l = w (softplus(s) - y s), ds = w (sigmoid(s) - y) / B.
+__global__ void head_kernel(const float* __restrict__ z2, const float* __restrict__ w3, const float* __restrict__ b3,
+                            int B, int H, const float* __restrict__ y, float pos_weight, float* __restrict__ s,
+                            float* __restrict__ ds, float* __restrict__ lrow) {
+    const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (row >= B) return;
+    float acc = 0.f;
+    for (int n = lane; n < H; n += 32) acc = fmaf(fmaxf(z2[(size_t)row * H + n], 0.f), w3[n], acc);
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+        const float v = acc + b3[0];
+        s[row] = v;
+        if (y) {
+            const float yy = y[row];
+            const float w = yy > 0.5f ? pos_weight : 1.0f;
+            const float sp = fmaxf(v, 0.f) + log1pf(expf(-fabsf(v)));
+            lrow[row] = w * (sp - yy * v);
+            ds[row] = w * (1.f / (1.f + expf(-v)) - yy) / (float)B;
+        }
+    }
+}
+
+// Deterministic sum of n values by one block.
+__global__ void sum_kernel(const float* __restrict__ v, int n, float* __restrict__ out, float scale) {
+    __shared__ float red[256];
+    float a = 0.f;
+    for (int i = threadIdx.x; i < n; i += 256) a += v[i];
+    red[threadIdx.x] = a;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = red[0] * scale;
+}
+
+// Layer-3 backward: dw3[n] = sum_b relu(z2) ds, dz2 = ds w3 (z2 > 0) (FP32 and BF16).
+__global__ void head_back_kernel(const float* __restrict__ z2, const float* __restrict__ w3,
+                                 const float* __restrict__ ds, int B, int H, float* __restrict__ dw3,
+                                 float* __restrict__ dz2, bf16* __restrict__ dz2b) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= H) return;
+    float a = 0.f;
+    for (int b = 0; b < B; ++b) {
+        const float z = z2[(size_t)b * H + n];
+        a = fmaf(fmaxf(z, 0.f), ds[b], a);
+        const float d = z > 0.f ? ds[b] * w3[n] : 0.f;
+        dz2[(size_t)b * H + n] = d;
+        dz2b[(size_t)b * H + n] = __float2bfloat16_rn(d);
+    }
+    dw3[n] = a;
+}
+
+// Column sums (bias gradients) of a [B][H] FP32 array.
+__global__ void colsum_kernel(const float* __restrict__ v, int B, int H, float* __restrict__ out) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= H) return;
+    float a = 0.f;
+    for (int b = 0; b < B; ++b) a += v[(size_t)b * H + n];
+    out[n] = a;
+}
+
+__global__ void adam_kernel(float* __restrict__ p, float* __restrict__ m, float* __restrict__ v,
+                            const float* __restrict__ gr, long long n, float lr, float c1, float c2,
+                            bf16* __restrict__ pb) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float gi = gr[i];
+        const float mi = 0.9f * m[i] + 0.1f * gi;
+        const float vi = 0.999f * v[i] + 0.001f * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        const float pi = p[i] - lr * (mi * c1) / (sqrtf(vi * c2) + 1e-8f);
+        p[i] = pi;
+        if (pb) pb[i] = __float2bfloat16_rn(pi);
+    }
+}
+
+__global__ void to_bf16_kernel(const float* __restrict__ x, long long n, bf16* __restrict__ y) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = __float2bfloat16_rn(x[i]);
+}
+
+__global__ void patch_kernel(const float* __restrict__ twoF, int n_f, int n_d, int s_a, int s_d, int n_fp,
+                             const int* __restrict__ f_start, int n_q, int n_pd, float shift, float scale,
+                             bf16* __restrict__ out) {
+    const int p = blockIdx.x;
+    const int pa = p / (n_pd * n_q);
+    const int r = p - pa * n_pd * n_q;
+    const int pd = r / n_q, q = r - pd * n_q;
+    const int row = s_a * s_d * n_fp;
+    const int f0 = f_start[q];
+    for (int e = threadIdx.x; e < row; e += blockDim.x) {
+        const int fl = e % n_fp;
+        const int sl = e / n_fp;
+        const int ia = pa * s_a + sl / s_d, id = pd * s_d + sl % s_d;
+        const float v = twoF[(size_t)(ia * n_d + id) * n_f + f0 + fl];
+        out[(size_t)p * row + e] = __float2bfloat16_rn((v - shift) * scale);
+    }
+}
+
+template <bool TA, bool TB, int EPI>
+cudaError_t gemm(int M, int N, int K, const bf16* A, int lda, const bf16* B, int ldb, const float* bias, float* Cf,
+                 bf16* Cb, const float* zref, int ldc, cudaStream_t s) {
+    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
+    gemm_bf16_kernel<TA, TB, EPI><<<grid, 128, 0, s>>>(M, N, K, A, lda, B, ldb, bias, Cf, Cb, zref, ldc);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_patches(const float* twoF, int n_f, int n_d, int s_a, int s_d, int n_fp, const int* f_start_dev,
+                           int n_q, int n_patches, int n_pd, float shift, float scale, void* out, cudaStream_t s) {
+    patch_kernel<<<n_patches, 256, 0, s>>>(twoF, n_f, n_d, s_a, s_d, n_fp, f_start_dev, n_q, n_pd, shift, scale,
+                                           reinterpret_cast<bf16*>(out));
+    return cudaGetLastError();
+}
+
+}  // namespace fs
+
+using namespace fs;
+
+struct fstat_mlp {
+    int device = 0;
+    int n_in = 0, H = 0, maxB = 0;
+    std::string err;
+    float *W1 = nullptr, *b1 = nullptr, *W2 = nullptr, *b2 = nullptr, *w3 = nullptr, *b3 = nullptr;
+    bf16 *W1b = nullptr, *W2b = nullptr;
+    float* mom[12] = {};    // m, v per parameter
+    float *gW1 = nullptr, *gb1 = nullptr, *gW2 = nullptr, *gb2 = nullptr, *gw3 = nullptr, *gb3 = nullptr;
+    bf16* Xb = nullptr;
+    float *y = nullptr, *z1 = nullptr, *z2 = nullptr, *s = nullptr, *ds = nullptr, *lrow = nullptr, *loss = nullptr;
+    bf16 *h1 = nullptr, *h2 = nullptr;
+    float *dz2 = nullptr, *dz1 = nullptr;
+    bf16 *dz2b = nullptr, *dz1b = nullptr;
+    int t = 0;
+    cudaStream_t stream = nullptr;
+    std::vector<void*> allocs;
+};
+
+namespace {
+
+int mfail(fstat_mlp* m, int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (m) m->err = buf;
+    return code;
+}
+
+#define MLP_TRY(m, call)                                                                              \
+    do {                                                                                              \
+        cudaError_t e_ = (call);                                                                      \
+        if (e_ != cudaSuccess) return mfail(m, FSTAT_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+template <class T>
+int alloc(fstat_mlp* m, T** p, size_t n) {
+    if (cudaMalloc((void**)p, std::max<size_t>(n, 1) * sizeof(T)) != cudaSuccess)
+        return mfail(m, FSTAT_ENOMEM, "cudaMalloc of %zu bytes failed", n * sizeof(T));
+    m->allocs.push_back((void*)*p);
+    return cudaMemset(*p, 0, std::max<size_t>(n, 1) * sizeof(T)) == cudaSuccess ? FSTAT_OK : FSTAT_ECUDA;
+}
+
+// Stage X (host or device) into the network's BF16 input buffer.
+int stage_input(fstat_mlp* m, const uint16_t* X, int B, int mem, cudaStream_t s, const bf16** Xd) {
+    if (mem == FSTAT_MEM_DEVICE) {
+        *Xd = reinterpret_cast<const bf16*>(X);
+        return FSTAT_OK;
+    }
+    MLP_TRY(m, cudaMemcpyAsync(m->Xb, X, (size_t)B * m->n_in * sizeof(uint16_t), cudaMemcpyHostToDevice, s));
+    *Xd = m->Xb;
+    return FSTAT_OK;
+}
+
+int run_forward(fstat_mlp* m, const bf16* X, int B, cudaStream_t s) {
+    const int n_in = m->n_in, H = m->H;
+    MLP_TRY(m, (gemm<false, false, EPI_RELU>(B, H, n_in, X, n_in, m->W1b, H, m->b1, m->z1, m->h1, nullptr, H, s)));
+    MLP_TRY(m, (gemm<false, false, EPI_RELU>(B, H, H, m->h1, H, m->W2b, H, m->b2, m->z2, m->h2, nullptr, H, s)));
+    return FSTAT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fstat_mlp_create(fstat_mlp** out, int device, int32_t n_in, int32_t n_hidden, int32_t max_batch) {
+    if (!out) return FSTAT_EINVAL;
+    *out = nullptr;
+    if (n_in < 8 || n_in % 8 || n_hidden < 8 || n_hidden % 8 || max_batch < 1 || max_batch > 65536) return FSTAT_EINVAL;
+    int n_dev = 0;
+    if (cudaGetDeviceCount(&n_dev) != cudaSuccess || device < 0 || device >= n_dev) return FSTAT_ECUDA;
+    if (cudaSetDevice(device) != cudaSuccess) return FSTAT_ECUDA;
+    fstat_mlp* m = new fstat_mlp();
+    m->device = device;
+    m->n_in = n_in;
+    m->H = n_hidden;
+    m->maxB = (max_batch + 7) & ~7;
+    const size_t H = n_hidden, I = n_in, Bm = m->maxB;
+    int rc = FSTAT_OK;
+    const size_t sizes[6] = {I * H, H, H * H, H, H, 1};
+    float** params[6] = {&m->W1, &m->b1, &m->W2, &m->b2, &m->w3, &m->b3};
+    float** grads[6] = {&m->gW1, &m->gb1, &m->gW2, &m->gb2, &m->gw3, &m->gb3};
+    for (int i = 0; i < 6 && rc == FSTAT_OK; ++i) {
+        rc = alloc(m, params[i], sizes[i]);
+        if (rc == FSTAT_OK) rc = alloc(m, grads[i], sizes[i]);
+        if (rc == FSTAT_OK) rc = alloc(m, &m->mom[2 * i], sizes[i]);
+        if (rc == FSTAT_OK) rc = alloc(m, &m->mom[2 * i + 1], sizes[i]);
+    }
+    if (rc == FSTAT_OK) rc = alloc(m, &m->W1b, I * H);
+    if (rc == FSTAT_OK) rc = alloc(m, &m->W2b, H * H);
+    if (rc == FSTAT_OK) rc = alloc(m, &m->Xb, Bm * I);
+    if (rc == FSTAT_OK) rc = alloc(m, &m->y, Bm);
+    if (rc == FSTAT_OK) rc = alloc(m, &m->z1, Bm * H);
+    if (rc == FSTAT_OK) rc = alloc(m, &m->z2, Bm * H);
+    if (rc == FSTAT_OK) rc = alloc(m, &m->h1, Bm * H);
+    if (rc == FSTAT_OK) rc = alloc(m, &m->h2, Bm * H);
+    if (rc == FSTAT_OK) rc = alloc(m, &m->s, Bm);
+    if (rc == FSTAT_OK) rc = alloc(m, &m->ds, Bm);
+    if (rc == FSTAT_OK) rc = alloc(m, &m->lrow, Bm);
+    if (rc == FSTAT_OK) rc = alloc(m, &m->loss, 1);
+    if (rc == FSTAT_OK) rc = alloc(m, &m->dz2, Bm * H);
+    if (rc == FSTAT_OK) rc = alloc(m, &m->dz1, Bm * H);
+    if (rc == FSTAT_OK) rc = alloc(m, &m->dz2b, Bm * H);
+    if (rc == FSTAT_OK) rc = alloc(m, &m->dz1b, Bm * H);
+    if (rc != FSTAT_OK) {
+        fstat_mlp_destroy(m);
+        return rc;
+    }
+    *out = m;
+    return FSTAT_OK;
+}
+
+void fstat_mlp_destroy(fstat_mlp* m) {
+    if (!m) return;
+    cudaSetDevice(m->device);
+    cudaDeviceSynchronize();
+    for (void* p : m->allocs) cudaFree(p);
+    delete m;
+}
+
+const char* fstat_mlp_last_error(const fstat_mlp* m) { return m ? m->err.c_str() : ""; }
+
+int fstat_mlp_set_params(fstat_mlp* m, const float* W1, const float* b1, const float* W2, const float* b2,
+                         const float* w3, const float* b3) {
+    if (!m || !W1 || !b1 || !W2 || !b2 || !w3 || !b3) return FSTAT_EINVAL;
+    m->err.clear();
+    MLP_TRY(m, cudaSetDevice(m->device));
+    const size_t H = m->H, I = m->n_in;
+    const float* src[6] = {W1, b1, W2, b2, w3, b3};
+    float* dst[6] = {m->W1, m->b1, m->W2, m->b2, m->w3, m->b3};
+    const size_t n[6] = {I * H, H, H * H, H, H, 1};
+    for (int i = 0; i < 6; ++i) {
+        for (size_t k = 0; k < n[i]; ++k)
+            if (!std::isfinite(src[i][k])) return mfail(m, FSTAT_EINVAL, "non-finite parameter");
+        MLP_TRY(m, cudaMemcpy(dst[i], src[i], n[i] * sizeof(float), cudaMemcpyHostToDevice));
+        MLP_TRY(m, cudaMemset(m->mom[2 * i], 0, n[i] * sizeof(float)));
+        MLP_TRY(m, cudaMemset(m->mom[2 * i + 1], 0, n[i] * sizeof(float)));
+    }
+    to_bf16_kernel<<<256, 256>>>(m->W1, (long long)(I * H), m->W1b);
+    to_bf16_kernel<<<64, 256>>>(m->W2, (long long)(H * H), m->W2b);
+    MLP_TRY(m, cudaGetLastError());
+    MLP_TRY(m, cudaDeviceSynchronize());
+    m->t = 0;
+    return FSTAT_OK;
+}
+
+int fstat_mlp_get_params(fstat_mlp* m, float* W1, float* b1, float* W2, float* b2, float* w3, float* b3) {
+    if (!m || !W1 || !b1 || !W2 || !b2 || !w3 || !b3) return FSTAT_EINVAL;
+    MLP_TRY(m, cudaSetDevice(m->device));
+    MLP_TRY(m, cudaStreamSynchronize(m->stream));
+    const size_t H = m->H, I = m->n_in;
+    float* dst[6] = {W1, b1, W2, b2, w3, b3};
+    const float* src[6] = {m->W1, m->b1, m->W2, m->b2, m->w3, m->b3};
+    const size_t n[6] = {I * H, H, H * H, H, H, 1};
+    for (int i = 0; i < 6; ++i) MLP_TRY(m, cudaMemcpy(dst[i], src[i], n[i] * sizeof(float), cudaMemcpyDeviceToHost));
+    return FSTAT_OK;
+}
+
+int fstat_mlp_forward(fstat_mlp* m, const uint16_t* X, int32_t B, float* logits, int32_t mem, void* cuda_stream) {
+    if (!m || !X || !logits) return FSTAT_EINVAL;
+    m->err.clear();
+    if (B < 1 || B > m->maxB) return mfail(m, FSTAT_EINVAL, "batch %d outside 1..%d", B, m->maxB);
+    MLP_TRY(m, cudaSetDevice(m->device));
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    m->stream = s;
+    const bf16* Xd = nullptr;
+    int rc = stage_input(m, X, B, mem, s, &Xd);
+    if (rc != FSTAT_OK) return rc;
+    if ((rc = run_forward(m, Xd, B, s)) != FSTAT_OK) return rc;
+    head_kernel<<<(B + 7) / 8, 256, 0, s>>>(m->z2, m->w3, m->b3, B, m->H, nullptr, 1.f, m->s, nullptr, nullptr);
+    MLP_TRY(m, cudaGetLastError());
+    if (mem == FSTAT_MEM_DEVICE) {
+        MLP_TRY(m, cudaMemcpyAsync(logits, m->s, B * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    } else {
+        MLP_TRY(m, cudaMemcpyAsync(logits, m->s, B * sizeof(float), cudaMemcpyDeviceToHost, s));
+        MLP_TRY(m, cudaStreamSynchronize(s));
+    }
+    return FSTAT_OK;
+}
+
+int fstat_mlp_train_step(fstat_mlp* m, const uint16_t* X, const float* y, int32_t B, float pos_weight, float lr,
+                         float* loss, int32_t mem, void* cuda_stream) {
+    if (!m || !X || !y) return FSTAT_EINVAL;
+    m->err.clear();
+    if (B < 8 || B > m->maxB || B % 8) return mfail(m, FSTAT_EINVAL, "training batch must be a multiple of 8 in 8..%d", m->maxB);
+    if (!(lr > 0.f) || !(pos_weight > 0.f)) return mfail(m, FSTAT_EINVAL, "lr and pos_weight must be > 0");
+    MLP_TRY(m, cudaSetDevice(m->device));
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    m->stream = s;
+    const int H = m->H, I = m->n_in;
+    const bf16* Xd = nullptr;
+    int rc = stage_input(m, X, B, mem, s, &Xd);
+    if (rc != FSTAT_OK) return rc;
+    MLP_TRY(m, cudaMemcpyAsync(m->y, y, B * sizeof(float),
+                               mem == FSTAT_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    if ((rc = run_forward(m, Xd, B, s)) != FSTAT_OK) return rc;
+    head_kernel<<<(B + 7) / 8, 256, 0, s>>>(m->z2, m->w3, m->b3, B, H, m->y, pos_weight, m->s, m->ds, m->lrow);
+    sum_kernel<<<1, 256, 0, s>>>(m->lrow, B, m->loss, 1.f / (float)B);
+    sum_kernel<<<1, 256, 0, s>>>(m->ds, B, m->gb3, 1.f);
+    head_back_kernel<<<(H + 127) / 128, 128, 0, s>>>(m->z2, m->w3, m->ds, B, H, m->gw3, m->dz2, m->dz2b);
+    colsum_kernel<<<(H + 127) / 128, 128, 0, s>>>(m->dz2, B, H, m->gb2);
+    MLP_TRY(m, cudaGetLastError());
+    // dW2 = h1^T dz2;  dz1 = (dz2 W2^T) * (z1 > 0);  dW1 = X^T dz1
+    MLP_TRY(m, (gemm<true, false, EPI_F32>(H, H, B, m->h1, H, m->dz2b, H, nullptr, m->gW2, nullptr, nullptr, H, s)));
+    MLP_TRY(m, (gemm<false, true, EPI_MASK>(B, H, H, m->dz2b, H, m->W2b, H, nullptr, m->dz1, m->dz1b, m->z1, H, s)));
+    colsum_kernel<<<(H + 127) / 128, 128, 0, s>>>(m->dz1, B, H, m->gb1);
+    MLP_TRY(m, (gemm<true, false, EPI_F32>(I, H, B, Xd, I, m->dz1b, H, nullptr, m->gW1, nullptr, nullptr, H, s)));
+    // Adam
+    m->t += 1;
+    const float c1 = 1.f / (1.f - powf(0.9f, (float)m->t)), c2 = 1.f / (1.f - powf(0.999f, (float)m->t));
+    float* P[6] = {m->W1, m->b1, m->W2, m->b2, m->w3, m->b3};
+    float* Gr[6] = {m->gW1, m->gb1, m->gW2, m->gb2, m->gw3, m->gb3};
+    bf16* Pb[6] = {m->W1b, nullptr, m->W2b, nullptr, nullptr, nullptr};
+    const long long n[6] = {(long long)I * H, H, (long long)H * H, H, H, 1};
+    for (int i = 0; i < 6; ++i)
+        adam_kernel<<<(int)std::min<long long>(1024, (n[i] + 255) / 256), 256, 0, s>>>(P[i], m->mom[2 * i], m->mom[2 * i + 1],
+                                                                                       Gr[i], n[i], lr, c1, c2, Pb[i]);
+    MLP_TRY(m, cudaGetLastError());
+    if (loss) {
+        MLP_TRY(m, cudaMemcpyAsync(loss, m->loss, sizeof(float), cudaMemcpyDeviceToHost, s));
+        MLP_TRY(m, cudaStreamSynchronize(s));
+    }
+    return FSTAT_OK;
+}
+
+int fstat_mlp_get_grads(fstat_mlp* m, float* dW1, float* db1, float* dW2, float* db2, float* dw3, float* db3) {
+    if (!m || !dW1 || !db1 || !dW2 || !db2 || !dw3 || !db3) return FSTAT_EINVAL;
+    MLP_TRY(m, cudaSetDevice(m->device));
+    MLP_TRY(m, cudaStreamSynchronize(m->stream));
+    const size_t H = m->H, I = m->n_in;
+    float* dst[6] = {dW1, db1, dW2, db2, dw3, db3};
+    const float* src[6] = {m->gW1, m->gb1, m->gW2, m->gb2, m->gw3, m->gb3};
+    const size_t n[6] = {I * H, H, H * H, H, H, 1};
+    for (int i = 0; i < 6; ++i) MLP_TRY(m, cudaMemcpy(dst[i], src[i], n[i] * sizeof(float), cudaMemcpyDeviceToHost));
+    return FSTAT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,251 @@
+"""Learned-proposal search: coarse F-statistic map -> patch-scoring network ->
+fine-grid F-statistic on the best patches, with the exhaustive fine grid as
+the fallback and the judge of the missed-signal rate.
+
+Host orchestration only: every 2F value, patch tensor, network forward,
+backward and Adam step is computed by libfstat's kernels (fstat.h,
+fstat_mlp.h); this module chooses which banks to run and keeps the books.
+
+Geometry (the design's reading of the learned-proposal configuration):
+  coarse sky   64 x 32 grid in (alpha, sin delta), cell-centred, index ia*32 + id
+  coarse freq  900 bins at 1/T from the workunit's band start
+  patch        16 x 16 coarse sky cells x 32 coarse frequencies (8192 inputs);
+               4 x 2 sky patches x 29 frequency patches (the last one overlaps)
+  fine grid    8x in frequency (1/(8T)) and 8x in sky points (4x alpha, 2x sin delta)
+"""
+from __future__ import annotations
+
+import math
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import FStat, MLP, fstat_extract_patches, fstat_set_sfts
+
+N_A, N_D = 64, 32          # coarse sky grid
+S_A, S_D = 16, 16          # sky cells per patch
+N_FP = 32                  # coarse frequencies per patch
+FINE_A, FINE_D, FINE_F = 4, 2, 8
+SHIFT, SCALE = 4.0, 1.0 / 8.0   # network input x = (2F - 4) / 8
+
+
+def f_starts(n_f: int) -> np.ndarray:
+    """Starts of the frequency patches; the last one ends at the band edge."""
+    q = list(range(0, n_f - N_FP + 1, N_FP))
+    if q[-1] + N_FP < n_f:
+        q.append(n_f - N_FP)
+    return np.asarray(q, dtype=np.int32)
+
+
+def patch_count(n_f: int) -> int:
+    return (N_A // S_A) * (N_D // S_D) * len(f_starts(n_f))
+
+
+def patch_of(ia: int, id_: int, q: int, n_q: int) -> int:
+    return ((ia // S_A) * (N_D // S_D) + id_ // S_D) * n_q + q
+
+
+def signal_patches(inj, bank) -> list:
+    """Indices of the patches whose sky cells and frequency span hold the signal."""
+    da = 2 * math.pi / N_A
+    ds = 2.0 / N_D
+    ia = min(N_A - 1, int((inj.alpha % (2 * math.pi)) / da))
+    id_ = min(N_D - 1, int((math.sin(inj.delta) + 1.0) / ds))
+    fb = (inj.f - bank.f0) / bank.df
+    fs = f_starts(bank.n_f)
+    return [patch_of(ia, id_, q, len(fs)) for q, s in enumerate(fs) if s <= fb < s + N_FP]
+
+
+def fine_bank(p: int, bank):
+    """Sky list, f0, df, n_f of the fine grid over patch p of a coarse bank."""
+    fs = f_starts(bank.n_f)
+    n_q = len(fs)
+    q = p % n_q
+    r = p // n_q
+    pd = r % (N_D // S_D)
+    pa = r // (N_D // S_D)
+    da = 2 * math.pi / N_A
+    ds = 2.0 / N_D
+    na, nd = S_A * FINE_A, S_D * FINE_D
+    a = pa * S_A * da + (np.arange(na) + 0.5) * (da / FINE_A)
+    s = -1.0 + pd * S_D * ds + (np.arange(nd) + 0.5) * (ds / FINE_D)
+    A, Sd = np.meshgrid(a, s, indexing="ij")
+    sky = np.stack([A.ravel(), np.arcsin(Sd.ravel())], axis=1)
+    f0 = bank.f0 + fs[q] * bank.df
+    return sky, f0, bank.df / FINE_F, N_FP * FINE_F
+
+
+@dataclass
+class WorkunitMaps:
+    patches: object            # torch CUDA tensor [n_patch, 8192] of BF16 bits (int16)
+    labels: np.ndarray         # [n_patch] 0/1
+    coarse_max: np.ndarray     # [n_patch] max coarse 2F per patch
+    has_signal: bool
+    sig_patches: list = field(default_factory=list)
+    coarse_ms: float = 0.0
+
+
+class ProposalSearch:
+    """Coarse maps, training data, network and refinement on one GPU."""
+
+    def __init__(self, device: int = 0, hidden: int = 256, max_batch: int = 1024):
+        import torch
+        self.torch = torch
+        self.device = device
+        self.fs = FStat(device, dterms=8, topk=1)
+        self.mlp = MLP(S_A * S_D * N_FP, hidden, max_batch, device)
+        self.stream = torch.cuda.Stream(device=device)
+
+    def close(self):
+        self.fs.close()
+        self.mlp.close()
+
+    # -- coarse map and patches ---------------------------------------------
+    def load(self, w) -> None:
+        for i, d in enumerate(w.detectors):
+            fstat_set_sfts(self.fs.ctx, i, d.lat, d.lon, d.az, w.T, w.k_lo, d.t_start, d.bins)
+        if w.injections:
+            self.fs.inject(w.injections, w.bank.t_ref)
+        self.fs.n_sft = w.n_sft_total
+
+    def coarse(self, w) -> WorkunitMaps:
+        torch = self.torch
+        self.load(w)
+        self.fs.set_bank(w.bank)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(self.stream)
+        self.fs.compute(self.stream)
+        ev1.record(self.stream)
+        fs_ = f_starts(w.bank.n_f)
+        n_p = patch_count(w.bank.n_f)
+        out = torch.empty((n_p, S_A * S_D * N_FP), dtype=torch.int16, device=f"cuda:{self.device}")
+        fstat_extract_patches(self.fs.ctx, N_A, N_D, S_A, S_D, N_FP, fs_, SHIFT, SCALE, out)
+        # coarse max per patch (the non-learned ranking), read back from the library's 2F map
+        twoF = self.fs.twoF().reshape(N_A, N_D, w.bank.n_f)
+        xmax = np.empty(n_p, dtype=np.float64)
+        n_q = len(fs_)
+        for pa in range(N_A // S_A):
+            for pd in range(N_D // S_D):
+                blk = twoF[pa * S_A:(pa + 1) * S_A, pd * S_D:(pd + 1) * S_D]
+                for q, f in enumerate(fs_):
+                    xmax[(pa * (N_D // S_D) + pd) * n_q + q] = blk[:, :, f:f + N_FP].max()
+        labels = np.zeros(n_p, dtype=np.float32)
+        sig = []
+        for inj in w.injections:
+            for p in signal_patches(inj, w.bank):
+                labels[p] = 1.0
+                sig.append(p)
+        return WorkunitMaps(out, labels, xmax, bool(w.injections), sig, ev0.elapsed_time(ev1))
+
+    # -- training -------------------------------------------------------------
+    def init_params(self, rng: np.random.Generator) -> None:
+        I, H = S_A * S_D * N_FP, self.mlp.H
+        p = {"W1": rng.standard_normal((I, H)) * math.sqrt(2.0 / I), "b1": np.zeros(H),
+             "W2": rng.standard_normal((H, H)) * math.sqrt(2.0 / H), "b2": np.zeros(H),
+             "w3": rng.standard_normal(H) * math.sqrt(1.0 / H), "b3": np.zeros(1)}
+        self.mlp.set_params(p)
+
+    def train(self, X, y: np.ndarray, steps: int, batch: int, lr: float, pos_frac: float, seed: int):
+        """Adam on batches with a fixed share of positive patches (sampled with
+        replacement); returns the loss history."""
+        torch = self.torch
+        rng = np.random.default_rng(seed)
+        pos = np.nonzero(y > 0.5)[0]
+        neg = np.nonzero(y <= 0.5)[0]
+        n_pos = max(1, int(round(batch * pos_frac))) if pos.size else 0
+        yt = torch.from_numpy(y.astype(np.float32)).to(X.device)
+        hist = []
+        for it in range(steps):
+            ip = rng.choice(pos, n_pos) if n_pos else np.zeros(0, dtype=np.int64)
+            ineg = rng.choice(neg, batch - n_pos)
+            idx = torch.from_numpy(np.concatenate([ip, ineg])).to(X.device)
+            xb = X.index_select(0, idx).contiguous()
+            yb = yt.index_select(0, idx).contiguous()
+            want = (it % 50 == 0) or it == steps - 1
+            l = self.mlp.train_step(xb, yb, 1.0, lr, stream=torch.cuda.current_stream(), want_loss=want)
+            if want:
+                hist.append(l)
+        torch.cuda.synchronize()
+        return hist
+
+    def scores(self, X) -> np.ndarray:
+        torch = self.torch
+        out = []
+        B = self.mlp.max_batch
+        for i in range(0, X.shape[0], B):
+            out.append(self.mlp.forward(X[i:i + B].contiguous(), stream=torch.cuda.current_stream()))
+        torch.cuda.synchronize()
+        return torch.cat(out).cpu().numpy()
+
+    # -- refinement -------------------------------------------------------------
+    def refine(self, w, patches) -> tuple:
+        """Fine-grid max 2F of each patch (SFTs of w must be loaded); returns
+        (max 2F array, device milliseconds)."""
+        torch = self.torch
+        from . import fstat_set_templates
+        res = np.zeros(len(patches), dtype=np.float64)
+        ms = 0.0
+        for i, p in enumerate(patches):
+            sky, f0, df, n_f = fine_bank(int(p), w.bank)
+            fstat_set_templates(self.fs.ctx, sky, f0, df, n_f, np.zeros(1), w.bank.t_ref)
+            self.fs.n_sky, self.fs.n_f, self.fs.n_fdot = sky.shape[0], n_f, 1
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(self.stream)
+            self.fs.compute(self.stream)
+            ev1.record(self.stream)
+            _, val = self.fs.toplist(1)
+            res[i] = float(val[0])
+            ms += ev0.elapsed_time(ev1)
+        return res, ms
+
+
+def evaluate(search: ProposalSearch, test_wus, n_refine: int, threshold: float | None = None,
+             noise_patches_per_wu: int | None = None):
+    """Recall of the learned proposal (top n_refine patches by network score),
+    of the coarse-max ranking and of a random choice, against the exhaustive
+    fine-grid judge (fine max 2F in the signal's patch above the threshold set
+    for 1 % false alarm per patch on the noise-only workunits)."""
+    rng = np.random.default_rng(77)
+    noise_max = []
+    rows = []
+    t_coarse = t_mlp = t_ref = 0.0
+    for w in test_wus:
+        m = search.coarse(w)
+        t0 = time.perf_counter()
+        sc = search.scores(m.patches)
+        t_mlp += 1e3 * (time.perf_counter() - t0)
+        t_coarse += m.coarse_ms
+        top_nn = list(np.argsort(-sc)[:n_refine])
+        top_cm = list(np.argsort(-m.coarse_max)[:n_refine])
+        top_rd = list(rng.choice(len(sc), n_refine, replace=False))
+        if not m.has_signal:
+            cand = np.arange(len(sc)) if noise_patches_per_wu is None else rng.choice(len(sc), noise_patches_per_wu,
+                                                                                      replace=False)
+            v, _ = search.refine(w, cand)
+            noise_max.extend(v.tolist())
+            v2, ms = search.refine(w, top_nn)
+            t_ref += ms
+            continue
+        sp = sorted(set(m.sig_patches))
+        v_sig, _ = search.refine(w, sp)
+        _, ms = search.refine(w, top_nn)
+        t_ref += ms
+        rows.append(dict(fine_max=float(v_sig.max()), in_nn=any(p in top_nn for p in sp),
+                         in_cm=any(p in top_cm for p in sp), in_rd=any(p in top_rd for p in sp)))
+    thr = threshold if threshold is not None else float(np.percentile(noise_max, 99.0))
+    judged = [r for r in rows if r["fine_max"] > thr]
+    n = max(1, len(judged))
+    n_wu = max(1, len(test_wus))
+    n_patch = patch_count(test_wus[0].bank.n_f)
+    ms_patch = t_ref / (n_wu * n_refine)
+    ms_learned = (t_coarse + t_mlp + t_ref) / n_wu
+    ms_exhaustive = n_patch * ms_patch
+    return dict(threshold=thr, n_signal=len(rows), n_detected_exhaustive=len(judged),
+                recall_nn=sum(r["in_nn"] for r in judged) / n, recall_coarse_max=sum(r["in_cm"] for r in judged) / n,
+                recall_random=sum(r["in_rd"] for r in judged) / n, n_refine=n_refine, n_patches=n_patch,
+                ms_per_wu_learned=ms_learned, ms_per_wu_exhaustive=ms_exhaustive,
+                speedup=ms_exhaustive / ms_learned, ms_coarse=t_coarse / n_wu, ms_mlp=t_mlp / n_wu,
+                ms_refine=t_ref / n_wu, n_test=len(test_wus), n_noise_patches=len(noise_max))
