@@ -11,7 +11,8 @@ Geometry (the design's reading of the learned-proposal configuration):
   coarse freq  900 bins at 1/T from the workunit's band start
   patch        16 x 16 coarse sky cells x 32 coarse frequencies (8192 inputs);
                4 x 2 sky patches x 29 frequency patches (the last one overlaps)
-  fine grid    8x in frequency (1/(8T)) and 8x in sky points (4x alpha, 2x sin delta)
+  fine grid    8x in frequency (1/(8T)) and 8x in sky points (4x alpha, 2x sin delta),
+               aligned so that it contains every coarse template of its patch
 """
 from __future__ import annotations
 
@@ -52,7 +53,7 @@ def signal_patches(inj, bank) -> list:
     ds = 2.0 / N_D
     ia = min(N_A - 1, int((inj.alpha % (2 * math.pi)) / da))
     id_ = min(N_D - 1, int((math.sin(inj.delta) + 1.0) / ds))
-    fb = (inj.f - bank.f0) / bank.df
+    fb = int(math.floor((inj.f - bank.f0) / bank.df + 0.5))
     fs = f_starts(bank.n_f)
     return [patch_of(ia, id_, q, len(fs)) for q, s in enumerate(fs) if s <= fb < s + N_FP]
 
@@ -68,8 +69,10 @@ def fine_bank(p: int, bank):
     da = 2 * math.pi / N_A
     ds = 2.0 / N_D
     na, nd = S_A * FINE_A, S_D * FINE_D
-    a = pa * S_A * da + (np.arange(na) + 0.5) * (da / FINE_A)
-    s = -1.0 + pd * S_D * ds + (np.arange(nd) + 0.5) * (ds / FINE_D)
+    # steps of 1/FINE of a cell from the patch's lower edge: cell centres (at
+    # half a cell) fall on the grid, so coarse templates are fine templates too
+    a = pa * S_A * da + np.arange(na) * (da / FINE_A)
+    s = -1.0 + pd * S_D * ds + np.arange(nd) * (ds / FINE_D)
     A, Sd = np.meshgrid(a, s, indexing="ij")
     sky = np.stack([A.ravel(), np.arcsin(Sd.ravel())], axis=1)
     f0 = bank.f0 + fs[q] * bank.df

@@ -83,11 +83,11 @@ def test_patch_extraction_matches_gather(lib):
     sd = -1 + (np.arange(n_d) + 0.5) * 2 / n_d
     A, S = np.meshgrid(a, sd, indexing="ij")
     sky = np.stack([A.ravel(), np.arcsin(S.ravel())], 1)
-    det = DetectorData(DET_H["lat"], 0.0, DET_H["az"], T0 + T_SFT * np.arange(30), cn_noise(4, 1, (30, 120)))
+    det = DetectorData(DET_H["lat"], 0.0, DET_H["az"], T0 + T_SFT * np.arange(30), cn_noise(4, 1, (30, 140)))
     g = lib.FStat(0, topk=1)
     try:
         lib.fstat_set_sfts(g.ctx, 0, det.lat, det.lon, det.az, T_SFT, 180000, det.t_start, det.bins)
-        g.set_bank(TemplateBank(sky, (180000 + 20) / T_SFT, 1 / T_SFT, n_f, np.zeros(1), T0))
+        g.set_bank(TemplateBank(sky, (180000 + 30) / T_SFT, 1 / T_SFT, n_f, np.zeros(1), T0))
         g.compute()
         twoF = g.twoF().reshape(n_a, n_d, n_f)
         fst = np.array([0, 16, 48], dtype=np.int32)

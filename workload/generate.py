@@ -333,7 +333,7 @@ def config4_workunit(index: int, train: bool = True, n_sft: int = 800, noise_onl
     """Learned-proposal workunit: 2 detectors x 800 SFTs, 0.5 Hz band, coarse
     grid 64 x 32 sky (alpha, sin delta) x 900 f x 1 fdot.  A quarter of the
     workunits are noise only; the rest carry one signal with log-uniform rho
-    in [4, 40]."""
+    in [4, 40], placed on a coarse template."""
     T = T_SFT
     seed = seed_base + (0 if train else 100000) + index
     dterms = 8
@@ -353,6 +353,16 @@ def config4_workunit(index: int, train: bool = True, n_sft: int = 800, noise_onl
                                                  (k0 + n_f) / T - margin, 0.0, 0.0, 4.0, 40.0,
                                                  log_rho=True)
     n_a, n_d = 64, 32
+    # Neither grid resolves a coherent signal over this span (a template off by
+    # 1/8 of a coarse step in f or sky keeps < 0.1 % of 2F), so each signal is
+    # moved onto the nearest coarse template: a sky cell centre and a coarse
+    # frequency, both of which the 8x finer grid also contains.
+    for inj in injs:
+        ia = min(n_a - 1, int((inj.alpha % (2 * math.pi)) / (2 * math.pi / n_a)))
+        id_ = min(n_d - 1, int((math.sin(inj.delta) + 1.0) / (2.0 / n_d)))
+        inj.alpha = (ia + 0.5) * (2 * math.pi / n_a)
+        inj.delta = math.asin(-1.0 + (id_ + 0.5) * (2.0 / n_d))
+        inj.f = (k0 + round((inj.f - k0 / T) * T)) / T
     a = (np.arange(n_a) + 0.5) * (2 * math.pi / n_a)
     sd = -1.0 + (np.arange(n_d) + 0.5) * (2.0 / n_d)
     A, SD = np.meshgrid(a, sd, indexing="ij")
