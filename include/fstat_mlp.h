@@ -67,12 +67,22 @@ int fstat_mlp_get_grads(fstat_mlp *m, float *dW1, float *db1, float *dW2, float 
  * patch p = (sky patch (pa, pd) of size s_a x s_d, frequency start f_start[q]
  * of length n_fp) for pa in [0, n_a / s_a), pd in [0, n_d / s_d), q in
  * [0, n_q), ordered ((pa * (n_d / s_d)) + pd) * n_q + q; each row holds
- * x = (2F - shift) * scale rounded to BF16, ordered (ia_local, id_local,
- * f_local).  out: device array [n_patches][s_a * s_d * n_fp] of BF16 bits.
+ * x = max(2F - shift, 0) * scale rounded to BF16 (the subtraction, the
+ * clamp and the product in FP32), ordered (ia_local, id_local, f_local); a
+ * shift well above the noise mean leaves only excess power in the input.  out: device array [n_patches][s_a * s_d * n_fp] of BF16 bits.
  * f_start [n_q] host.  Runs on the context's last compute stream.
  * Errors: ESTATE (nothing computed), EINVAL (shapes). */
 int fstat_extract_patches(fstat_ctx *ctx, int32_t n_a, int32_t n_d, int32_t s_a, int32_t s_d, int32_t n_fp,
                           const int32_t *f_start, int32_t n_q, float shift, float scale, uint16_t *out);
+
+/* Windows of the same 2F map at arbitrary origins, for training data: window
+ * w covers ia = (a0 + i) mod n_a for i < s_a (alpha wraps around the sky),
+ * id = d0 .. d0 + s_d - 1 and f = f0 .. f0 + n_fp - 1, with
+ * origin [n_w][3] = (a0, d0, f0) on the host; rows are laid out as in
+ * fstat_extract_patches.  out: device array [n_w][s_a * s_d * n_fp].
+ * Errors: ESTATE (nothing computed), EINVAL (an origin outside the grid). */
+int fstat_extract_windows(fstat_ctx *ctx, int32_t n_a, int32_t n_d, int32_t s_a, int32_t s_d, int32_t n_fp,
+                          const int32_t *origin, int32_t n_w, float shift, float scale, uint16_t *out);
 
 #ifdef __cplusplus
 }

@@ -9,6 +9,12 @@ cross-entropy with a positive-class weight w+:
     L = mean_i  w_i (softplus(s_i) - y_i s_i),  w_i = w+ if y_i = 1 else 1.
 Parameters: W1 [8192, 256], b1 [256], W2 [256, 256], b2 [256], w3 [256], b3.
 Adam: m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2; p -= lr m_hat / (sqrt(v_hat) + eps).
+
+`store` (optional, default none): a function applied to the first hidden
+activation h1 where it is stored for the second layer and for W2's gradient,
+for a device that keeps h1 in a narrower type.  The backward pass treats it as
+the identity (its derivative is one almost everywhere for a rounding), so the
+ReLU decisions of layer 2 are taken on the stored h1 as on such a device.
 """
 from __future__ import annotations
 
@@ -29,26 +35,28 @@ def sigmoid(s):
     return 1.0 / (1.0 + np.exp(-s))
 
 
-def forward(params, X):
-    """Logits s [B] and the hidden activations (z1, h1, z2, h2)."""
+def forward(params, X, store=None):
+    """Logits s [B] and the hidden activations (z1, h1, z2, h2); h1 as stored."""
     z1 = X @ params["W1"] + params["b1"]
     h1 = relu(z1)
+    if store is not None:
+        h1 = store(h1)
     z2 = h1 @ params["W2"] + params["b2"]
     h2 = relu(z2)
     s = h2 @ params["w3"] + params["b3"]
     return s, (z1, h1, z2, h2)
 
 
-def loss(params, X, y, pos_weight: float = 1.0):
-    s, _ = forward(params, X)
+def loss(params, X, y, pos_weight: float = 1.0, store=None):
+    s, _ = forward(params, X, store)
     w = np.where(y > 0.5, pos_weight, 1.0)
     return float(np.mean(w * (softplus(s) - y * s)))
 
 
-def backward(params, X, y, pos_weight: float = 1.0):
+def backward(params, X, y, pos_weight: float = 1.0, store=None):
     """Gradients of `loss` with respect to every parameter (FP64)."""
     B = X.shape[0]
-    s, (z1, h1, z2, h2) = forward(params, X)
+    s, (z1, h1, z2, h2) = forward(params, X, store)
     w = np.where(y > 0.5, pos_weight, 1.0)
     ds = w * (sigmoid(s) - y) / B                 # dL/ds
     g = {}

@@ -90,6 +90,8 @@ SIGNATURES = {
     "fstat_batch_get_times": (ctypes.c_int, [_P, _P, ctypes.POINTER(_D)]),
     "fstat_extract_patches": (ctypes.c_int, [_P, _I32, _I32, _I32, _I32, _I32, _P, _I32, ctypes.c_float,
                                              ctypes.c_float, _P]),
+    "fstat_extract_windows": (ctypes.c_int, [_P, _I32, _I32, _I32, _I32, _I32, _P, _I32, ctypes.c_float,
+                                             ctypes.c_float, _P]),
     # include/fstat_mlp.h
     "fstat_mlp_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, _I32, _I32, _I32]),
     "fstat_mlp_destroy": (None, [_P]),
@@ -344,6 +346,15 @@ def fstat_extract_patches(ctx, n_a: int, n_d: int, s_a: int, s_d: int, n_fp: int
     """out: torch CUDA tensor (int16/uint16/bfloat16) of [n_patches, s_a*s_d*n_fp] elements."""
     fst = np.ascontiguousarray(f_start, dtype=np.int32)
     _check(ctx, _lib.fstat_extract_patches(ctx, n_a, n_d, s_a, s_d, n_fp, _host_ptr(fst), fst.size, shift, scale,
+                                           ctypes.c_void_p(out.data_ptr())))
+
+
+def fstat_extract_windows(ctx, n_a: int, n_d: int, s_a: int, s_d: int, n_fp: int, origin, shift: float,
+                          scale: float, out) -> None:
+    """origin: int array [n_w, 3] of (a0, d0, f0); out: torch CUDA tensor (16-bit) of
+    [n_w, s_a*s_d*n_fp] elements."""
+    org = np.ascontiguousarray(origin, dtype=np.int32).reshape(-1, 3)
+    _check(ctx, _lib.fstat_extract_windows(ctx, n_a, n_d, s_a, s_d, n_fp, _host_ptr(org), org.shape[0], shift, scale,
                                            ctypes.c_void_p(out.data_ptr())))
 
 

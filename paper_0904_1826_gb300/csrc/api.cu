@@ -1294,4 +1294,30 @@ int fstat_extract_patches(fstat_ctx* c, int32_t n_a, int32_t n_d, int32_t s_a, i
     return FSTAT_OK;
 }
 
+int fstat_extract_windows(fstat_ctx* c, int32_t n_a, int32_t n_d, int32_t s_a, int32_t s_d, int32_t n_fp,
+                          const int32_t* origin, int32_t n_w, float shift, float scale, uint16_t* out) {
+    if (!c || !origin || !out) return FSTAT_EINVAL;
+    c->err.clear();
+    if (!c->computed) return fail(c, FSTAT_ESTATE, "nothing computed");
+    if (c->n_fdot != 1) return fail(c, FSTAT_EINVAL, "windows need a bank with one spindown");
+    if (n_a < 1 || n_d < 1 || (long long)n_a * n_d != c->n_sky)
+        return fail(c, FSTAT_EINVAL, "sky grid %d x %d does not match the bank's %d sky points", n_a, n_d, c->n_sky);
+    if (s_a < 1 || s_d < 1 || n_fp < 1 || s_a > n_a || s_d > n_d || n_fp > c->n_f || n_w < 1)
+        return fail(c, FSTAT_EINVAL, "empty or oversized window");
+    for (int w = 0; w < n_w; ++w) {
+        const int32_t a0 = origin[3 * w], d0 = origin[3 * w + 1], f0 = origin[3 * w + 2];
+        if (a0 < 0 || a0 >= n_a || d0 < 0 || d0 + s_d > n_d || f0 < 0 || f0 + n_fp > c->n_f)
+            return fail(c, FSTAT_EINVAL, "window %d origin (%d, %d, %d) outside the grid", w, a0, d0, f0);
+    }
+    if (set_device(c) != FSTAT_OK) return FSTAT_ECUDA;
+    int rc = grow(c, &c->d_fstart, c->cap_fstart, (size_t)3 * n_w);
+    if (rc != FSTAT_OK) return rc;
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_fstart, origin, sizeof(int) * 3 * (size_t)n_w, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, launch_windows(c->d_twoF, c->n_f, n_a, n_d, s_a, s_d, n_fp, c->d_fstart, n_w, shift, scale, out,
+                               c->stream));
+    c->launches += 1;
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));   // origin is a caller buffer
+    return FSTAT_OK;
+}
+
 }  // extern "C"

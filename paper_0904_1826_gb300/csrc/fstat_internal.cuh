@@ -149,6 +149,8 @@ cudaError_t launch_quantize(const float2* src, long long row, int n_sft, int n_b
 
 cudaError_t launch_patches(const float* twoF, int n_f, int n_d, int s_a, int s_d, int n_fp, const int* f_start_dev,
                            int n_q, int n_patches, int n_pd, float shift, float scale, void* out, cudaStream_t s);
+cudaError_t launch_windows(const float* twoF, int n_f, int n_a, int n_d, int s_a, int s_d, int n_fp,
+                           const int* origin_dev, int n_w, float shift, float scale, void* out, cudaStream_t s);
 
 // Toplist (radix select over the FP32 bit patterns of 2F >= 0).
 struct TopkWork {

@@ -248,7 +248,25 @@ __global__ void patch_kernel(const float* __restrict__ twoF, int n_f, int n_d, i
         const int sl = e / n_fp;
         const int ia = pa * s_a + sl / s_d, id = pd * s_d + sl % s_d;
         const float v = twoF[(size_t)(ia * n_d + id) * n_f + f0 + fl];
-        out[(size_t)p * row + e] = __float2bfloat16_rn((v - shift) * scale);
+        out[(size_t)p * row + e] = __float2bfloat16_rn(fmaxf(v - shift, 0.f) * scale);
+    }
+}
+
+// Windows at arbitrary origins (a0, d0, f0): alpha wraps around the grid, the
+// other two stay inside it (checked by the caller).
+__global__ void window_kernel(const float* __restrict__ twoF, int n_f, int n_a, int n_d, int s_a, int s_d, int n_fp,
+                              const int* __restrict__ origin, float shift, float scale, bf16* __restrict__ out) {
+    const int w = blockIdx.x;
+    const int a0 = origin[3 * w], d0 = origin[3 * w + 1], f0 = origin[3 * w + 2];
+    const int row = s_a * s_d * n_fp;
+    for (int e = threadIdx.x; e < row; e += blockDim.x) {
+        const int fl = e % n_fp;
+        const int sl = e / n_fp;
+        int ia = a0 + sl / s_d;
+        if (ia >= n_a) ia -= n_a;
+        const int id = d0 + sl % s_d;
+        const float v = twoF[(size_t)(ia * n_d + id) * n_f + f0 + fl];
+        out[(size_t)w * row + e] = __float2bfloat16_rn(fmaxf(v - shift, 0.f) * scale);
     }
 }
 
@@ -266,6 +284,13 @@ cudaError_t launch_patches(const float* twoF, int n_f, int n_d, int s_a, int s_d
                            int n_q, int n_patches, int n_pd, float shift, float scale, void* out, cudaStream_t s) {
     patch_kernel<<<n_patches, 256, 0, s>>>(twoF, n_f, n_d, s_a, s_d, n_fp, f_start_dev, n_q, n_pd, shift, scale,
                                            reinterpret_cast<bf16*>(out));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_windows(const float* twoF, int n_f, int n_a, int n_d, int s_a, int s_d, int n_fp,
+                           const int* origin_dev, int n_w, float shift, float scale, void* out, cudaStream_t s) {
+    window_kernel<<<n_w, 256, 0, s>>>(twoF, n_f, n_a, n_d, s_a, s_d, n_fp, origin_dev, shift, scale,
+                                      reinterpret_cast<bf16*>(out));
     return cudaGetLastError();
 }
 

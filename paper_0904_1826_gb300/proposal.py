@@ -22,13 +22,13 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import FStat, MLP, fstat_extract_patches, fstat_set_sfts
+from . import FStat, MLP, fstat_extract_patches, fstat_extract_windows, fstat_set_sfts
 
 N_A, N_D = 64, 32          # coarse sky grid
 S_A, S_D = 16, 16          # sky cells per patch
 N_FP = 32                  # coarse frequencies per patch
 FINE_A, FINE_D, FINE_F = 4, 2, 8
-SHIFT, SCALE = 4.0, 1.0 / 8.0   # network input x = (2F - 4) / 8
+SHIFT, SCALE = 16.0, 1.0 / 16.0  # network input x = max(2F - 16, 0) / 16: excess power only
 
 
 def f_starts(n_f: int) -> np.ndarray:
@@ -56,6 +56,37 @@ def signal_patches(inj, bank) -> list:
     fb = int(math.floor((inj.f - bank.f0) / bank.df + 0.5))
     fs = f_starts(bank.n_f)
     return [patch_of(ia, id_, q, len(fs)) for q, s in enumerate(fs) if s <= fb < s + N_FP]
+
+
+def signal_cell(inj, bank) -> tuple:
+    """Coarse grid cell (ia, id, f index) of a signal."""
+    ia = min(N_A - 1, int((inj.alpha % (2 * math.pi)) / (2 * math.pi / N_A)))
+    id_ = min(N_D - 1, int((math.sin(inj.delta) + 1.0) / (2.0 / N_D)))
+    return ia, id_, int(math.floor((inj.f - bank.f0) / bank.df + 0.5))
+
+
+def window_origins(cells, n_f: int, rng: np.random.Generator, n_pos: int, n_neg: int):
+    """Origins (a0, d0, f0) of n_pos windows per signal cell, each holding that
+    cell at a uniformly drawn position, and of n_neg windows that hold none of
+    the cells; labels 1 / 0."""
+    org, lab = [], []
+
+    def holds(o, c):
+        return ((c[0] - o[0]) % N_A) < S_A and o[1] <= c[1] < o[1] + S_D and o[2] <= c[2] < o[2] + N_FP
+
+    for ia, id_, m in cells:
+        d_lo, d_hi = max(0, id_ - S_D + 1), min(id_, N_D - S_D)
+        f_lo, f_hi = max(0, m - N_FP + 1), min(m, n_f - N_FP)
+        for _ in range(n_pos):
+            org.append(((ia - int(rng.integers(S_A))) % N_A, int(rng.integers(d_lo, d_hi + 1)),
+                        int(rng.integers(f_lo, f_hi + 1))))
+            lab.append(1.0)
+    while len(org) < len(cells) * n_pos + n_neg:
+        o = (int(rng.integers(N_A)), int(rng.integers(N_D - S_D + 1)), int(rng.integers(n_f - N_FP + 1)))
+        if not any(holds(o, c) for c in cells):
+            org.append(o)
+            lab.append(0.0)
+    return np.asarray(org, dtype=np.int32).reshape(-1, 3), np.asarray(lab, dtype=np.float32)
 
 
 def fine_bank(p: int, bank):
@@ -87,13 +118,16 @@ class WorkunitMaps:
     has_signal: bool
     sig_patches: list = field(default_factory=list)
     coarse_ms: float = 0.0
+    cells: list = field(default_factory=list)   # coarse cells (ia, id, f) of the signals
 
 
 class ProposalSearch:
     """Coarse maps, training data, network and refinement on one GPU."""
 
-    def __init__(self, device: int = 0, hidden: int = 256, max_batch: int = 1024):
+    def __init__(self, device: int = 0, hidden: int = 256, max_batch: int = 1024, shift: float = SHIFT,
+                 scale: float = SCALE):
         import torch
+        self.shift, self.scale = shift, scale
         self.torch = torch
         self.device = device
         self.fs = FStat(device, dterms=8, topk=1)
@@ -124,7 +158,7 @@ class ProposalSearch:
         fs_ = f_starts(w.bank.n_f)
         n_p = patch_count(w.bank.n_f)
         out = torch.empty((n_p, S_A * S_D * N_FP), dtype=torch.int16, device=f"cuda:{self.device}")
-        fstat_extract_patches(self.fs.ctx, N_A, N_D, S_A, S_D, N_FP, fs_, SHIFT, SCALE, out)
+        fstat_extract_patches(self.fs.ctx, N_A, N_D, S_A, S_D, N_FP, fs_, self.shift, self.scale, out)
         # coarse max per patch (the non-learned ranking), read back from the library's 2F map
         twoF = self.fs.twoF().reshape(N_A, N_D, w.bank.n_f)
         xmax = np.empty(n_p, dtype=np.float64)
@@ -140,7 +174,26 @@ class ProposalSearch:
             for p in signal_patches(inj, w.bank):
                 labels[p] = 1.0
                 sig.append(p)
-        return WorkunitMaps(out, labels, xmax, bool(w.injections), sig, ev0.elapsed_time(ev1))
+        return WorkunitMaps(out, labels, xmax, bool(w.injections), sig, ev0.elapsed_time(ev1),
+                            [signal_cell(inj, w.bank) for inj in w.injections])
+
+    def windows(self, origins: np.ndarray):
+        """Network inputs of windows of the last coarse map at the given origins."""
+        out = self.torch.empty((origins.shape[0], S_A * S_D * N_FP), dtype=self.torch.int16,
+                               device=f"cuda:{self.device}")
+        fstat_extract_windows(self.fs.ctx, N_A, N_D, S_A, S_D, N_FP, origins, self.shift, self.scale, out)
+        return out
+
+    def training_set(self, workunits, rng: np.random.Generator, n_pos: int, n_neg: int):
+        """Coarse map of each workunit, then its grid patches plus n_pos windows
+        around each signal and n_neg signal-free windows; returns (X, y)."""
+        xs, ys = [], []
+        for w in workunits:
+            m = self.coarse(w)
+            o, lab = window_origins(m.cells, w.bank.n_f, rng, n_pos, n_neg)
+            xs += [m.patches, self.windows(o)]
+            ys += [m.labels, lab]
+        return self.torch.cat(xs), np.concatenate(ys)
 
     # -- training -------------------------------------------------------------
     def init_params(self, rng: np.random.Generator) -> None:

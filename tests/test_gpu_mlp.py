@@ -37,13 +37,15 @@ def test_forward_and_gradients_match_oracle(lib, I, H, B):
     m = lib.MLP(I, H, 1024)
     try:
         m.set_params(p)
+        # the device keeps h1 in BF16 (round to nearest even) between the layers
+        store = lambda h: _bf16(h)[1]  # noqa: E731
         s = m.forward(xbits).astype(np.float64)
-        s_ref, _ = MO.forward(pq, X)
+        s_ref, _ = MO.forward(pq, X, store)
         assert np.max(np.abs(s - s_ref)) <= 2e-2 * np.max(np.abs(s_ref)) + 1e-3
         loss = m.train_step(xbits, y, 2.5, 1e-3)
-        assert abs(loss - MO.loss(pq, X, y, 2.5)) <= 1e-2 * abs(loss) + 1e-4
+        assert abs(loss - MO.loss(pq, X, y, 2.5, store)) <= 1e-2 * abs(loss) + 1e-4
         g = m.get_grads()
-        gr = MO.backward(pq, X, y, 2.5)
+        gr = MO.backward(pq, X, y, 2.5, store)
         for k in MO.NAMES:
             a, b = np.asarray(g[k], np.float64).ravel(), np.asarray(gr[k], np.float64).ravel()
             assert np.linalg.norm(a - b) <= 2e-2 * np.linalg.norm(b) + 1e-6, k
@@ -98,31 +100,32 @@ def test_patch_extraction_matches_gather(lib):
             for pd in range(2):
                 for q, f in enumerate(fst):
                     blk = twoF[pa * 4:(pa + 1) * 4, pd * 2:(pd + 1) * 2, f:f + 16].reshape(-1)
-                    want = Q.f32_to_bf16_bits(((blk - np.float32(4.0)) * np.float32(0.125)).astype(np.float32))
+                    x = np.maximum(blk - np.float32(4.0), np.float32(0.0)) * np.float32(0.125)
+                    want = Q.f32_to_bf16_bits(x.astype(np.float32))
                     np.testing.assert_array_equal(got[(pa * 2 + pd) * 3 + q], want)
     finally:
         g.close()
 
 
 def test_learned_proposal_beats_random_choice(lib):
-    """Small learned-proposal run: the trained network's top patches hold more
-    of the signals the exhaustive fine grid detects than a random choice."""
+    """Small learned-proposal run: trained on windows of coarse maps (eight
+    signals per training workunit), the network's 8 best patches of 232 hold
+    most of the held-out signals the exhaustive fine grid detects, far more
+    than 8 random patches, at a fraction of the exhaustive grid's cost."""
     pytest.importorskip("torch")
-    import torch
     from paper_0904_1826_gb300 import proposal as PR
     search = PR.ProposalSearch(0, hidden=64, max_batch=512)
     try:
-        train = [config4_workunit(i, True, n_sft=150, noise_only_frac=0.25) for i in range(40)]
-        maps = [search.coarse(w) for w in train]
-        X = torch.cat([m.patches for m in maps])
-        y = np.concatenate([m.labels for m in maps])
+        train = [config4_workunit(i, True, n_sft=150, n_signals=8) for i in range(40)]
+        X, y = search.training_set(train, np.random.default_rng(5), 16, 256)
         search.init_params(np.random.default_rng(1))
-        hist = search.train(X, y, steps=250, batch=256, lr=1e-3, pos_frac=0.25, seed=2)
-        assert hist[-1] < hist[0]
-        test = [config4_workunit(i, False, n_sft=150, noise_only_frac=0.25) for i in range(16)]
+        hist = search.train(X, y, steps=800, batch=256, lr=3e-4, pos_frac=0.25, seed=2)
+        assert hist[-1] < 0.3 * hist[0]
+        test = [config4_workunit(i, False, n_sft=150) for i in range(16)]
         res = PR.evaluate(search, test, n_refine=8, noise_patches_per_wu=24)
-        assert res["n_detected_exhaustive"] >= 3
-        assert res["recall_nn"] > res["recall_random"]
-        assert res["speedup"] > 5
+        assert res["n_detected_exhaustive"] >= 6
+        assert res["recall_nn"] >= 0.5
+        assert res["recall_nn"] >= res["recall_random"] + 0.3
+        assert res["speedup"] > 10
     finally:
         search.close()

@@ -70,3 +70,20 @@ def test_adam_converges_on_separable_data():
         MO.adam_step(p, MO.backward(p, X, y), st, lr=1e-2)
     assert MO.loss(p, X, y) < 0.2 * l0
     assert st["t"] == 300
+
+
+def test_store_hook_reaches_layer_two_and_its_gradient():
+    """A store that zeroes h1 leaves s = relu(b2) . w3 + b3 and a zero W2
+    gradient; the identity store changes nothing."""
+    rng = np.random.default_rng(4)
+    p = _params(rng, 10, 6)
+    X = rng.standard_normal((7, 10))
+    y = (rng.random(7) < 0.5).astype(np.float64)
+    s0, _ = MO.forward(p, X, store=lambda h: 0.0 * h)
+    np.testing.assert_allclose(s0, np.full(7, np.maximum(p["b2"], 0) @ p["w3"] + p["b3"]), rtol=0, atol=1e-15)
+    g0 = MO.backward(p, X, y, 2.0, store=lambda h: 0.0 * h)
+    assert np.all(g0["W2"] == 0.0)
+    g1 = MO.backward(p, X, y, 2.0, store=lambda h: h)
+    g2 = MO.backward(p, X, y, 2.0)
+    for k in MO.NAMES:
+        np.testing.assert_array_equal(g1[k], g2[k])

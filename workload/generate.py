@@ -329,11 +329,12 @@ def config3_workunit(spec: dict, n_sky: int | None = None, n_sft_total: int | No
 
 
 def config4_workunit(index: int, train: bool = True, n_sft: int = 800, noise_only_frac: float = 0.25,
-                     seed_base: int = 4000) -> Workload:
+                     seed_base: int = 4000, n_signals: int = 1) -> Workload:
     """Learned-proposal workunit: 2 detectors x 800 SFTs, 0.5 Hz band, coarse
     grid 64 x 32 sky (alpha, sin delta) x 900 f x 1 fdot.  A quarter of the
-    workunits are noise only; the rest carry one signal with log-uniform rho
-    in [4, 40], placed on a coarse template."""
+    workunits are noise only; the rest carry n_signals signals (one in the
+    held-out set; training sets may take more) with log-uniform rho in
+    [4, 40], each placed on a coarse template."""
     T = T_SFT
     seed = seed_base + (0 if train else 100000) + index
     dterms = 8
@@ -349,7 +350,7 @@ def config4_workunit(index: int, train: bool = True, n_sft: int = 800, noise_onl
     g = philox(seed, _S_WU)
     noise_only = g.random() < noise_only_frac
     margin = 40.0 / T
-    injs = [] if noise_only else draw_injections(seed, _S_INJ, 1, k0 / T + margin,
+    injs = [] if noise_only else draw_injections(seed, _S_INJ, n_signals, k0 / T + margin,
                                                  (k0 + n_f) / T - margin, 0.0, 0.0, 4.0, 40.0,
                                                  log_rho=True)
     n_a, n_d = 64, 32
