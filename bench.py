@@ -49,9 +49,14 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--compare-forms", action="store_true", help="also time the other storage forms")
-    ap.add_argument("--config", default="workunit", choices=["workunit", "batch"],
+    ap.add_argument("--config", default="workunit", choices=["workunit", "batch", "proposal"],
                     help="workunit: one workunit-sized bank (default); batch: 64 heterogeneous workunits")
     ap.add_argument("--n-wu", type=int, default=64, help="workunits in the batch mode")
+    ap.add_argument("--n-train", type=int, default=512, help="training workunits (proposal mode)")
+    ap.add_argument("--n-test", type=int, default=128, help="held-out workunits (proposal mode)")
+    ap.add_argument("--n-refine", type=int, default=8, help="patches refined per workunit (proposal mode)")
+    ap.add_argument("--train-steps", type=int, default=6000, help="Adam steps (proposal mode)")
+    ap.add_argument("--proposal-sft", type=int, default=800, help="SFTs per detector (proposal mode)")
     ap.add_argument("--tile-m", type=int, default=0, help="templates per thread (0 = planner)")
     ap.add_argument("--tile-warps", type=int, default=0, help="warps per block (0 = planner)")
     ap.add_argument("--sft-chunk", type=int, default=0, help="SFTs per staging round (0 = planner)")
@@ -254,10 +259,72 @@ def run_batch(args):
     print(json.dumps(line))
 
 
+def run_proposal(args):
+    """Learned proposal: coarse 2F maps of 2 det x 800 SFT workunits (64 x 32
+    sky x 900 f), a 8192-256-256-1 network trained on the GPU on windows of
+    the training maps, then on held-out workunits the network's best patches
+    refined on the 8x finer grid; recall against the exhaustive fine grid and
+    end-to-end device time against it."""
+    import torch
+    from paper_0904_1826_gb300 import proposal as PR
+    from workload import config4_workunit
+    torch.cuda.set_device(0)
+    search = PR.ProposalSearch(0, hidden=256, max_batch=1024)
+    rng = np.random.default_rng(11)
+    t0 = time.perf_counter()
+    train = (config4_workunit(i, True, n_sft=args.proposal_sft, n_signals=8) for i in range(args.n_train))
+    X, y = search.training_set(train, rng, 16, 256)
+    t_set = time.perf_counter() - t0
+    search.init_params(np.random.default_rng(1))
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    hist = search.train(X, y, steps=args.train_steps, batch=256, lr=1e-4, pos_frac=0.25, seed=2)
+    e1.record()
+    torch.cuda.synchronize()
+    train_ms = e0.elapsed_time(e1)
+    n_rows, n_pos = int(X.shape[0]), int(y.sum())
+    del X
+    test = [config4_workunit(i, False, n_sft=args.proposal_sft) for i in range(args.n_test)]
+    sampler = ClockSampler(0)
+    sampler.start()
+    t1 = time.perf_counter()
+    res = PR.evaluate(search, test, n_refine=args.n_refine, noise_patches_per_wu=24)
+    t_eval = time.perf_counter() - t1
+    ex_ms = [PR.exhaustive_ms(search, w) for w in test[:2]]
+    clocks = sampler.stop()
+    search.close()
+    ms_learned = res["ms_per_wu_learned"]
+    ms_exh = float(np.mean(ex_ms))
+    line = {"metric": "learned-proposal device time per workunit vs exhaustive fine grid, at stated recall",
+            "value": ms_exh / ms_learned, "unit": "x (speedup)", "n_gpus": 1, "steps": args.n_test, "warmup": 0,
+            "ms_per_step": ms_learned, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 2F, bf16 network (fp32 accumulate)", "data": "synthetic",
+            "config": {"workload": f"learned proposal: 2 det x {args.proposal_sft} SFTs, coarse 64x32 sky x 900 f "
+                                   f"(0.5 Hz at 1/T), patches 16x16x32, fine grid 4x2 sky x 8 f per patch; "
+                                   f"{args.n_train} training WUs (8 signals each or noise), {args.n_test} held-out "
+                                   f"WUs (1 signal or noise), rho log-uniform 4-40, {args.n_refine} of "
+                                   f"{res['n_patches']} patches refined",
+                       "network": "8192-256-256-1 ReLU, BF16 weights/activations, FP32 accumulate, Adam lr 1e-4, "
+                                  f"batch 256, {args.train_steps} steps"},
+            "recall": {k: res[k] for k in ("recall_nn", "recall_coarse_max", "recall_random", "n_signal",
+                                           "n_detected_exhaustive", "threshold", "n_noise_patches")},
+            "ms_per_wu": {"learned_total": ms_learned, "coarse": res["ms_coarse"], "network": res["ms_mlp"],
+                          "refine": res["ms_refine"], "exhaustive_measured": ms_exh,
+                          "exhaustive_from_patch_time": res["ms_per_wu_exhaustive"]},
+            "train": {"rows": n_rows, "positives": n_pos, "device_ms": train_ms, "loss_first": hist[0],
+                      "loss_last": hist[-1], "set_s": t_set},
+            "eval_wall_s": t_eval, "clocks": clocks}
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.config == "proposal":
+        run_proposal(args)
         return
     if args.config == "batch":
         run_batch(args)

@@ -305,3 +305,12 @@ def evaluate(search: ProposalSearch, test_wus, n_refine: int, threshold: float |
                 ms_per_wu_learned=ms_learned, ms_per_wu_exhaustive=ms_exhaustive,
                 speedup=ms_exhaustive / ms_learned, ms_coarse=t_coarse / n_wu, ms_mlp=t_mlp / n_wu,
                 ms_refine=t_ref / n_wu, n_test=len(test_wus), n_noise_patches=len(noise_max))
+
+
+def exhaustive_ms(search: ProposalSearch, w) -> float:
+    """Device milliseconds of the exhaustive fine grid over every patch of a
+    workunit (the method without the proposal)."""
+    search.coarse(w)
+    _, ms = search.refine(w, np.arange(patch_count(w.bank.n_f)))
+    return ms
+
