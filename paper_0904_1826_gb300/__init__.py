@@ -92,6 +92,8 @@ SIGNATURES = {
                                              ctypes.c_float, _P]),
     "fstat_extract_windows": (ctypes.c_int, [_P, _I32, _I32, _I32, _I32, _I32, _P, _I32, ctypes.c_float,
                                              ctypes.c_float, _P]),
+    # include/fstat_noalloc.h
+    "fstat_toplist_noalloc": (ctypes.c_int, [ctypes.c_int, _P, _I64, _I32, _P, _P, _P, ctypes.c_char_p, _I32]),
     # include/fstat_mlp.h
     "fstat_mlp_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, _I32, _I32, _I32]),
     "fstat_mlp_destroy": (None, [_P]),
@@ -356,6 +358,21 @@ def fstat_extract_windows(ctx, n_a: int, n_d: int, s_a: int, s_d: int, n_fp: int
     org = np.ascontiguousarray(origin, dtype=np.int32).reshape(-1, 3)
     _check(ctx, _lib.fstat_extract_windows(ctx, n_a, n_d, s_a, s_d, n_fp, _host_ptr(org), org.shape[0], shift, scale,
                                            ctypes.c_void_p(out.data_ptr())))
+
+
+NOALLOC_MAX_K = 16384
+
+
+def fstat_toplist_noalloc(v, k: int, idx_out, val_out, stream=None) -> None:
+    """Top-k of a CUDA FP32 tensor v into caller-owned CUDA tensors idx_out
+    (int64 [k]) and val_out (float32 [k]) without any device allocation by the
+    library (include/fstat_noalloc.h); asynchronous on `stream`."""
+    msg = ctypes.create_string_buffer(256)
+    rc = _lib.fstat_toplist_noalloc(v.device.index, ctypes.c_void_p(v.data_ptr()), int(v.numel()), int(k),
+                                    ctypes.c_void_p(idx_out.data_ptr()), ctypes.c_void_p(val_out.data_ptr()),
+                                    _stream_handle(stream), msg, len(msg))
+    if rc != FSTAT_OK:
+        raise FstatError(rc, msg.value.decode())
 
 
 MLP_NAMES = ("W1", "b1", "W2", "b2", "w3", "b3")

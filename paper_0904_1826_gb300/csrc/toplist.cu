@@ -7,6 +7,11 @@
 // result is deterministic.  A single block then sorts the K candidates.
 #include "fstat_internal.cuh"
 
+#include <cstdio>
+#include <mutex>
+
+#include "../../include/fstat_noalloc.h"
+
 namespace fs {
 namespace {
 
@@ -248,4 +253,81 @@ cudaError_t launch_topk(const float* v, long long n, int k, TopkWork& w, cudaStr
     return cudaGetLastError();
 }
 
+
+// ---------------------------------------------------------------------------
+// Toplist without device allocation: the same launch sequence as above, with
+// its scratch in one static device array instead of context buffers.
+// Sections (byte offsets, each start 4-byte aligned, the candidates 256-byte
+// aligned): histograms 3 x 2048 words, state 16 words, tie counts for the
+// 1024 collect blocks, the candidate slot counter, then the candidates.
+namespace {
+constexpr int kNaBlocks = 1024;
+constexpr size_t kNaHist = 0;
+constexpr size_t kNaState = kNaHist + sizeof(unsigned int) * 3 * kBins;
+constexpr size_t kNaTies = kNaState + sizeof(unsigned int) * 16;
+constexpr size_t kNaCount = kNaTies + sizeof(unsigned int) * kNaBlocks;
+constexpr size_t kNaIdx = (kNaCount + sizeof(unsigned int) + 255) / 256 * 256;
+constexpr size_t kNaVal = kNaIdx + sizeof(long long) * FSTAT_NOALLOC_MAX_K;
+constexpr size_t kNaBytes = kNaVal + sizeof(float) * FSTAT_NOALLOC_MAX_K;
+static_assert(kNaBytes == 225536, "scratch size stated in fstat_noalloc.h");
+constexpr int kNaMaxDevices = 64;
+
+std::mutex g_na_mutex;
+void* g_na_addr[kNaMaxDevices] = {};
+}  // namespace
 }  // namespace fs
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[fs::kNaBytes];
+
+namespace {
+int na_fail(char* msg, int32_t msg_len, int code, const char* text, long long a = 0, long long b = 0) {
+    if (msg && msg_len > 0) snprintf(msg, (size_t)msg_len, text, a, b);
+    return code;
+}
+}  // namespace
+
+extern "C" int fstat_toplist_noalloc(int device, const float* v, int64_t n, int32_t k, int64_t* idx_out,
+                                     float* val_out, void* cuda_stream, char* msg, int32_t msg_len) {
+    using namespace fs;
+    if (msg && msg_len > 0) msg[0] = 0;
+    if (!v || !idx_out || !val_out) return na_fail(msg, msg_len, FSTAT_EINVAL, "null array pointer");
+    if (k > FSTAT_NOALLOC_MAX_K)
+        return na_fail(msg, msg_len, FSTAT_ERANGE, "k = %lld is above the static scratch limit of %lld", k,
+                       FSTAT_NOALLOC_MAX_K);
+    if (n < 1 || k < 1 || (int64_t)k > n)
+        return na_fail(msg, msg_len, FSTAT_EINVAL, "need 1 <= k <= n (k = %lld, n = %lld)", k, (long long)n);
+    int count = 0;
+    cudaError_t e = cudaGetDeviceCount(&count);
+    if (e != cudaSuccess) return na_fail(msg, msg_len, FSTAT_ECUDA, "cudaGetDeviceCount failed (error %lld)", (long long)e);
+    if (device < 0 || device >= count || device >= kNaMaxDevices)
+        return na_fail(msg, msg_len, FSTAT_EINVAL, "device %lld not available (%lld devices)", device, count);
+    e = cudaSetDevice(device);
+    if (e != cudaSuccess) return na_fail(msg, msg_len, FSTAT_ECUDA, "cudaSetDevice(%lld) failed (error %lld)", device, (long long)e);
+    unsigned char* base = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_na_mutex);
+        if (!g_na_addr[device]) {
+            void* p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess || !p)
+                return na_fail(msg, msg_len, FSTAT_ECUDA, "cudaGetSymbolAddress of the scratch failed on device %lld (error %lld)",
+                               device, (long long)e);
+            g_na_addr[device] = p;
+        }
+        base = static_cast<unsigned char*>(g_na_addr[device]);
+    }
+    TopkWork w{};
+    w.hist = reinterpret_cast<unsigned int*>(base + kNaHist);
+    w.state = reinterpret_cast<unsigned int*>(base + kNaState);
+    w.tie_count = reinterpret_cast<unsigned int*>(base + kNaTies);
+    w.n_cand = reinterpret_cast<unsigned int*>(base + kNaCount);
+    w.cand_idx = reinterpret_cast<long long*>(base + kNaIdx);
+    w.cand_val = reinterpret_cast<float*>(base + kNaVal);
+    w.out_idx = reinterpret_cast<long long*>(idx_out);
+    w.out_val = val_out;
+    w.n_blocks = kNaBlocks;
+    e = launch_topk(v, (long long)n, (int)k, w, static_cast<cudaStream_t>(cuda_stream));
+    if (e != cudaSuccess) return na_fail(msg, msg_len, FSTAT_ECUDA, "toplist launch failed (error %lld)", (long long)e);
+    return FSTAT_OK;
+}
+
