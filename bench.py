@@ -35,7 +35,9 @@ FLOP_PER_PAIR = 100.0          # algorithmic FP32 work of one template.SFT pair 
 N_SM = 152
 FP32_LANES = 128
 METRIC = "template·SFT pairs/s (2F) on 1 GB300, chosen vs plain FP32 form at stated 2F error"
-KERNEL_SOURCES = ["dirichlet.cuh", "dirichlet_c64.cu", "dirichlet_f16.cu", "dirichlet_bf16.cu"]
+KERNEL_SOURCES = {"direct": ["dirichlet.cuh", "dirichlet_c64.cu", "dirichlet_f16.cu", "dirichlet_bf16.cu"],
+                  "farpoly": ["dirichlet.cuh", "dirichlet_far.cu"]}
+KERNEL_NAMES = {"direct": "dirichlet_kernel", "farpoly": "dirichlet_far_kernel"}
 
 
 def parse():
@@ -57,6 +59,8 @@ def parse():
     ap.add_argument("--n-refine", type=int, default=8, help="patches refined per workunit (proposal mode)")
     ap.add_argument("--train-steps", type=int, default=6000, help="Adam steps (proposal mode)")
     ap.add_argument("--proposal-sft", type=int, default=800, help="SFTs per detector (proposal mode)")
+    ap.add_argument("--algo", default="auto", choices=["auto", "direct", "farpoly"],
+                    help="evaluation of the D-term kernel sum")
     ap.add_argument("--tile-m", type=int, default=0, help="templates per thread (0 = planner)")
     ap.add_argument("--tile-warps", type=int, default=0, help="warps per block (0 = planner)")
     ap.add_argument("--sft-chunk", type=int, default=0, help="SFTs per staging round (0 = planner)")
@@ -74,15 +78,15 @@ def workload(rank: int, world: int, n_sky: int):
     return config1(sky=sky_all[rank * n_sky:(rank + 1) * n_sky])
 
 
-def kernel_hash() -> str:
+def kernel_hash(algo: str) -> str:
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in KERNEL_SOURCES[algo]:
         with open(os.path.join(ROOT, "paper_0904_1826_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(form: str):
+def ncu_traffic(form: str, algo: str):
     """DRAM bytes per launch of the Dirichlet kernel from the committed ncu
     summary, if it was taken on the current kernel source (else None)."""
     p = os.path.join(ROOT, "profiles", "dirichlet_counters.json")
@@ -91,8 +95,8 @@ def ncu_traffic(form: str):
             d = json.load(fh)
     except (OSError, ValueError):
         return None
-    e = d.get(form)
-    if not e or e.get("kernel_hash") != kernel_hash():
+    e = d.get(f"{algo}/{form}")
+    if not e or e.get("kernel_hash") != kernel_hash(algo):
         return None
     return e.get("dram_bytes_per_full_launch")
 
@@ -344,7 +348,7 @@ def main():
 
     def make(form):
         g = fs.FStat(local_rank, dterms=w.dterms, topk=w.topk, bins_form=form, tile_m=args.tile_m,
-                     tile_warps=args.tile_warps, sft_chunk=args.sft_chunk)
+                     tile_warps=args.tile_warps, sft_chunk=args.sft_chunk, algo=args.algo)
         g.load_workload(w)
         g.inject(w.injections, w.bank.t_ref)
         return g
@@ -452,8 +456,9 @@ def main():
     clock_mhz = 2070.0
     peak = N_SM * FP32_LANES * 2 * clock_mhz * 1e6 / 1e12       # TFLOP/s, recipe unit counts, max clock
     achieved = FLOP_PER_PAIR * n_pairs / (k_dir / 1e3) / 1e12
+    algo_used = "farpoly" if plan.get("variant", 0) >= 100 else "direct"
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": ncu_traffic(args.form), "kernel": "dirichlet_kernel",
+                "traffic": ncu_traffic(args.form, algo_used), "kernel": KERNEL_NAMES[algo_used],
                 "dirichlet_ms": k_dir, "step_ms_device": k_step,
                 "peak_note": "152 SM x 128 FP32 lanes x 2 flop x 2070 MHz (max SM clock)"}
     if clocks and clocks.get("sm_mhz"):
@@ -464,7 +469,7 @@ def main():
             "data": "synthetic",
             "config": {"workload": "plain workunit: 2 det x 1200 gapped SFT (T=1800 s), 1 Hz band at 100 Hz, "
                                    "8 injected signals; 10000 sky x 1800 f x 10 fdot, D=8, top-1000",
-                       "form": args.form, "pairs_per_step_per_gpu": n_pairs,
+                       "form": args.form, "algo": algo_used, "pairs_per_step_per_gpu": n_pairs,
                        "l2": "per-step working set ~5 GB (bases, 2F array) > 129 MB L2; L2 flushed before timing",
                        "plan": plan},
             "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": int(h2d),

@@ -76,8 +76,18 @@ typedef struct {
     int32_t tile_m;       /* templates per thread (0 = chosen by the tuner) */
     int32_t tile_warps;   /* warps per thread block (0 = chosen by the tuner) */
     int32_t sft_chunk;    /* SFTs staged per shared-memory round (0 = tuner) */
-    int32_t reserved;
+    int32_t algo;         /* fstat_algo: how the D-term kernel sum is evaluated */
 } fstat_opts;
+
+/* Evaluation of the kernel sum over the 2D bins (fstat_opts.algo).
+ * DIRECT: every bin's term, two bins per reciprocal (any D, Kahan allowed).
+ * FARPOLY (D = 8, no Kahan): the four bins next to kappa's poles exactly, the
+ *   other twelve through a degree-5 polynomial in kappa whose coefficients
+ *   are precomputed per SFT and window position (interpolation error below
+ *   5e-6 of each term); needs two tables of 16 and 48 bytes per stored bin
+ *   and SFT.  Batched workunits always use DIRECT.
+ * AUTO: FARPOLY where it applies, else DIRECT. */
+typedef enum { FSTAT_ALGO_AUTO = 0, FSTAT_ALGO_DIRECT = 1, FSTAT_ALGO_FARPOLY = 2 } fstat_algo;
 
 typedef struct {
     double lat_rad;       /* geodetic latitude of the vertex */
@@ -101,8 +111,8 @@ const char *fstat_version(void);
 
 /* Create a context on CUDA device `device`.  opts == NULL takes the defaults
  * (D = 8, complex64 storage, topk = 1000, no Kahan, tuned tiles).
- * Errors: EINVAL (D < 1 or > 64, topk outside 0..16384, unknown form),
- * ECUDA (device unavailable), ENOMEM. */
+ * Errors: EINVAL (D < 1 or > 64, topk outside 0..16384, unknown form or
+ * algo, FARPOLY with D != 8 or Kahan), ECUDA (device unavailable), ENOMEM. */
 int fstat_create(fstat_ctx **out, int device, const fstat_opts *opts);
 
 /* Release the context and all its device memory.  NULL is ignored. */
@@ -188,7 +198,8 @@ int fstat_get_error_flags(fstat_ctx *ctx, int32_t *flags);
 
 /* Tile configuration chosen for the current bank (after fstat_set_templates):
  * out[8] = (P, L, M, warps, sft_chunk, lane-groups per column row,
- *           staged pairs per SFT, kernel variant id). */
+ *           staged pairs per SFT, kernel variant id; ids from 100 up are the
+ *           far-field polynomial form). */
 int fstat_get_plan(fstat_ctx *ctx, int32_t *out);
 
 /* Number of CUDA kernels this context has launched since it was created. */

@@ -34,7 +34,7 @@ class FstatError(RuntimeError):
 class fstat_opts(ctypes.Structure):
     _fields_ = [("dterms", ctypes.c_int32), ("bins_form", ctypes.c_int32), ("topk", ctypes.c_int32),
                 ("kahan", ctypes.c_int32), ("tile_m", ctypes.c_int32), ("tile_warps", ctypes.c_int32),
-                ("sft_chunk", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("sft_chunk", ctypes.c_int32), ("algo", ctypes.c_int32)]
 
 
 class fstat_detector(ctypes.Structure):
@@ -140,10 +140,14 @@ def fstat_version() -> str:
     return _lib.fstat_version().decode()
 
 
+ALGOS = {"auto": 0, "direct": 1, "farpoly": 2}
+
+
 def fstat_create(device: int = 0, dterms: int = 8, bins_form="c64", topk: int = 1000, kahan: bool = False,
-                 tile_m: int = 0, tile_warps: int = 0, sft_chunk: int = 0):
+                 tile_m: int = 0, tile_warps: int = 0, sft_chunk: int = 0, algo="auto"):
     form = FORMS[bins_form] if isinstance(bins_form, str) else int(bins_form)
-    o = fstat_opts(dterms, form, topk, int(bool(kahan)), tile_m, tile_warps, sft_chunk, 0)
+    al = ALGOS[algo] if isinstance(algo, str) else int(algo)
+    o = fstat_opts(dterms, form, topk, int(bool(kahan)), tile_m, tile_warps, sft_chunk, al)
     ctx = _P()
     _check(None, _lib.fstat_create(ctypes.byref(ctx), device, ctypes.byref(o)))
     return ctx

@@ -41,11 +41,20 @@ const VariantRow kVariants[] = {{8, 9, 2, 0}, {8, 7, 2, 0}, {8, 5, 2, 0}, {8, 9,
                                 {8, 5, 2, 1}, {8, 5, 1, 1}, {8, 1, 1, 1}, {0, 1, 1, 0}, {0, 1, 1, 1}};
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
+// Far-field polynomial variants, in the order of FS_FAR_VARIANTS: (M, L); D = 8.
+struct FarRow {
+    int M, L;
+};
+const FarRow kFarVariants[] = {{7, 2}, {5, 2}, {9, 2}, {7, 1}, {9, 1}, {5, 1}, {1, 1}};
+constexpr int kNumFar = sizeof(kFarVariants) / sizeof(kFarVariants[0]);
+constexpr int kFarIdBase = 100;   // variant ids reported for the far-field form
+
 constexpr int kTimedRing = 256;
 
 struct Plan {
     int P = 1, L = 1, M = 1, W = 8, C = 8, lg_row = 1, lg_cta = 32, n_col = 1, chunks_per_col = 1;
     int w_pairs = 0, w_tab = 0, w_raw = 0, variant = 5;
+    bool far = false;   // far-field polynomial form (variant indexes kFarVariants)
     size_t smem = 0;
     long long grid = 0;
 };
@@ -78,6 +87,12 @@ struct fstat_ctx {
     double* d_tstart = nullptr;
     int* d_det_of = nullptr;
     bool sft_dirty = true;          // state / quantisation need refresh
+    bool tab_dirty = true;          // far-field tables need a rebuild
+    FarGamma gam{};                 // far-field interpolation weights
+    float4* d_ptab = nullptr;       // far-field pair table [n_sft][n_pos]
+    float4* d_pcoef = nullptr;      // far-field coefficients [n_sft][4][n_pos]
+    size_t cap_ptab = 0, cap_pcoef = 0;
+    int n_pos = 0;
     // template bank
     bool have_templates = false;
     int n_sky = 0, n_f = 0, n_fdot = 0;
@@ -198,6 +213,129 @@ int pairs_needed(const fstat_ctx* c, int span_templates, int D) {
     return (int)std::ceil((span_templates - 1) * dk_max + spread) + 2 * D + 4;
 }
 
+// Weights of the far-field form: for each far offset k, the monomial
+// coefficients of the degree-kFarDeg polynomial interpolating 0.5 / (kappa - k)
+// at the Chebyshev points of [0, 1] (FP64 Gaussian elimination, stored FP32).
+FarGamma far_gamma() {
+    FarGamma G{};
+    constexpr int N = kFarDeg + 1;
+    for (int i = 0; i < kFarTerms; ++i) {
+        const double k = far_offset(i);
+        double A[N][N + 1];
+        for (int j = 0; j < N; ++j) {
+            const double x = 0.5 + 0.5 * std::cos((2.0 * j + 1.0) * kPi / (2.0 * N));
+            double pw = 1.0;
+            for (int n = 0; n < N; ++n) {
+                A[j][n] = pw;
+                pw *= x;
+            }
+            A[j][N] = 0.5 / (x - k);
+        }
+        for (int col = 0; col < N; ++col) {
+            int piv = col;
+            for (int r = col + 1; r < N; ++r)
+                if (std::fabs(A[r][col]) > std::fabs(A[piv][col])) piv = r;
+            for (int t = 0; t <= N; ++t) std::swap(A[col][t], A[piv][t]);
+            for (int r = 0; r < N; ++r) {
+                if (r == col) continue;
+                const double f = A[r][col] / A[col][col];
+                for (int t = col; t <= N; ++t) A[r][t] -= f * A[col][t];
+            }
+        }
+        for (int n = 0; n < N; ++n) G.g[i][n] = (float)(A[n][N] / A[n][n]);
+    }
+    return G;
+}
+
+bool far_eligible(const fstat_ctx* c) {
+    return c->opts.dterms == 8 && !c->opts.kahan && c->opts.algo != FSTAT_ALGO_DIRECT;
+}
+
+// Plan of the far-field form (D = 8); false when no variant fits.  Cost model
+// per block and SFT: ~40 instructions of set-up per thread plus ~58 per
+// template (polynomial, two near pairs, twiddle, accumulation, 6 table
+// loads), ~8 per staged table entry and plane, ~2000 per round (barrier).
+bool make_far_plan(fstat_ctx* c, int P, int L, bool found, Plan& best) {
+    std::vector<int> Ms;
+    if (found) Ms = (L == 2) ? std::vector<int>{5, 7, 9} : std::vector<int>{5, 7, 9};
+    else Ms = {1};
+    if (c->opts.tile_m > 0) Ms = {c->opts.tile_m};
+    double best_cost = 1e300;
+    bool have = false;
+    for (int M_ : Ms) {
+        const int Lq = (M_ == 1) ? 1 : L;
+        if (M_ > 1 && !found) continue;
+        int fid = -1;
+        for (int i = 0; i < kNumFar; ++i)
+            if (kFarVariants[i].M == M_ && kFarVariants[i].L == Lq) fid = i;
+        if (fid < 0) continue;
+        const int Pv = found ? P : 1;
+        const int PM = Pv * M_;
+        const int lg_full = (c->n_f + PM - 1) / PM;
+        for (int W = Pv; W <= 10; W += Pv) {
+            if (c->opts.tile_warps > 0 && W != c->opts.tile_warps) continue;
+            const int lg_cta = 32 * W / Pv;
+            const int lg_max = std::min(lg_full, lg_cta);
+            for (int lg_row = 1; lg_row <= lg_max; ++lg_row) {
+                const int col_w = lg_row * PM;
+                const int n_col = (c->n_f + col_w - 1) / col_w;
+                const int w_pairs = std::max(pairs_needed(c, col_w, 8), (M_ - 1) * Lq + 2 * 8 + 2);
+                int w_tab = w_pairs;
+                if (Lq == 2) {
+                    int hf = (w_pairs + 1) / 2;
+                    hf += ((4 - hf % 8) + 8) % 8;
+                    w_tab = 2 * hf;
+                }
+                int C = c->opts.sft_chunk > 0 ? c->opts.sft_chunk : 4;
+                size_t smem = farpoly_smem(C, w_tab, c->n_fdot).total;
+                while (C > 1 && smem > 110 * 1024) {
+                    --C;
+                    smem = farpoly_smem(C, w_tab, c->n_fdot).total;
+                }
+                if (smem > 220 * 1024) continue;
+                double cost = 0.0;
+                int chunks_max = 0;
+                for (int col = 0; col < n_col; ++col) {
+                    const int width = std::min(col_w, c->n_f - col * col_w);
+                    const int Gc = (width + PM - 1) / PM;
+                    const long long LG = (long long)c->n_fdot * Gc;
+                    const int chunks = (int)((LG + lg_cta - 1) / lg_cta);
+                    chunks_max = std::max(chunks_max, chunks);
+                    for (int k = 0; k < chunks; ++k) {
+                        const long long lgs = std::min<long long>(lg_cta, LG - (long long)k * lg_cta);
+                        const long long warps = (lgs + 31) / 32 * Pv;
+                        // the barrier of each round idles the block's warps: ~30 % of a round's work / C
+                        cost += ((double)warps * 32.0 * (40.0 + 50.0 * M_) + (double)w_pairs * 4.0 * 8.0) *
+                                (1.0 + 0.3 / C);
+                    }
+                }
+                if (cost < best_cost * 0.999) {
+                    best_cost = cost;
+                    best = Plan{};
+                    best.P = Pv;
+                    best.L = Lq;
+                    best.M = M_;
+                    best.W = W;
+                    best.C = C;
+                    best.lg_row = lg_row;
+                    best.lg_cta = lg_cta;
+                    best.n_col = n_col;
+                    best.chunks_per_col = chunks_max;
+                    best.w_pairs = w_pairs;
+                    best.w_tab = w_tab;
+                    best.w_raw = 0;
+                    best.variant = fid;
+                    best.far = true;
+                    best.smem = smem;
+                    best.grid = (long long)c->n_sky * n_col * chunks_max;
+                    have = true;
+                }
+            }
+        }
+    }
+    return have;
+}
+
 int make_plan(fstat_ctx* c, Plan& out) {
     const int D = c->opts.dterms;
     const int kahan = c->opts.kahan ? 1 : 0;
@@ -214,6 +352,11 @@ int make_plan(fstat_ctx* c, Plan& out) {
                     L = Ls[li];
                     found = true;
                 }
+    }
+    if (far_eligible(c)) {
+        if (make_far_plan(c, P, L, found, out)) return FSTAT_OK;
+        if (c->opts.algo == FSTAT_ALGO_FARPOLY)
+            return fail(c, FSTAT_EINVAL, "no far-field tile plan fits this template bank");
     }
     std::vector<int> Ms;
     if (found) {
@@ -386,6 +529,7 @@ int refresh_sft_state(fstat_ctx* c, cudaStream_t s) {
     // the host vectors are copied asynchronously: wait before they go out of scope
     CUDA_TRY(c, cudaStreamSynchronize(s));
     c->sft_dirty = false;
+    c->tab_dirty = true;
     return FSTAT_OK;
 }
 
@@ -408,11 +552,14 @@ int fstat_create(fstat_ctx** out, int device, const fstat_opts* opts) {
     if (o.bins_form < 0 || o.bins_form > 2) return FSTAT_EINVAL;
     if (o.tile_m < 0 || o.tile_warps < 0 || o.tile_warps > 10 || o.sft_chunk < 0 || o.sft_chunk > 64)
         return FSTAT_EINVAL;
+    if (o.algo < FSTAT_ALGO_AUTO || o.algo > FSTAT_ALGO_FARPOLY) return FSTAT_EINVAL;
+    if (o.algo == FSTAT_ALGO_FARPOLY && (o.dterms != 8 || o.kahan)) return FSTAT_EINVAL;
     int n_dev = 0;
     if (cudaGetDeviceCount(&n_dev) != cudaSuccess || device < 0 || device >= n_dev) return FSTAT_ECUDA;
     fstat_ctx* c = new fstat_ctx();
     c->device = device;
     c->opts = o;
+    c->gam = far_gamma();
     if (set_device(c) != FSTAT_OK) {
         delete c;
         return FSTAT_ECUDA;
@@ -445,7 +592,7 @@ void fstat_destroy(fstat_ctx* c) {
     void* ptrs[] = {c->d_fstart, c->d_base, c->d_bins, c->d_bins16, c->d_scale, c->d_state, c->d_tstart, c->d_det_of, c->d_sky,
                     c->d_fdot, c->d_meta, c->d_kh0, c->d_ph0, c->d_abcd, c->d_comb, c->d_twoF, c->d_err,
                     c->tw.hist, c->tw.state, c->tw.tie_count, c->tw.cand_idx, c->tw.cand_val, c->tw.n_cand,
-                    c->tw.out_idx, c->tw.out_val, c->d_inj_work, c->d_sig};
+                    c->tw.out_idx, c->tw.out_val, c->d_inj_work, c->d_sig, c->d_ptab, c->d_pcoef};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (int i = 0; i < kTimedRing; ++i) {
@@ -630,6 +777,17 @@ int prepare(fstat_ctx* c, cudaStream_t s) {
     if ((rc = grow(c, &c->d_comb, c->cap_comb, (size_t)c->n_sky)) != FSTAT_OK) return rc;
     if ((rc = grow(c, &c->d_twoF, c->cap_twoF, n_twoF)) != FSTAT_OK) return rc;
     if ((rc = ensure_topk(c)) != FSTAT_OK) return rc;
+    if (c->plan.far && c->tab_dirty) {
+        c->n_pos = c->n_bins + 2 * kFarXoff;
+        const size_t n_tab = (size_t)c->n_sft * c->n_pos;
+        if ((rc = grow(c, &c->d_ptab, c->cap_ptab, n_tab)) != FSTAT_OK) return rc;
+        if ((rc = grow(c, &c->d_pcoef, c->cap_pcoef, 3 * n_tab)) != FSTAT_OK) return rc;
+        const void* bins = c->opts.bins_form == FSTAT_BINS_C64 ? (const void*)c->d_bins : (const void*)c->d_bins16;
+        CUDA_TRY(c, launch_far_tables(bins, c->opts.bins_form, c->row, c->n_sft, c->n_bins, c->gam, c->d_ptab,
+                                      c->d_pcoef, c->n_pos, kFarXoff, s));
+        c->launches += 1;
+        c->tab_dirty = false;
+    }
     return FSTAT_OK;
 }
 
@@ -688,12 +846,19 @@ DirichletParams dirichlet_params(const fstat_ctx* c) {
     dp.w_raw = pl.w_raw;
     dp.sft_chunk = pl.C;
     dp.err = c->d_err;
+    if (pl.far) {
+        dp.ptab = c->d_ptab;
+        dp.pcoef = c->d_pcoef;
+        dp.n_pos = c->n_pos;
+        dp.xoff = kFarXoff;
+    }
     return dp;
 }
 
 cudaError_t launch_dir(const fstat_ctx* c, const DirichletParams& dp, long long grid, cudaStream_t s) {
     const Plan& pl = c->plan;
     const int threads = pl.W * 32;
+    if (pl.far) return launch_dirichlet_far(pl.variant, dp, threads, pl.smem, grid, s);
     if (c->opts.bins_form == FSTAT_BINS_C64)
         return launch_dirichlet_c64(pl.variant, dp, c->opts.dterms, threads, pl.smem, grid, s);
     if (c->opts.bins_form == FSTAT_BINS_F16)
@@ -864,7 +1029,7 @@ int fstat_get_plan(fstat_ctx* c, int32_t* out) {
         c->plan_valid = true;
     }
     const Plan& p = c->plan;
-    const int v[8] = {p.P, p.L, p.M, p.W, p.C, p.lg_row, p.w_pairs, p.variant};
+    const int v[8] = {p.P, p.L, p.M, p.W, p.C, p.lg_row, p.w_pairs, p.far ? kFarIdBase + p.variant : p.variant};
     std::memcpy(out, v, sizeof(v));
     return FSTAT_OK;
 }
@@ -938,7 +1103,8 @@ int fstat_autotune(fstat_ctx* c, void* cuda_stream, int32_t* out) {
     else if (c->opts.kahan) Ms = {5};
     else if (c->plan.L == 2) Ms = {5, 7, 9};
     else Ms = {7, 9};
-    const int Cs[3] = {6, 8, 10};
+    std::vector<int> Cs = {6, 8, 10};
+    if (c->plan.far) Cs = {2, 3, 4};
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -958,7 +1124,8 @@ int fstat_autotune(fstat_ctx* c, void* cuda_stream, int32_t* out) {
             const long long want = 4LL * occ * 152;
             const int n_sky_sub = (int)std::min<long long>(c->n_sky, std::max<long long>(1, (want + per_sky - 1) / per_sky));
             if (launch_timing(timing_params(c, n_sky_sub), s) != cudaSuccess) continue;
-            const DirichletParams dp = dirichlet_params(c);
+            DirichletParams dp = dirichlet_params(c);
+            dp.n_sky = n_sky_sub;   // the far-field form orders blocks sky-fastest
             const long long grid = (long long)n_sky_sub * per_sky;
             float t = 1e30f;
             for (int rep = 0; rep < 3; ++rep) {
@@ -1003,7 +1170,9 @@ int fstat_batch_add(fstat_ctx* c, const fstat_workunit* wu, int32_t* wu_id) {
     if (wu->n_det < 1 || wu->n_det > kMaxDet || !wu->det || !wu->n_sft || !wu->t_start || !wu->bins)
         return fail(c, FSTAT_EINVAL, "workunit needs 1..8 detectors with SFTs");
     fstat_ctx* w = nullptr;
-    int rc = fstat_create(&w, c->device, &c->opts);
+    fstat_opts wo = c->opts;
+    wo.algo = FSTAT_ALGO_DIRECT;   // the persistent batch kernel runs the direct form
+    int rc = fstat_create(&w, c->device, &wo);
     if (rc != FSTAT_OK) return fail(c, rc, "workunit context creation failed");
     for (int d = 0; d < wu->n_det; ++d) {
         rc = fstat_set_sfts(w, d, &wu->det[d], wu->Tsft, wu->k_lo, wu->n_bins, wu->n_sft[d], wu->t_start[d],

@@ -1,0 +1,352 @@
+// Far-field polynomial form of the Dirichlet accumulation (D = 8).
+//
+// The SFT term of the F-statistic (Section 2, the kernel sum of Listing 1)
+// sums X_k / (kappa - k) over the 16 bins k0-7 .. k0+8 around khat.  Twelve of
+// them (offsets -7..-2 and 3..8) never come closer than 2 bins to kappa in
+// [0, 1): their sum is smooth in kappa and is replaced by its degree-5
+// interpolant c_0 + c_1 kappa + ... + c_5 kappa^5 (error below 5e-6 of each
+// term), with c_n = sum_k X_{k0+k} gamma[k][n] precomputed once per SFT and
+// window position.  The four bins next to the poles (offsets -1..2) keep the
+// exact pair form with product-form denominators, so a template.SFT pair
+// costs one polynomial (5 packed multiply-adds) and two reciprocals instead of
+// eight pair terms and eight reciprocals.
+//
+// Tables (built by far_tables_kernel from the stored bins, FP32):
+//   ptab [n_sft][n_pos]      (X_b + X_{b+1}, X_{b+1} - X_b) for bin b
+//   pcoef[n_sft][n_pos][3]   record (c0, c1), (c2, c3), (c4, c5) for window k0 = b
+// with position x <-> bin k_lo - xoff + x; bins outside the stored band are 0.
+// A record is 3 x 16 bytes: an odd number of 16-byte slots, so lanes whose
+// records sit an odd number of records apart read without bank conflicts,
+// and a template's three loads share one address (immediate offsets).
+//
+// The block works like the direct kernel (one sky point, one column of
+// frequencies, a run of spindown rows; M templates per thread at stride P
+// whose windows sit L bins apart) but stages both tables for a round of C
+// SFTs with cp.async into a double buffer, so one barrier per round suffices.
+// Blocks are ordered sky-fastest inside a column: the blocks resident at one
+// time read the same column slice of the tables, which stays in L2.
+#include "dirichlet.cuh"
+
+namespace fs {
+namespace {
+
+template <int FORM>
+__global__ void __launch_bounds__(256) far_tables_kernel(const typename RawT<FORM>::T* __restrict__ bins,
+                                                         long long row, int n_sft, int n_bins, const FarGamma gam,
+                                                         float4* __restrict__ ptab, float4* __restrict__ pcoef,
+                                                         int n_pos, int xoff) {
+    using RT = RawT<FORM>;
+    const long long total = (long long)n_sft * n_pos;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int s = (int)(t / n_pos);
+        const int x = (int)(t - (long long)s * n_pos);
+        const int r = x - xoff;   // bin relative to k_lo
+        const typename RT::T* rp = bins + (size_t)s * row;
+        auto X = [&](int i) -> float2 {
+            return (i >= 0 && i < n_bins) ? RT::f2(rp[i]) : make_float2(0.f, 0.f);
+        };
+        const float2 x0 = X(r), x1 = X(r + 1);
+        ptab[t] = make_float4(x0.x + x1.x, x0.y + x1.y, x1.x - x0.x, x1.y - x0.y);
+        float cr[kFarDeg + 1], ci[kFarDeg + 1];
+#pragma unroll
+        for (int n = 0; n <= kFarDeg; ++n) cr[n] = ci[n] = 0.f;
+#pragma unroll
+        for (int i = 0; i < kFarTerms; ++i) {
+            const float2 v = X(r + far_offset(i));
+#pragma unroll
+            for (int n = 0; n <= kFarDeg; ++n) {
+                cr[n] = fmaf(v.x, gam.g[i][n], cr[n]);
+                ci[n] = fmaf(v.y, gam.g[i][n], ci[n]);
+            }
+        }
+        float4* cp = pcoef + (size_t)t * 3;
+        cp[0] = make_float4(cr[0], ci[0], cr[1], ci[1]);
+        cp[1] = make_float4(cr[2], ci[2], cr[3], ci[3]);
+        cp[2] = make_float4(cr[4], ci[4], cr[5], ci[5]);
+    }
+}
+
+// Window sum of one template: far polynomial plus the two exact near pairs.
+// pn: pair entry of offsets (-1, 0); the pair of offsets (1, 2) is STRIDE
+// entries further.  cp: the template's coefficient record.  Same scaling as
+// the pair form of the direct kernel: Q = (1/2) sum_k X_k / (kappa - k).
+template <int STRIDE>
+__device__ __forceinline__ float2 far_window_sum(const float4* __restrict__ pn, const float4* __restrict__ cp,
+                                                 float kap) {
+    const float4 e0 = cp[0], e1 = cp[1], e2 = cp[2];
+    const float2 kk = make_float2(kap, kap);
+    float2 F = make_float2(e2.z, e2.w);
+    F = __ffma2_rn(F, kk, make_float2(e2.x, e2.y));
+    F = __ffma2_rn(F, kk, make_float2(e1.z, e1.w));
+    F = __ffma2_rn(F, kk, make_float2(e1.x, e1.y));
+    F = __ffma2_rn(F, kk, make_float2(e0.z, e0.w));
+    F = __ffma2_rn(F, kk, make_float2(e0.x, e0.y));
+    const float4 n3 = pn[0], n4 = pn[STRIDE];
+    // offsets (-1, 0): Y = 2 kappa + 1, Y^2 - 1 = 4 kappa (kappa + 1)
+    const float k4 = 4.0f * kap;
+    const float r3 = rcp_approx(fmaf(k4, kap, k4));
+    // offsets (1, 2): Y = 2 kappa - 3, Y^2 - 1 = 4 (kappa - 1)(kappa - 2)
+    const float u = kap - 1.0f, u4 = 4.0f * u;
+    const float r4 = rcp_approx(fmaf(u4, u, -u4));
+    const float y3 = fmaf(2.0f, kap, 1.0f), y4 = fmaf(2.0f, kap, -3.0f);
+    const float2 S3 = __ffma2_rn(make_float2(y3, y3), make_float2(n3.x, n3.y), make_float2(n3.z, n3.w));
+    const float2 S4 = __ffma2_rn(make_float2(y4, y4), make_float2(n4.x, n4.y), make_float2(n4.z, n4.w));
+    F = __ffma2_rn(S3, make_float2(r3, r3), F);
+    return __ffma2_rn(S4, make_float2(r4, r4), F);
+}
+
+template <int M, int L>
+__device__ __forceinline__ void far_block(const DirichletParams& p, long long bid, unsigned char* smem) {
+    constexpr int D = 8;
+    constexpr int STRIDE = (L == 2) ? 1 : 2;
+    const int NT = blockDim.x;
+    const int C = p.sft_chunk;
+    const PolySmem lay = farpoly_smem(C, p.w_tab, p.n_fdot);
+    float4* s_pair = reinterpret_cast<float4*>(smem + lay.pairs);           // [2][C][w_tab]
+    float4* s_coef = reinterpret_cast<float4*>(smem + lay.coef);            // [2][C][w_tab][3]
+    SkySftMeta* s_meta = reinterpret_cast<SkySftMeta*>(smem + lay.meta);    // [3][C]
+    SkySftBase* s_base = reinterpret_cast<SkySftBase*>(smem + lay.base);    // [3][C]
+    long long* s_kh0 = reinterpret_cast<long long*>(smem + lay.kh0);        // [3][C][n_fdot]
+    unsigned int* s_ph0 = reinterpret_cast<unsigned int*>(smem + lay.ph0);  // [3][C][n_fdot]
+
+    const int chunk = (int)(bid % p.chunks_per_col);
+    bid /= p.chunks_per_col;
+    const int sky = (int)(bid % p.n_sky);
+    const int col = (int)(bid / p.n_sky);
+    const int PM = p.P * M;
+    const int col_w = p.lg_row * PM;
+    const int j_col0 = col * col_w;
+    const int width = min(col_w, p.n_f - j_col0);
+    const int Gc = (width + PM - 1) / PM;
+    const int LG = p.n_fdot * Gc;
+    const int u0 = chunk * p.lg_cta;
+    if (u0 >= LG) return;
+    const int u_end = min(u0 + p.lg_cta, LG);
+    const int d_lo = u0 / Gc;
+    const int d_hi = (u_end - 1) / Gc;
+    const int n_rows = d_hi - d_lo + 1;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r = warp % p.P;
+    const int ul = (warp / p.P) * 32 + lane;
+    const int u = u0 + ul;
+    const bool active = (ul < p.lg_cta) && (u < u_end);
+    const int uu = active ? u : u0;
+    const int drow = uu / Gc;
+    const int g = uu - drow * Gc;
+    const int j_t = j_col0 + g * PM + r;
+    const int row_i = drow - d_lo;
+    const bool warp_live = __any_sync(0xffffffffu, active);
+    const int half = p.w_tab >> 1;
+
+    const size_t meta0 = (size_t)sky * p.n_sft;
+    const size_t base0 = (size_t)sky * p.n_fdot * p.n_sft;
+    const int n_rounds = (p.n_sft + C - 1) / C;
+
+    auto issue_consts = [&](int rd) {
+        const int a0 = rd * C, slot = rd % 3;
+        const int nc = min(C, p.n_sft - a0);
+        const char* msrc = reinterpret_cast<const char*>(p.meta + meta0 + a0);
+        char* mdst = reinterpret_cast<char*>(s_meta + slot * C);
+        for (int t = threadIdx.x; t < nc * 3; t += NT) cp_async16(mdst + 16 * t, msrc + 16 * t, 16);
+        if (p.base) {
+            const char* bsrc = reinterpret_cast<const char*>(p.base + meta0 + a0);
+            char* bdst = reinterpret_cast<char*>(s_base + slot * C);
+            for (int t = threadIdx.x; t < nc * 2; t += NT) cp_async16(bdst + 16 * t, bsrc + 16 * t, 16);
+            return;
+        }
+        for (int t = threadIdx.x; t < nc * n_rows; t += NT) {
+            const int c = t / n_rows, rr = t - c * n_rows;
+            const size_t o = base0 + (size_t)(d_lo + rr) * p.n_sft + a0 + c;
+            cp_async8(s_kh0 + (slot * C + c) * p.n_fdot + rr, p.kh0 + o);
+            cp_async4(s_ph0 + (slot * C + c) * p.n_fdot + rr, p.ph0 + o);
+        }
+    };
+    // table index 0 of an SFT row <-> bin k_lo + lo_of(m)
+    auto lo_of = [&](const SkySftMeta& m) -> int {
+        const long long kb = m.khmin + (long long)j_col0 * m.dk;
+        return (int)((kb >> 32) - p.k_lo) - (D - 1);
+    };
+    auto issue_tabs = [&](int rd) {
+        const int a0 = rd * C, slot = rd & 1, cslot = rd % 3;
+        const int nc = min(C, p.n_sft - a0);
+        for (int c = 0; c < nc; ++c) {
+            const int x0 = lo_of(s_meta[cslot * C + c]) + p.xoff;
+            const float4* pt = p.ptab + (size_t)(a0 + c) * p.n_pos;
+            const float4* pc = p.pcoef + (size_t)(a0 + c) * 3 * p.n_pos;
+            float4* dpair = s_pair + ((size_t)slot * C + c) * p.w_tab;
+            float4* dcoef = s_coef + ((size_t)slot * C + c) * 3 * p.w_tab;
+            for (int i = threadIdx.x; i < p.w_pairs; i += NT) {
+                const int x = x0 + i;
+                const bool in = (x >= 0) && (x < p.n_pos);
+                const int xs = in ? x : 0;
+                const int nb = in ? 16 : 0;
+                const int tp = tab_pos<L>(i, half);
+                cp_async16(dpair + tp, pt + xs, nb);
+#pragma unroll
+                for (int k = 0; k < 3; ++k) cp_async16(dcoef + 3 * tp + k, pc + 3 * (size_t)xs + k, nb);
+            }
+        }
+    };
+
+    float2 fa[M], fb[M];
+#pragma unroll
+    for (int q = 0; q < M; ++q) fa[q] = fb[q] = make_float2(0.f, 0.f);
+    int bad = 0;
+
+    // prologue: constants of rounds 0 and 1, tables of round 0
+    issue_consts(0);
+    if (n_rounds > 1) issue_consts(1);
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncthreads();
+    issue_tabs(0);
+    cp_async_commit();
+
+    for (int rd = 0; rd < n_rounds; ++rd) {
+        const int a0 = rd * C;
+        const int nc = min(C, p.n_sft - a0);
+        const int cslot = rd % 3, slot = rd & 1;
+        cp_async_wait_all();
+        __syncthreads();   // tables(rd), consts(rd+1) visible; everyone done with round rd-1
+        if (rd + 1 < n_rounds) issue_tabs(rd + 1);
+        if (rd + 2 < n_rounds) issue_consts(rd + 2);
+        cp_async_commit();
+
+        for (int c = 0; c < (warp_live ? nc : 0); ++c) {
+            const SkySftMeta m = s_meta[cslot * C + c];
+            long long kh_row;
+            unsigned int ph0;
+            if (p.base) {
+                const SkySftBase bs = s_base[cslot * C + c];
+                kh_row = bs.kh0 + (long long)drow * bs.dkh;
+                ph0 = bs.ph0 + (unsigned int)drow * bs.dph;
+            } else {
+                kh_row = s_kh0[(cslot * C + c) * p.n_fdot + row_i];
+                ph0 = s_ph0[(cslot * C + c) * p.n_fdot + row_i];
+            }
+            const long long kh = kh_row + (long long)j_t * m.dk;
+            const int k0 = (int)(kh >> 32);
+            const int b = (k0 - (int)p.k_lo) - (D - 1) - lo_of(m);   // first pair of template 0
+            const float4* tab = s_pair + ((size_t)slot * C + c) * p.w_tab;
+            const float4* cf = s_coef + ((size_t)slot * C + c) * 3 * p.w_tab;
+            const float2 a2 = make_float2(m.a, m.a), b2 = make_float2(m.b, m.b);
+            const bool fast = ((int)((kh + m.span) >> 32) == k0 + (M - 1) * L);
+            if (fast) {
+                int bb = b;
+                if (bb < 0 || bb + (M - 1) * L + 2 * (D - 1) >= p.w_pairs) {
+                    bad = 1;
+                    bb = max(0, min(bb, p.w_pairs - 1 - (M - 1) * L - 2 * (D - 1)));
+                }
+                const float4* pn = tab + tab_pos<L>(bb, half) + 3 * STRIDE;
+                const float4* cp = cf + 3 * tab_pos<L>(bb + 7, half);
+                const unsigned int ph = ph0 + (unsigned int)j_t * m.dphi + ((unsigned int)k0 << 31);
+                float sn, cs;
+                __sincosf((float)(int)ph * kPhaseToRad, &sn, &cs);
+                float tw_re = cs, tw_im = -sn;
+                const float kap0 = clamp_kappa(frac_to_float((unsigned int)kh));
+#pragma unroll
+                for (int q = 0; q < M; ++q) {
+                    const float kap = clamp_kappa(fmaf((float)q, m.eps, kap0));
+                    const float2 Q = far_window_sum<STRIDE>(pn + q, cp + 3 * q, kap);
+                    accumulate(tw_re, tw_im, sinpi_unit(kap), Q, a2, b2, fa[q], fb[q]);
+                    if (q + 1 < M) {
+                        const float t = fmaf(tw_re, m.rot_re, -tw_im * m.rot_im);
+                        tw_im = fmaf(tw_re, m.rot_im, tw_im * m.rot_re);
+                        tw_re = t;
+                    }
+                }
+            } else {
+                const long long pdk = (long long)p.P * m.dk;
+#pragma unroll
+                for (int q = 0; q < M; ++q) {
+                    const long long khq = kh + (long long)q * pdk;
+                    const int k0q = (int)(khq >> 32);
+                    const float kap = clamp_kappa(frac_to_float((unsigned int)khq));
+                    const unsigned int phq = ph0 + (unsigned int)(j_t + q * p.P) * m.dphi + ((unsigned int)k0q << 31);
+                    float s2, c2;
+                    __sincosf((float)(int)phq * kPhaseToRad, &s2, &c2);
+                    int bq = b + (k0q - k0);
+                    if (bq < 0 || bq + 2 * (D - 1) >= p.w_pairs) {
+                        bad = 1;
+                        bq = max(0, min(bq, p.w_pairs - 1 - 2 * (D - 1)));
+                    }
+                    const float2 Q = far_window_sum<STRIDE>(tab + tab_pos<L>(bq, half) + 3 * STRIDE,
+                                                            cf + 3 * tab_pos<L>(bq + 7, half), kap);
+                    accumulate(c2, -s2, sinpi_unit(kap), Q, a2, b2, fa[q], fb[q]);
+                }
+            }
+        }
+    }
+    if (bad) atomicOr(p.err, 1);
+    // ---- 2F combine
+    if (!active) return;
+    const float4 cm = p.comb[sky];
+    float* out = p.twoF + ((size_t)sky * p.n_fdot + drow) * p.n_f;
+    const int j_end = j_col0 + width;
+#pragma unroll
+    for (int q = 0; q < M; ++q) {
+        const int j = j_t + q * p.P;
+        if (j < j_end) {
+            const float2 A_ = fa[q], B_ = fb[q];
+            const float v = cm.x * fmaf(A_.x, A_.x, A_.y * A_.y) + cm.y * fmaf(B_.x, B_.x, B_.y * B_.y) +
+                            cm.z * fmaf(A_.x, B_.x, A_.y * B_.y);
+            out[j] = fmaxf(v, 0.0f);
+        }
+    }
+}
+
+template <int M, int L>
+__global__ void __launch_bounds__(kMaxThreads, 2) dirichlet_far_kernel(const DirichletParams p) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    far_block<M, L>(p, (long long)blockIdx.x, smem);
+}
+
+}  // namespace
+
+// Compiled variants of the far-field form: (ID, M, L).
+#define FS_FAR_VARIANTS(X) \
+    X(0, 7, 2)             \
+    X(1, 5, 2)             \
+    X(2, 9, 2)             \
+    X(3, 7, 1)             \
+    X(4, 9, 1)             \
+    X(5, 5, 1)             \
+    X(6, 1, 1)
+
+cudaError_t launch_dirichlet_far(int v, const DirichletParams& p, int threads, size_t smem, long long grid,
+                                 cudaStream_t s) {
+    switch (v) {
+#define FS_FCASE(ID, M_, L_)                                                                              \
+    case ID: {                                                                                            \
+        auto fn = dirichlet_far_kernel<M_, L_>;                                                           \
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        if (e != cudaSuccess) return e;                                                                   \
+        fn<<<(unsigned)grid, threads, smem, s>>>(p);                                                      \
+        return cudaGetLastError();                                                                        \
+    }
+        FS_FAR_VARIANTS(FS_FCASE)
+#undef FS_FCASE
+        default:
+            return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_far_tables(const void* bins, int form, long long row, int n_sft, int n_bins, const FarGamma& gam,
+                              float4* ptab, float4* pcoef, int n_pos, int xoff, cudaStream_t s) {
+    const long long total = (long long)n_sft * n_pos;
+    const int grid = (int)std::min<long long>((total + 255) / 256, 152LL * 16);
+    if (form == FSTAT_BINS_C64)
+        far_tables_kernel<FSTAT_BINS_C64><<<grid, 256, 0, s>>>(static_cast<const float2*>(bins), row, n_sft, n_bins,
+                                                                gam, ptab, pcoef, n_pos, xoff);
+    else if (form == FSTAT_BINS_F16)
+        far_tables_kernel<FSTAT_BINS_F16><<<grid, 256, 0, s>>>(static_cast<const __half2*>(bins), row, n_sft, n_bins,
+                                                                gam, ptab, pcoef, n_pos, xoff);
+    else
+        far_tables_kernel<FSTAT_BINS_BF16><<<grid, 256, 0, s>>>(static_cast<const __nv_bfloat162*>(bins), row, n_sft,
+                                                                 n_bins, gam, ptab, pcoef, n_pos, xoff);
+    return cudaGetLastError();
+}
+
+}  // namespace fs

@@ -83,6 +83,31 @@ struct DirichletParams {
     int w_raw;                 // raw staging row length (bins, multiple of 4)
     int sft_chunk;             // SFTs per staging round
     int* err;                  // device error flags
+    // far-field polynomial form only (null otherwise): per SFT, per window
+    // position x (bin k_lo - xoff + x), the adjacent-bin pair table and the
+    // far-bin polynomial coefficients, one 48-byte record per position
+    const float4* ptab;        // [n_sft][n_pos]
+    const float4* pcoef;       // [n_sft][n_pos][3]
+    int n_pos;                 // positions per SFT row
+    int xoff;                  // position of bin k_lo
+};
+
+// Far-field polynomial form (D = 8): the window's 12 bins at offsets -7..-2
+// and 3..8 from k0 = floor(khat) contribute (1/2) sum X_k / (kappa - k), a
+// smooth function of kappa in [0, 1) (nearest pole 2 away), replaced by its
+// degree-5 interpolant sum_n c_n kappa^n; c_n = sum_k X_{k0+k} gamma[k][n].
+// The four bins -1..2 next to the poles keep the exact pair form.
+constexpr int kFarDeg = 5;
+constexpr int kFarTerms = 12;
+constexpr int kFarXoff = 10;          // positions below k_lo kept in the tables
+struct FarGamma {
+    float g[kFarTerms][kFarDeg + 1];  // [far offset index][power]
+};
+__host__ __device__ constexpr int far_offset(int i) { return i < 6 ? i - 7 : i - 3; }
+
+// Shared-memory layout of the far-field kernel (offsets in bytes).
+struct PolySmem {
+    size_t pairs, coef, meta, base, kh0, ph0, total;
 };
 
 // Shared-memory layout of the Dirichlet kernel (offsets in bytes).
@@ -102,6 +127,19 @@ __host__ __device__ inline DirSmem dirichlet_smem(int sft_chunk, int w_tab, int 
     m.ph0 = smem_align16(m.kh0 + 3 * C * n_fdot * 8);                      // [3][C][n_fdot]
     m.lo = smem_align16(m.ph0 + 3 * C * n_fdot * 4);                       // [2][C][2]
     m.total = smem_align16(m.lo + 2 * C * 8);
+    return m;
+}
+
+__host__ __device__ inline PolySmem farpoly_smem(int sft_chunk, int w_tab, int n_fdot) {
+    PolySmem m;
+    const size_t C = (size_t)sft_chunk;
+    m.pairs = 0;                                                     // float4 [2][C][w_tab]
+    m.coef = smem_align16(m.pairs + 2 * C * w_tab * 16);              // float4 [2][C][w_tab][3]
+    m.meta = smem_align16(m.coef + 6 * C * w_tab * 16);               // [3][C]
+    m.base = smem_align16(m.meta + 3 * C * sizeof(SkySftMeta));       // [3][C]
+    m.kh0 = smem_align16(m.base + 3 * C * sizeof(SkySftBase));        // [3][C][n_fdot]
+    m.ph0 = smem_align16(m.kh0 + 3 * C * n_fdot * 8);                 // [3][C][n_fdot]
+    m.total = smem_align16(m.ph0 + 3 * C * n_fdot * 4);
     return m;
 }
 
@@ -164,6 +202,10 @@ struct TopkWork {
     float* out_val;            // [topk]
     int n_blocks;
 };
+cudaError_t launch_far_tables(const void* bins, int form, long long row, int n_sft, int n_bins, const FarGamma& gam,
+                              float4* ptab, float4* pcoef, int n_pos, int xoff, cudaStream_t s);
+cudaError_t launch_dirichlet_far(int v, const DirichletParams& p, int threads, size_t smem, long long grid,
+                                 cudaStream_t s);
 cudaError_t launch_topk(const float* v, long long n, int k, TopkWork& w, cudaStream_t s);
 
 }  // namespace fs

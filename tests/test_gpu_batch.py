@@ -86,16 +86,17 @@ def test_batch_with_two_kernel_variants(lib):
         g.close()
 
 
-def test_autotune_picks_a_valid_tiling_and_keeps_parity(lib):
+@pytest.mark.parametrize("algo,chunks", [("direct", (6, 8, 10)), ("farpoly", (2, 3, 4))])
+def test_autotune_picks_a_valid_tiling_and_keeps_parity(lib, algo, chunks):
     w = config_mid(n_sky=40, n_f=150, n_fdot=3)
     b = _with_signals(w)
     dets = [DetectorData(d.lat, d.lon, d.az, d.t_start, x) for d, x in zip(w.detectors, b)]
     ref = O.compute_fstat_freq_band(dets, w.T, w.k_lo, w.dterms, w.bank, range(5)).ravel()
-    g = lib.FStat(0, topk=10)
+    g = lib.FStat(0, topk=10, algo=algo)
     try:
         g.load_workload(w, bins_override=b)
         t = g.autotune()
-        assert t["M"] in (5, 7, 9) and t["sft_chunk"] in (6, 8, 10) and t["slice_us"] > 0
+        assert t["M"] in (5, 7, 9) and t["sft_chunk"] in chunks and t["slice_us"] > 0
         g.compute()
         assert g.plan()["M"] == t["M"]
         got = g.twoF(0, ref.size).astype(np.float64)

@@ -99,11 +99,16 @@ def test_sft_timing_and_abcd_match_oracle(lib):
 
 # ---------------------------------------------------------------- kernels (b)-(d): 2F and toplist
 
-def test_config0_parity_and_recovery(lib):
+ALGOS = ["farpoly", "direct"]
+
+
+@pytest.mark.parametrize("algo", ALGOS)
+def test_config0_parity_and_recovery(lib, algo):
     w = config0()
     bins = _oracle_bins(w)
     ref = O.compute_fstat_freq_band(_dets(w, bins), w.T, w.k_lo, w.dterms, w.bank).ravel()
-    out = _gpu(lib, w, bins)
+    out = _gpu(lib, w, bins, algo=algo)
+    assert (out["plan"]["variant"] >= 100) == (algo == "farpoly")
     assert out["flags"] == 0
     _assert_parity(out["twoF"], ref, "config0")
     _check_toplist(out["top"], out["twoF"], ref, w.topk)
@@ -111,29 +116,32 @@ def test_config0_parity_and_recovery(lib):
     assert abs(out["twoF"].max() - 4 - inj.rho ** 2) < 4 * math.sqrt(8 + 4 * inj.rho ** 2)
 
 
+@pytest.mark.parametrize("algo", ALGOS)
 @pytest.mark.parametrize("df_bins,expect", [(1.0, (2, 2)), (0.125, (8, 1)), (2.0, (1, 2)),
                                             (0.5, (4, 2)), (0.37, (1, 1))])
-def test_mid_parity_grids(lib, df_bins, expect):
+def test_mid_parity_grids(lib, df_bins, expect, algo):
     """Workunit-shaped data: 2 gapped detectors, band edges inside the Doppler
     excursion (zero-filled windows), several columns and ragged tails, and
-    frequency spacings that select each thread layout (P, L)."""
+    frequency spacings that select each thread layout (P, L), in both
+    evaluations of the kernel sum."""
     w = config_mid(df_bins=df_bins)
     bins = _oracle_bins(w)
     ref = O.compute_fstat_freq_band(_dets(w, bins), w.T, w.k_lo, w.dterms, w.bank).ravel()
-    out = _gpu(lib, w, bins)
+    out = _gpu(lib, w, bins, algo=algo)
     assert (out["plan"]["P"], out["plan"]["L"]) == expect
     assert out["flags"] == 0
     _assert_parity(out["twoF"], ref, f"mid df={df_bins}/T")
     _check_toplist(out["top"], out["twoF"], ref, w.topk)
 
 
+@pytest.mark.parametrize("algo", ALGOS)
 @pytest.mark.parametrize("tile", [dict(tile_m=7), dict(tile_m=5, tile_warps=4), dict(tile_warps=2, sft_chunk=3),
-                                  dict(tile_m=1), dict(sft_chunk=1)])
-def test_tile_overrides_keep_parity(lib, tile):
+                                  dict(tile_m=1), dict(sft_chunk=1), dict(tile_m=9, sft_chunk=2)])
+def test_tile_overrides_keep_parity(lib, tile, algo):
     w = config_mid(n_f=97, n_fdot=4, n_sky=3)
     bins = _oracle_bins(w)
     ref = O.compute_fstat_freq_band(_dets(w, bins), w.T, w.k_lo, w.dterms, w.bank).ravel()
-    out = _gpu(lib, w, bins, **tile)
+    out = _gpu(lib, w, bins, algo=algo, **tile)
     _assert_parity(out["twoF"], ref, str(tile))
 
 
@@ -258,6 +266,10 @@ def test_errors_are_reported_not_raised_on_device(lib):
         assert e.value.code == lib.FSTAT_EINVAL
         with pytest.raises(lib.FstatError):
             lib.fstat_create(0, dterms=0)
+        for bad_opts in (dict(algo=3), dict(algo="farpoly", dterms=5), dict(algo="farpoly", kahan=True)):
+            with pytest.raises(lib.FstatError) as e:
+                lib.fstat_create(0, **bad_opts)
+            assert e.value.code == lib.FSTAT_EINVAL
     finally:
         g.close()
 
