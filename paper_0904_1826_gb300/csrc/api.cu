@@ -257,7 +257,9 @@ bool far_eligible(const fstat_ctx* c) {
 // loads), ~8 per staged table entry and plane, ~2000 per round (barrier).
 bool make_far_plan(fstat_ctx* c, int P, int L, bool found, Plan& best) {
     std::vector<int> Ms;
-    if (found) Ms = (L == 2) ? std::vector<int>{5, 7, 9} : std::vector<int>{5, 7, 9};
+    // M = 5 measured fastest on GB300 (the wider tiles give up round size to
+    // shared memory); the autotuner also tries 7 and 9
+    if (found) Ms = {5};
     else Ms = {1};
     if (c->opts.tile_m > 0) Ms = {c->opts.tile_m};
     double best_cost = 1e300;
@@ -272,6 +274,7 @@ bool make_far_plan(fstat_ctx* c, int P, int L, bool found, Plan& best) {
         const int Pv = found ? P : 1;
         const int PM = Pv * M_;
         const int lg_full = (c->n_f + PM - 1) / PM;
+        const size_t smem_cap = 110 * 1024;
         for (int W = Pv; W <= 10; W += Pv) {
             if (c->opts.tile_warps > 0 && W != c->opts.tile_warps) continue;
             const int lg_cta = 32 * W / Pv;
@@ -288,7 +291,7 @@ bool make_far_plan(fstat_ctx* c, int P, int L, bool found, Plan& best) {
                 }
                 int C = c->opts.sft_chunk > 0 ? c->opts.sft_chunk : 4;
                 size_t smem = farpoly_smem(C, w_tab, c->n_fdot).total;
-                while (C > 1 && smem > 110 * 1024) {
+                while (C > 1 && smem > smem_cap) {
                     --C;
                     smem = farpoly_smem(C, w_tab, c->n_fdot).total;
                 }
@@ -1101,7 +1104,7 @@ int fstat_autotune(fstat_ctx* c, void* cuda_stream, int32_t* out) {
     std::vector<int> Ms;
     if (c->plan.M == 1) Ms = {1};
     else if (c->opts.kahan) Ms = {5};
-    else if (c->plan.L == 2) Ms = {5, 7, 9};
+    else if (c->plan.L == 2 || c->plan.far) Ms = {5, 7, 9};
     else Ms = {7, 9};
     std::vector<int> Cs = {6, 8, 10};
     if (c->plan.far) Cs = {2, 3, 4};
