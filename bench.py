@@ -31,7 +31,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-FLOP_PER_PAIR = 100.0          # algorithmic FP32 work of one template.SFT pair
+FLOP_PER_PAIR = 100.0          # direct-sum FP32 work of one template.SFT pair: 16 bins x (4 + 1) + 20 per-pair constants
 N_SM = 152
 FP32_LANES = 128
 METRIC = "template·SFT pairs/s (2F) on 1 GB300, chosen vs plain FP32 form at stated 2F error"
