@@ -346,9 +346,10 @@ def main():
     n_pairs = w.n_pairs
     stream = torch.cuda.Stream()
 
-    def make(form):
-        g = fs.FStat(local_rank, dterms=w.dterms, topk=w.topk, bins_form=form, tile_m=args.tile_m,
-                     tile_warps=args.tile_warps, sft_chunk=args.sft_chunk, algo=args.algo)
+    def make(form, kahan=False, algo=None):
+        g = fs.FStat(local_rank, dterms=w.dterms, topk=w.topk, bins_form=form, kahan=kahan, tile_m=args.tile_m,
+                     tile_warps=args.tile_warps, sft_chunk=args.sft_chunk,
+                     algo=args.algo if algo is None else algo)
         g.load_workload(w)
         g.inject(w.injections, w.bank.t_ref)
         return g
@@ -440,12 +441,16 @@ def main():
 
     forms = {}
     if args.compare_forms and rank == 0:
-        for f in ("c64", "f16", "bf16"):
-            if f == args.form:
+        for f, kahan, algo in (("c64", False, "auto"), ("c64", False, "direct"), ("f16", False, "auto"),
+                               ("bf16", False, "auto"), ("c64", True, "direct"), ("f16", True, "direct"),
+                               ("bf16", True, "direct")):
+            if (f, kahan, algo) == (args.form, False, args.algo):
                 continue
-            g2 = make(f)
+            g2 = make(f, kahan, algo)
             ms2, kd2, _, _ = timed_run(g2, args.steps, 1)
-            forms[f] = {"value": n_pairs * args.steps / (ms2 / 1e3), "dirichlet_ms": kd2}
+            name = f + ("+kahan" if kahan else "") + ("" if kahan or algo == "auto" else "/" + algo)
+            forms[name] = {"value": n_pairs * args.steps / (ms2 / 1e3), "dirichlet_ms": kd2,
+                           "algo": "farpoly" if g2.plan()["variant"] >= 100 else "direct"}
             g2.close()
 
     if rank != 0:
