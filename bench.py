@@ -462,8 +462,9 @@ def main():
     peak = N_SM * FP32_LANES * 2 * clock_mhz * 1e6 / 1e12       # TFLOP/s, recipe unit counts, max clock
     achieved = FLOP_PER_PAIR * n_pairs / (k_dir / 1e3) / 1e12
     algo_used = "farpoly" if plan.get("variant", 0) >= 100 else "direct"
+    kernel_name = KERNEL_NAMES[algo_used] if plan.get("variant", 0) < 107 else "dirichlet_far_ring_kernel"
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": ncu_traffic(args.form, algo_used), "kernel": KERNEL_NAMES[algo_used],
+                "traffic": ncu_traffic(args.form, algo_used), "kernel": kernel_name,
                 "dirichlet_ms": k_dir, "step_ms_device": k_step,
                 "peak_note": "152 SM x 128 FP32 lanes x 2 flop x 2070 MHz (max SM clock)"}
     if clocks and clocks.get("sm_mhz"):

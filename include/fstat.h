@@ -74,7 +74,10 @@ typedef struct {
     int32_t topk;         /* toplist length kept by fstat_compute (0..16384) */
     int32_t kahan;        /* 1: compensated (Kahan) summation of Fa, Fb over SFTs */
     int32_t tile_m;       /* templates per thread (0 = chosen by the tuner) */
-    int32_t tile_warps;   /* warps per thread block (0 = chosen by the tuner) */
+    int32_t tile_warps;   /* warps per thread block (0 = chosen by the tuner).  The far-field form on
+                             a uniform spindown grid with L = 2 runs TMA-ring staging (10 compute
+                             warps + 1 copy warp by default; 9 or 11 choose 8 or 10 compute warps);
+                             2..8 or 10 select its shared-memory-round staging instead */
     int32_t sft_chunk;    /* SFTs staged per shared-memory round (0 = tuner) */
     int32_t algo;         /* fstat_algo: how the D-term kernel sum is evaluated */
 } fstat_opts;

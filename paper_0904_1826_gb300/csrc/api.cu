@@ -44,8 +44,10 @@ constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 // Far-field polynomial variants, in the order of FS_FAR_VARIANTS: (M, L); D = 8.
 struct FarRow {
     int M, L;
+    int ring;   // compute warps of the TMA-ring staging (L = 2, uniform spindown grid), 0 = cp.async rounds
 };
-const FarRow kFarVariants[] = {{7, 2}, {5, 2}, {9, 2}, {7, 1}, {9, 1}, {5, 1}, {1, 1}};
+const FarRow kFarVariants[] = {{7, 2, 0}, {5, 2, 0}, {9, 2, 0}, {7, 1, 0}, {9, 1, 0}, {5, 1, 0},
+                               {1, 1, 0}, {5, 2, 8}, {7, 2, 8}, {9, 2, 8}, {5, 2, 10}, {7, 2, 10}};
 constexpr int kNumFar = sizeof(kFarVariants) / sizeof(kFarVariants[0]);
 constexpr int kFarIdBase = 100;   // variant ids reported for the far-field form
 
@@ -55,6 +57,7 @@ struct Plan {
     int P = 1, L = 1, M = 1, W = 8, C = 8, lg_row = 1, lg_cta = 32, n_col = 1, chunks_per_col = 1;
     int w_pairs = 0, w_tab = 0, w_raw = 0, variant = 5;
     bool far = false;   // far-field polynomial form (variant indexes kFarVariants)
+    bool ring = false;  // far-field form with TMA-ring staging; C = stages, W includes the producer warp
     size_t smem = 0;
     long long grid = 0;
 };
@@ -92,7 +95,8 @@ struct fstat_ctx {
     float4* d_ptab = nullptr;       // far-field pair table [n_sft][n_pos]
     float4* d_pcoef = nullptr;      // far-field coefficients [n_sft][4][n_pos]
     size_t cap_ptab = 0, cap_pcoef = 0;
-    int n_pos = 0;
+    int n_pos = 0, far_xoff = 0;     // table extent of the current plan
+    int tab_npos = -1, tab_xoff = -1; // extent the built tables have
     // template bank
     bool have_templates = false;
     int n_sky = 0, n_f = 0, n_fdot = 0;
@@ -251,11 +255,115 @@ bool far_eligible(const fstat_ctx* c) {
     return c->opts.dterms == 8 && !c->opts.kahan && c->opts.algo != FSTAT_ALGO_DIRECT;
 }
 
+// Extent of the far-field tables such that every block's rows [x0, x0 + w_pairs)
+// lie inside them: khat is bounded over the bank by the frequency and spindown
+// ranges, |tdot - 1| <= 1.1e-4 (orbital + rotational speed over c) and dtau
+// within the SFT span of t_ref widened by 500 s of Roemer delay.
+void far_extent(const fstat_ctx* c, int w_pairs, int* xoff, int* n_pos) {
+    double tmin = 1e300, tmax = -1e300;
+    for (int d = 0; d < kMaxDet; ++d)
+        for (double t : c->det[d].t_start) {
+            tmin = std::min(tmin, t);
+            tmax = std::max(tmax, t + c->T);
+        }
+    double fdmin = c->h_fdot[0], fdmax = c->h_fdot[0];
+    for (double v : c->h_fdot) {
+        fdmin = std::min(fdmin, v);
+        fdmax = std::max(fdmax, v);
+    }
+    const double fs[2] = {c->f0, c->f0 + (c->n_f - 1) * c->df};
+    const double fds[2] = {fdmin, fdmax};
+    const double dts[2] = {tmin - c->t_ref - 500.0, tmax - c->t_ref + 500.0};
+    const double tds[2] = {1.0 - 1.1e-4, 1.0 + 1.1e-4};
+    double kmin = 1e300, kmax = -1e300;
+    for (double f : fs)
+        for (double fd : fds)
+            for (double dt : dts)
+                for (double td : tds) {
+                    const double k = (f + fd * dt) * td * c->T;
+                    kmin = std::min(kmin, k);
+                    kmax = std::max(kmax, k);
+                }
+    const long long lo_min = (long long)std::floor(kmin) - c->k_lo - 7 - 2;
+    const long long lo_max = (long long)std::floor(kmax) - c->k_lo - 7 + 2;
+    const long long xo = std::max<long long>(kFarXoff, -lo_min);
+    long long np = std::max<long long>(c->n_bins + xo + kFarXoff, xo + lo_max + w_pairs + 2);
+    *xoff = (int)xo;
+    *n_pos = (int)((np + 1) & ~1LL);   // even: two equal parity halves
+}
+
 // Plan of the far-field form (D = 8); false when no variant fits.  Cost model
 // per block and SFT: ~40 instructions of set-up per thread plus ~58 per
 // template (polynomial, two near pairs, twiddle, accumulation, 6 table
 // loads), ~8 per staged table entry and plane, ~2000 per round (barrier).
 bool make_far_plan(fstat_ctx* c, int P, int L, bool found, Plan& best) {
+    bool have_ring = false;
+    // TMA-ring form first: L = 2, compact spindown bases
+    // default: 10 compute warps + 1 copy warp (measured fastest on GB300); tile_warps 9 / 11 choose 8 / 10
+    if (found && L == 2 && c->fdot_uniform && (c->opts.tile_warps == 0 || c->opts.tile_warps >= 9)) {
+        std::vector<int> Mr = {7, 5, 9};
+        if (c->opts.tile_m > 0) Mr = {c->opts.tile_m};
+        const int nwc = c->opts.tile_warps ? c->opts.tile_warps - 1 : 10;   // the last warp produces
+        double best_r = 1e300;
+        for (int M_ : Mr) {
+            int fid = -1;
+            for (int i = 0; i < kNumFar; ++i)
+                if (kFarVariants[i].ring == nwc && kFarVariants[i].M == M_) fid = i;
+            if (fid < 0) continue;
+            const int PM = P * M_;
+            const int lg_cta = 32 * nwc / P;
+            const int lg_max = std::min((c->n_f + PM - 1) / PM, lg_cta);
+            for (int lg_row = 1; lg_row <= lg_max; ++lg_row) {
+                const int col_w = lg_row * PM;
+                const int n_col = (c->n_f + col_w - 1) / col_w;
+                const int w_pairs = std::max(pairs_needed(c, col_w, 8), (M_ - 1) * 2 + 2 * 8 + 2);
+                int hf = (w_pairs + 1) / 2;
+                hf += ((4 - hf % 8) + 8) % 8;
+                const int w_tab = 2 * hf;
+                int S = c->opts.sft_chunk > 0 ? c->opts.sft_chunk : 8;
+                while (S > 3 && ring_smem(S, w_tab).total > 110 * 1024) --S;
+                const size_t smem = ring_smem(S, w_tab).total;
+                if (smem > 220 * 1024) continue;
+                double cost = 0.0;
+                int chunks_max = 0;
+                for (int col = 0; col < n_col; ++col) {
+                    const int width = std::min(col_w, c->n_f - col * col_w);
+                    const int Gc = (width + PM - 1) / PM;
+                    const long long LG = (long long)c->n_fdot * Gc;
+                    const int chunks = (int)((LG + lg_cta - 1) / lg_cta);
+                    chunks_max = std::max(chunks_max, chunks);
+                    for (int k = 0; k < chunks; ++k) {
+                        const long long lgs = std::min<long long>(lg_cta, LG - (long long)k * lg_cta);
+                        const long long warps = (lgs + 31) / 32 * P;
+                        // fewer stages leave less slack between the fastest and slowest warp
+                        cost += (double)warps * 32.0 * (40.0 + 50.0 * M_) * (1.0 + 0.2 / S) + 0.05 * w_pairs * 64.0;
+                    }
+                }
+                if (cost < best_r * 0.999) {
+                    best_r = cost;
+                    best = Plan{};
+                    best.P = P;
+                    best.L = 2;
+                    best.M = M_;
+                    best.W = nwc + 1;
+                    best.C = S;
+                    best.lg_row = lg_row;
+                    best.lg_cta = lg_cta;
+                    best.n_col = n_col;
+                    best.chunks_per_col = chunks_max;
+                    best.w_pairs = w_pairs;
+                    best.w_tab = w_tab;
+                    best.variant = fid;
+                    best.far = true;
+                    best.ring = true;
+                    best.smem = smem;
+                    best.grid = (long long)c->n_sky * n_col * chunks_max;
+                    have_ring = true;
+                }
+            }
+        }
+        if (have_ring) return true;
+    }
     std::vector<int> Ms;
     // M = 5 measured fastest on GB300 (the wider tiles give up round size to
     // shared memory); the autotuner also tries 7 and 9
@@ -269,7 +377,7 @@ bool make_far_plan(fstat_ctx* c, int P, int L, bool found, Plan& best) {
         if (M_ > 1 && !found) continue;
         int fid = -1;
         for (int i = 0; i < kNumFar; ++i)
-            if (kFarVariants[i].M == M_ && kFarVariants[i].L == Lq) fid = i;
+            if (kFarVariants[i].ring == 0 && kFarVariants[i].M == M_ && kFarVariants[i].L == Lq) fid = i;
         if (fid < 0) continue;
         const int Pv = found ? P : 1;
         const int PM = Pv * M_;
@@ -312,7 +420,7 @@ bool make_far_plan(fstat_ctx* c, int P, int L, bool found, Plan& best) {
                                 (1.0 + 0.3 / C);
                     }
                 }
-                if (cost < best_cost * 0.999) {
+                if (cost < best_cost * 0.999 && !have_ring) {
                     best_cost = cost;
                     best = Plan{};
                     best.P = Pv;
@@ -553,7 +661,7 @@ int fstat_create(fstat_ctx** out, int device, const fstat_opts* opts) {
     if (o.dterms < 1 || o.dterms > 64) return FSTAT_EINVAL;
     if (o.topk < 0 || o.topk > 16384) return FSTAT_EINVAL;
     if (o.bins_form < 0 || o.bins_form > 2) return FSTAT_EINVAL;
-    if (o.tile_m < 0 || o.tile_warps < 0 || o.tile_warps > 10 || o.sft_chunk < 0 || o.sft_chunk > 64)
+    if (o.tile_m < 0 || o.tile_warps < 0 || o.tile_warps > 11 || o.sft_chunk < 0 || o.sft_chunk > 64)
         return FSTAT_EINVAL;
     if (o.algo < FSTAT_ALGO_AUTO || o.algo > FSTAT_ALGO_FARPOLY) return FSTAT_EINVAL;
     if (o.algo == FSTAT_ALGO_FARPOLY && (o.dterms != 8 || o.kahan)) return FSTAT_EINVAL;
@@ -780,16 +888,18 @@ int prepare(fstat_ctx* c, cudaStream_t s) {
     if ((rc = grow(c, &c->d_comb, c->cap_comb, (size_t)c->n_sky)) != FSTAT_OK) return rc;
     if ((rc = grow(c, &c->d_twoF, c->cap_twoF, n_twoF)) != FSTAT_OK) return rc;
     if ((rc = ensure_topk(c)) != FSTAT_OK) return rc;
-    if (c->plan.far && c->tab_dirty) {
-        c->n_pos = c->n_bins + 2 * kFarXoff;
+    if (c->plan.far) far_extent(c, c->plan.w_pairs, &c->far_xoff, &c->n_pos);
+    if (c->plan.far && (c->tab_dirty || c->tab_npos != c->n_pos || c->tab_xoff != c->far_xoff)) {
         const size_t n_tab = (size_t)c->n_sft * c->n_pos;
         if ((rc = grow(c, &c->d_ptab, c->cap_ptab, n_tab)) != FSTAT_OK) return rc;
         if ((rc = grow(c, &c->d_pcoef, c->cap_pcoef, 3 * n_tab)) != FSTAT_OK) return rc;
         const void* bins = c->opts.bins_form == FSTAT_BINS_C64 ? (const void*)c->d_bins : (const void*)c->d_bins16;
         CUDA_TRY(c, launch_far_tables(bins, c->opts.bins_form, c->row, c->n_sft, c->n_bins, c->gam, c->d_ptab,
-                                      c->d_pcoef, c->n_pos, kFarXoff, s));
+                                      c->d_pcoef, c->n_pos, c->far_xoff, s));
         c->launches += 1;
         c->tab_dirty = false;
+        c->tab_npos = c->n_pos;
+        c->tab_xoff = c->far_xoff;
     }
     return FSTAT_OK;
 }
@@ -853,7 +963,7 @@ DirichletParams dirichlet_params(const fstat_ctx* c) {
         dp.ptab = c->d_ptab;
         dp.pcoef = c->d_pcoef;
         dp.n_pos = c->n_pos;
-        dp.xoff = kFarXoff;
+        dp.xoff = c->far_xoff;
     }
     return dp;
 }
@@ -1107,7 +1217,8 @@ int fstat_autotune(fstat_ctx* c, void* cuda_stream, int32_t* out) {
     else if (c->plan.L == 2 || c->plan.far) Ms = {5, 7, 9};
     else Ms = {7, 9};
     std::vector<int> Cs = {6, 8, 10};
-    if (c->plan.far) Cs = {2, 3, 4};
+    if (c->plan.ring) Cs = {4, 6, 8};
+    else if (c->plan.far) Cs = {2, 3, 4};
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);

@@ -11,9 +11,11 @@
 // costs one polynomial (5 packed multiply-adds) and two reciprocals instead of
 // eight pair terms and eight reciprocals.
 //
-// Tables (built by far_tables_kernel from the stored bins, FP32):
-//   ptab [n_sft][n_pos]      (X_b + X_{b+1}, X_{b+1} - X_b) for bin b
-//   pcoef[n_sft][n_pos][3]   record (c0, c1), (c2, c3), (c4, c5) for window k0 = b
+// Tables (built by far_tables_kernel from the stored bins, FP32), split by
+// the parity of the position so that a block's entries of one parity are one
+// contiguous run (half = n_pos / 2, position x at [x & 1][x >> 1]):
+//   ptab [n_sft][2][half]      (X_b + X_{b+1}, X_{b+1} - X_b) for bin b
+//   pcoef[n_sft][2][half][3]   record (c0, c1), (c2, c3), (c4, c5) for window k0 = b
 // with position x <-> bin k_lo - xoff + x; bins outside the stored band are 0.
 // A record is 3 x 16 bytes: an odd number of 16-byte slots, so lanes whose
 // records sit an odd number of records apart read without bank conflicts,
@@ -21,8 +23,13 @@
 //
 // The block works like the direct kernel (one sky point, one column of
 // frequencies, a run of spindown rows; M templates per thread at stride P
-// whose windows sit L bins apart) but stages both tables for a round of C
-// SFTs with cp.async into a double buffer, so one barrier per round suffices.
+// whose windows sit L bins apart).  Two stagings:
+//  * far_block: every thread stages rounds of C SFTs with cp.async into a
+//    double buffer, one barrier per round (any L, any spindown list);
+//  * far_ring_block (L = 2, uniform spindown grid): one producer warp copies
+//    each SFT's rows with TMA bulk copies into a ring of S stages guarded by
+//    mbarriers (full: copies landed; empty: all compute warps done), so
+//    compute warps run up to S SFTs apart and never meet at a block barrier.
 // Blocks are ordered sky-fastest inside a column: the blocks resident at one
 // time read the same column slice of the tables, which stays in L2.
 #include "dirichlet.cuh"
@@ -46,8 +53,9 @@ __global__ void __launch_bounds__(256) far_tables_kernel(const typename RawT<FOR
         auto X = [&](int i) -> float2 {
             return (i >= 0 && i < n_bins) ? RT::f2(rp[i]) : make_float2(0.f, 0.f);
         };
+        const size_t o = (size_t)s * n_pos + (size_t)(x & 1) * (n_pos >> 1) + (x >> 1);   // parity-split slot
         const float2 x0 = X(r), x1 = X(r + 1);
-        ptab[t] = make_float4(x0.x + x1.x, x0.y + x1.y, x1.x - x0.x, x1.y - x0.y);
+        ptab[o] = make_float4(x0.x + x1.x, x0.y + x1.y, x1.x - x0.x, x1.y - x0.y);
         float cr[kFarDeg + 1], ci[kFarDeg + 1];
 #pragma unroll
         for (int n = 0; n <= kFarDeg; ++n) cr[n] = ci[n] = 0.f;
@@ -60,7 +68,7 @@ __global__ void __launch_bounds__(256) far_tables_kernel(const typename RawT<FOR
                 ci[n] = fmaf(v.y, gam.g[i][n], ci[n]);
             }
         }
-        float4* cp = pcoef + (size_t)t * 3;
+        float4* cp = pcoef + o * 3;
         cp[0] = make_float4(cr[0], ci[0], cr[1], ci[1]);
         cp[1] = make_float4(cr[2], ci[2], cr[3], ci[3]);
         cp[2] = make_float4(cr[4], ci[4], cr[5], ci[5]);
@@ -96,10 +104,89 @@ __device__ __forceinline__ float2 far_window_sum(const float4* __restrict__ pn, 
     return __ffma2_rn(S4, make_float2(r4, r4), F);
 }
 
+// One SFT of one thread's M templates: kh_row / ph0 are the fixed-point bin
+// and phase bases of the thread's spindown row, lo_rel the bin of the staged
+// rows' entry 0 relative to k_lo, tab / cf the staged pair and coefficient
+// rows (parity-split for L = 2).
+template <int M, int L>
+__device__ __forceinline__ void far_sft(const DirichletParams& p, const SkySftMeta& m, long long kh_row,
+                                        unsigned int ph0, int lo_rel, const float4* __restrict__ tab,
+                                        const float4* __restrict__ cf, int half, int j_t, float2 (&fa)[M],
+                                        float2 (&fb)[M], int& bad) {
+    constexpr int D = 8;
+    constexpr int STRIDE = (L == 2) ? 1 : 2;
+    const long long kh = kh_row + (long long)j_t * m.dk;
+    const int k0 = (int)(kh >> 32);
+    const int b = (k0 - (int)p.k_lo) - (D - 1) - lo_rel;   // first pair of template 0
+    const float2 a2 = make_float2(m.a, m.a), b2 = make_float2(m.b, m.b);
+    const bool fast = ((int)((kh + m.span) >> 32) == k0 + (M - 1) * L);
+    if (fast) {
+        int bb = b;
+        if (bb < 0 || bb + (M - 1) * L + 2 * (D - 1) >= p.w_pairs) {
+            bad = 1;
+            bb = max(0, min(bb, p.w_pairs - 1 - (M - 1) * L - 2 * (D - 1)));
+        }
+        const float4* pn = tab + tab_pos<L>(bb, half) + 3 * STRIDE;
+        const float4* cp = cf + 3 * tab_pos<L>(bb + 7, half);
+        const unsigned int ph = ph0 + (unsigned int)j_t * m.dphi + ((unsigned int)k0 << 31);
+        float sn, cs;
+        __sincosf((float)(int)ph * kPhaseToRad, &sn, &cs);
+        float tw_re = cs, tw_im = -sn;
+        const float kap0 = clamp_kappa(frac_to_float((unsigned int)kh));
+#pragma unroll
+        for (int q = 0; q < M; ++q) {
+            const float kap = clamp_kappa(fmaf((float)q, m.eps, kap0));
+            const float2 Q = far_window_sum<STRIDE>(pn + q, cp + 3 * q, kap);
+            accumulate(tw_re, tw_im, sinpi_unit(kap), Q, a2, b2, fa[q], fb[q]);
+            if (q + 1 < M) {
+                const float t = fmaf(tw_re, m.rot_re, -tw_im * m.rot_im);
+                tw_im = fmaf(tw_re, m.rot_im, tw_im * m.rot_re);
+                tw_re = t;
+            }
+        }
+    } else {
+        const long long pdk = (long long)p.P * m.dk;
+#pragma unroll
+        for (int q = 0; q < M; ++q) {
+            const long long khq = kh + (long long)q * pdk;
+            const int k0q = (int)(khq >> 32);
+            const float kap = clamp_kappa(frac_to_float((unsigned int)khq));
+            const unsigned int phq = ph0 + (unsigned int)(j_t + q * p.P) * m.dphi + ((unsigned int)k0q << 31);
+            float s2, c2;
+            __sincosf((float)(int)phq * kPhaseToRad, &s2, &c2);
+            int bq = b + (k0q - k0);
+            if (bq < 0 || bq + 2 * (D - 1) >= p.w_pairs) {
+                bad = 1;
+                bq = max(0, min(bq, p.w_pairs - 1 - 2 * (D - 1)));
+            }
+            const float2 Q = far_window_sum<STRIDE>(tab + tab_pos<L>(bq, half) + 3 * STRIDE,
+                                                    cf + 3 * tab_pos<L>(bq + 7, half), kap);
+            accumulate(c2, -s2, sinpi_unit(kap), Q, a2, b2, fa[q], fb[q]);
+        }
+    }
+}
+
+// 2F of a thread's M templates (fused combine, written once per template).
+template <int M>
+__device__ __forceinline__ void far_store(const DirichletParams& p, int sky, int drow, int j_t, int j_end,
+                                          const float2 (&fa)[M], const float2 (&fb)[M]) {
+    const float4 cm = p.comb[sky];
+    float* out = p.twoF + ((size_t)sky * p.n_fdot + drow) * p.n_f;
+#pragma unroll
+    for (int q = 0; q < M; ++q) {
+        const int j = j_t + q * p.P;
+        if (j < j_end) {
+            const float2 A_ = fa[q], B_ = fb[q];
+            const float v = cm.x * fmaf(A_.x, A_.x, A_.y * A_.y) + cm.y * fmaf(B_.x, B_.x, B_.y * B_.y) +
+                            cm.z * fmaf(A_.x, B_.x, A_.y * B_.y);
+            out[j] = fmaxf(v, 0.0f);
+        }
+    }
+}
+
 template <int M, int L>
 __device__ __forceinline__ void far_block(const DirichletParams& p, long long bid, unsigned char* smem) {
     constexpr int D = 8;
-    constexpr int STRIDE = (L == 2) ? 1 : 2;
     const int NT = blockDim.x;
     const int C = p.sft_chunk;
     const PolySmem lay = farpoly_smem(C, p.w_tab, p.n_fdot);
@@ -173,19 +260,19 @@ __device__ __forceinline__ void far_block(const DirichletParams& p, long long bi
         const int nc = min(C, p.n_sft - a0);
         for (int c = 0; c < nc; ++c) {
             const int x0 = lo_of(s_meta[cslot * C + c]) + p.xoff;
-            const float4* pt = p.ptab + (size_t)(a0 + c) * p.n_pos;
-            const float4* pc = p.pcoef + (size_t)(a0 + c) * 3 * p.n_pos;
+            const size_t row0 = (size_t)(a0 + c) * p.n_pos;
+            const int nh = p.n_pos >> 1;
             float4* dpair = s_pair + ((size_t)slot * C + c) * p.w_tab;
             float4* dcoef = s_coef + ((size_t)slot * C + c) * 3 * p.w_tab;
             for (int i = threadIdx.x; i < p.w_pairs; i += NT) {
                 const int x = x0 + i;
                 const bool in = (x >= 0) && (x < p.n_pos);
-                const int xs = in ? x : 0;
+                const size_t o = row0 + (in ? (size_t)(x & 1) * nh + (x >> 1) : 0);
                 const int nb = in ? 16 : 0;
                 const int tp = tab_pos<L>(i, half);
-                cp_async16(dpair + tp, pt + xs, nb);
+                cp_async16(dpair + tp, p.ptab + o, nb);
 #pragma unroll
-                for (int k = 0; k < 3; ++k) cp_async16(dcoef + 3 * tp + k, pc + 3 * (size_t)xs + k, nb);
+                for (int k = 0; k < 3; ++k) cp_async16(dcoef + 3 * tp + k, p.pcoef + 3 * o + k, nb);
             }
         }
     };
@@ -226,75 +313,12 @@ __device__ __forceinline__ void far_block(const DirichletParams& p, long long bi
                 kh_row = s_kh0[(cslot * C + c) * p.n_fdot + row_i];
                 ph0 = s_ph0[(cslot * C + c) * p.n_fdot + row_i];
             }
-            const long long kh = kh_row + (long long)j_t * m.dk;
-            const int k0 = (int)(kh >> 32);
-            const int b = (k0 - (int)p.k_lo) - (D - 1) - lo_of(m);   // first pair of template 0
-            const float4* tab = s_pair + ((size_t)slot * C + c) * p.w_tab;
-            const float4* cf = s_coef + ((size_t)slot * C + c) * 3 * p.w_tab;
-            const float2 a2 = make_float2(m.a, m.a), b2 = make_float2(m.b, m.b);
-            const bool fast = ((int)((kh + m.span) >> 32) == k0 + (M - 1) * L);
-            if (fast) {
-                int bb = b;
-                if (bb < 0 || bb + (M - 1) * L + 2 * (D - 1) >= p.w_pairs) {
-                    bad = 1;
-                    bb = max(0, min(bb, p.w_pairs - 1 - (M - 1) * L - 2 * (D - 1)));
-                }
-                const float4* pn = tab + tab_pos<L>(bb, half) + 3 * STRIDE;
-                const float4* cp = cf + 3 * tab_pos<L>(bb + 7, half);
-                const unsigned int ph = ph0 + (unsigned int)j_t * m.dphi + ((unsigned int)k0 << 31);
-                float sn, cs;
-                __sincosf((float)(int)ph * kPhaseToRad, &sn, &cs);
-                float tw_re = cs, tw_im = -sn;
-                const float kap0 = clamp_kappa(frac_to_float((unsigned int)kh));
-#pragma unroll
-                for (int q = 0; q < M; ++q) {
-                    const float kap = clamp_kappa(fmaf((float)q, m.eps, kap0));
-                    const float2 Q = far_window_sum<STRIDE>(pn + q, cp + 3 * q, kap);
-                    accumulate(tw_re, tw_im, sinpi_unit(kap), Q, a2, b2, fa[q], fb[q]);
-                    if (q + 1 < M) {
-                        const float t = fmaf(tw_re, m.rot_re, -tw_im * m.rot_im);
-                        tw_im = fmaf(tw_re, m.rot_im, tw_im * m.rot_re);
-                        tw_re = t;
-                    }
-                }
-            } else {
-                const long long pdk = (long long)p.P * m.dk;
-#pragma unroll
-                for (int q = 0; q < M; ++q) {
-                    const long long khq = kh + (long long)q * pdk;
-                    const int k0q = (int)(khq >> 32);
-                    const float kap = clamp_kappa(frac_to_float((unsigned int)khq));
-                    const unsigned int phq = ph0 + (unsigned int)(j_t + q * p.P) * m.dphi + ((unsigned int)k0q << 31);
-                    float s2, c2;
-                    __sincosf((float)(int)phq * kPhaseToRad, &s2, &c2);
-                    int bq = b + (k0q - k0);
-                    if (bq < 0 || bq + 2 * (D - 1) >= p.w_pairs) {
-                        bad = 1;
-                        bq = max(0, min(bq, p.w_pairs - 1 - 2 * (D - 1)));
-                    }
-                    const float2 Q = far_window_sum<STRIDE>(tab + tab_pos<L>(bq, half) + 3 * STRIDE,
-                                                            cf + 3 * tab_pos<L>(bq + 7, half), kap);
-                    accumulate(c2, -s2, sinpi_unit(kap), Q, a2, b2, fa[q], fb[q]);
-                }
-            }
+            far_sft<M, L>(p, m, kh_row, ph0, lo_of(m), s_pair + ((size_t)slot * C + c) * p.w_tab,
+                          s_coef + ((size_t)slot * C + c) * 3 * p.w_tab, half, j_t, fa, fb, bad);
         }
     }
     if (bad) atomicOr(p.err, 1);
-    // ---- 2F combine
-    if (!active) return;
-    const float4 cm = p.comb[sky];
-    float* out = p.twoF + ((size_t)sky * p.n_fdot + drow) * p.n_f;
-    const int j_end = j_col0 + width;
-#pragma unroll
-    for (int q = 0; q < M; ++q) {
-        const int j = j_t + q * p.P;
-        if (j < j_end) {
-            const float2 A_ = fa[q], B_ = fb[q];
-            const float v = cm.x * fmaf(A_.x, A_.x, A_.y * A_.y) + cm.y * fmaf(B_.x, B_.x, B_.y * B_.y) +
-                            cm.z * fmaf(A_.x, B_.x, A_.y * B_.y);
-            out[j] = fmaxf(v, 0.0f);
-        }
-    }
+    if (active) far_store<M>(p, sky, drow, j_t, j_col0 + width, fa, fb);
 }
 
 template <int M, int L>
@@ -303,9 +327,192 @@ __global__ void __launch_bounds__(kMaxThreads, 2) dirichlet_far_kernel(const Dir
     far_block<M, L>(p, (long long)blockIdx.x, smem);
 }
 
+
+// ---- TMA ring form ------------------------------------------------------------
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n"
+        " .reg .pred p;\n"
+        " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n"
+        "}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Global -> shared bulk copy (16-byte aligned addresses, size a multiple of
+// 16) that signals its bytes on the mbarrier at `bar`.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Wait for the phase of parity `parity` of an mbarrier; gives up (false)
+// after about two seconds or 2^30 polls, whichever comes first.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (unsigned int it = 1; it < (1u << 30); ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 255u) == 0 && global_ns() - t0 > 2000000000ull) return false;
+    }
+    return false;
+}
+
+// L = 2, uniform spindown grid.  Warps 0..NW-1 compute, warp NW produces.
+// Error flag bit 2: a pipeline wait gave up (results of the block invalid).
+template <int M>
+__device__ __forceinline__ void far_ring_block(const DirichletParams& p, long long bid, unsigned char* smem) {
+    constexpr int D = 8, L = 2;
+    const int S = p.sft_chunk;
+    const RingSmem lay = ring_smem(S, p.w_tab);
+    const int NW = (int)(blockDim.x >> 5) - 1;
+
+    const int chunk = (int)(bid % p.chunks_per_col);
+    bid /= p.chunks_per_col;
+    const int sky = (int)(bid % p.n_sky);
+    const int col = (int)(bid / p.n_sky);
+    const int PM = p.P * M;
+    const int col_w = p.lg_row * PM;
+    const int j_col0 = col * col_w;
+    const int width = min(col_w, p.n_f - j_col0);
+    const int Gc = (width + PM - 1) / PM;
+    const int LG = p.n_fdot * Gc;
+    const int u0 = chunk * p.lg_cta;
+    if (u0 >= LG) return;   // block-uniform, before any barrier exists
+    const int u_end = min(u0 + p.lg_cta, LG);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool producer = (warp == NW);
+    const int r = producer ? 0 : warp % p.P;
+    const int ul = producer ? p.lg_cta : (warp / p.P) * 32 + lane;
+    const int u = u0 + ul;
+    const bool active = !producer && (ul < p.lg_cta) && (u < u_end);
+    const int uu = active ? u : u0;
+    const int drow = uu / Gc;
+    const int g = uu - drow * Gc;
+    const int j_t = j_col0 + g * PM + r;
+    const bool warp_live = __any_sync(0xffffffffu, active);
+
+    const uint32_t sb = smem_u32(smem);
+    volatile int* ctrl = reinterpret_cast<volatile int*>(smem + lay.ctrl);   // [0] issued, [1] abort
+    auto full_bar = [&](int s) { return sb + (uint32_t)(lay.bars + 16 * (size_t)s); };
+    auto empty_bar = [&](int s) { return sb + (uint32_t)(lay.bars + 16 * (size_t)s + 8); };
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(full_bar(s), 1);
+            mbar_init(empty_bar(s), (uint32_t)NW);
+        }
+        ctrl[0] = 0;
+        ctrl[1] = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    const size_t meta0 = (size_t)sky * p.n_sft;
+    if (producer) {
+        if (lane == 0) {
+            const int nh = p.n_pos >> 1;
+            const int half = p.w_tab >> 1;
+            const int n0 = (p.w_pairs + 1) >> 1, n1 = p.w_pairs >> 1;
+            const uint32_t bytes = 48u + 32u + (uint32_t)(n0 + n1) * 64u;
+            int a = 0;
+            for (; a < p.n_sft; ++a) {
+                const int slot = a % S, k = a / S;
+                if (k > 0 && !mbar_wait(empty_bar(slot), (uint32_t)((k - 1) & 1))) {
+                    ctrl[1] = 1;
+                    atomicOr(p.err, 4);
+                    break;
+                }
+                if (ctrl[1]) break;
+                const SkySftMeta* gm = p.meta + meta0 + a;
+                int x0 = (int)(((gm->khmin + (long long)j_col0 * gm->dk) >> 32) - p.k_lo) - (D - 1) + p.xoff;
+                if (x0 < 0 || x0 + p.w_pairs > p.n_pos) {   // outside the padded tables: clamp, flag
+                    atomicOr(p.err, 1);
+                    x0 = max(0, min(x0, p.n_pos - p.w_pairs));
+                }
+                unsigned char* st = smem + (size_t)slot * lay.stage;
+                *reinterpret_cast<int*>(st + lay.lo) = x0 - p.xoff;
+                const uint32_t ss = sb + (uint32_t)((size_t)slot * lay.stage);
+                mbar_expect_tx(full_bar(slot), bytes);
+                bulk_g2s(ss + (uint32_t)lay.meta, gm, 48, full_bar(slot));
+                bulk_g2s(ss + (uint32_t)lay.base, p.base + meta0 + a, 32, full_bar(slot));
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int cnt = h ? n1 : n0;
+                    const size_t go = (size_t)a * p.n_pos + (size_t)((x0 + h) & 1) * nh + ((x0 + h) >> 1);
+                    bulk_g2s(ss + (uint32_t)(lay.pairs + (size_t)h * half * 16), p.ptab + go, (uint32_t)cnt * 16u,
+                             full_bar(slot));
+                    bulk_g2s(ss + (uint32_t)(lay.coef + (size_t)h * half * 48), p.pcoef + 3 * go, (uint32_t)cnt * 48u,
+                             full_bar(slot));
+                }
+            }
+            ctrl[0] = a;
+        }
+    } else {
+        float2 fa[M], fb[M];
+#pragma unroll
+        for (int q = 0; q < M; ++q) fa[q] = fb[q] = make_float2(0.f, 0.f);
+        int bad = 0;
+        const int half = p.w_tab >> 1;
+        for (int a = 0; a < p.n_sft; ++a) {
+            const int slot = a % S, k = a / S;
+            if (!mbar_wait(full_bar(slot), (uint32_t)(k & 1))) {
+                ctrl[1] = 1;
+                atomicOr(p.err, 4);
+                break;
+            }
+            const unsigned char* st = smem + (size_t)slot * lay.stage;
+            if (warp_live) {
+                const SkySftMeta m = *reinterpret_cast<const SkySftMeta*>(st + lay.meta);
+                const SkySftBase bs = *reinterpret_cast<const SkySftBase*>(st + lay.base);
+                const int lo_rel = *reinterpret_cast<const int*>(st + lay.lo);
+                far_sft<M, L>(p, m, bs.kh0 + (long long)drow * bs.dkh, bs.ph0 + (unsigned int)drow * bs.dph, lo_rel,
+                              reinterpret_cast<const float4*>(st + lay.pairs),
+                              reinterpret_cast<const float4*>(st + lay.coef), half, j_t, fa, fb, bad);
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(empty_bar(slot));
+            if (ctrl[1]) break;
+        }
+        if (bad) atomicOr(p.err, 1);
+        if (active) far_store<M>(p, sky, drow, j_t, j_col0 + width, fa, fb);
+    }
+    // after a give-up, wait for the copies still in flight into this block's
+    // shared memory (each slot's latest phase) before the block retires
+    __syncthreads();
+    if (threadIdx.x == 0 && ctrl[1]) {
+        const int issued = ctrl[0];
+        for (int a = max(0, issued - S); a < issued; ++a) mbar_wait(full_bar(a % S), (uint32_t)((a / S) & 1));
+    }
+}
+
+// NWC compute warps plus the producer; two resident blocks per SM.
+template <int M, int NWC>
+__global__ void __launch_bounds__(32 * (NWC + 1), 2) dirichlet_far_ring_kernel(const DirichletParams p) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    far_ring_block<M>(p, (long long)blockIdx.x, smem);
+}
 }  // namespace
 
-// Compiled variants of the far-field form: (ID, M, L).
+// Compiled variants of the far-field form: (ID, M, L); IDs 7.. are the ring
+// form (L = 2).
 #define FS_FAR_VARIANTS(X) \
     X(0, 7, 2)             \
     X(1, 5, 2)             \
@@ -314,6 +521,12 @@ __global__ void __launch_bounds__(kMaxThreads, 2) dirichlet_far_kernel(const Dir
     X(4, 9, 1)             \
     X(5, 5, 1)             \
     X(6, 1, 1)
+#define FS_RING_VARIANTS(X) \
+    X(7, 5, 8)              \
+    X(8, 7, 8)              \
+    X(9, 9, 8)              \
+    X(10, 5, 10)            \
+    X(11, 7, 10)
 
 cudaError_t launch_dirichlet_far(int v, const DirichletParams& p, int threads, size_t smem, long long grid,
                                  cudaStream_t s) {
@@ -328,6 +541,16 @@ cudaError_t launch_dirichlet_far(int v, const DirichletParams& p, int threads, s
     }
         FS_FAR_VARIANTS(FS_FCASE)
 #undef FS_FCASE
+#define FS_RCASE(ID, M_, W_)                                                                              \
+    case ID: {                                                                                            \
+        auto fn = dirichlet_far_ring_kernel<M_, W_>;                                                      \
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        if (e != cudaSuccess) return e;                                                                   \
+        fn<<<(unsigned)grid, threads, smem, s>>>(p);                                                      \
+        return cudaGetLastError();                                                                        \
+    }
+        FS_RING_VARIANTS(FS_RCASE)
+#undef FS_RCASE
         default:
             return cudaErrorInvalidValue;
     }

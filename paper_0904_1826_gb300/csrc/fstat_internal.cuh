@@ -143,6 +143,27 @@ __host__ __device__ inline PolySmem farpoly_smem(int sft_chunk, int w_tab, int n
     return m;
 }
 
+// Shared-memory layout of the far-field ring kernel: S stages of
+// [pairs w_tab x 16 B][coefficient records w_tab x 48 B][meta 48 B][base 32 B]
+// [window base 16 B] (128-byte aligned), then a full and an empty mbarrier
+// per stage, then two control words (stages issued, abort).
+struct RingSmem {
+    size_t stage, pairs, coef, meta, base, lo, bars, ctrl, total;
+};
+__host__ __device__ inline RingSmem ring_smem(int stages, int w_tab) {
+    RingSmem r;
+    r.pairs = 0;
+    r.coef = (size_t)w_tab * 16;
+    r.meta = r.coef + (size_t)w_tab * 48;
+    r.base = r.meta + 48;
+    r.lo = r.base + 32;
+    r.stage = (r.lo + 16 + 127) & ~(size_t)127;
+    r.bars = (size_t)stages * r.stage;
+    r.ctrl = r.bars + 16 * (size_t)stages;
+    r.total = r.ctrl + 16;
+    return r;
+}
+
 // Device-side description of a batch of template banks for the persistent kernel.
 struct DirichletBatch {
     const DirichletParams* banks;     // [n_wu]

@@ -86,7 +86,7 @@ def test_batch_with_two_kernel_variants(lib):
         g.close()
 
 
-@pytest.mark.parametrize("algo,chunks", [("direct", (6, 8, 10)), ("farpoly", (2, 3, 4))])
+@pytest.mark.parametrize("algo,chunks", [("direct", (6, 8, 10)), ("farpoly", (2, 3, 4, 6, 8))])
 def test_autotune_picks_a_valid_tiling_and_keeps_parity(lib, algo, chunks):
     w = config_mid(n_sky=40, n_f=150, n_fdot=3)
     b = _with_signals(w)
