@@ -364,11 +364,15 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 // Wait for the phase of parity `parity` of an mbarrier; gives up (false)
-// after about two seconds or 2^30 polls, whichever comes first.
+// after about two seconds or 2^30 polls, whichever comes first.  SLEEP_NS > 0
+// backs off between polls (for a waiter that is ahead and must not take issue
+// slots from the compute warps).
+template <unsigned SLEEP_NS = 0>
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
     for (unsigned int it = 1; it < (1u << 30); ++it) {
+        if (SLEEP_NS) __nanosleep(SLEEP_NS);
         if (mbar_try_wait(bar, parity)) return true;
         if ((it & 255u) == 0 && global_ns() - t0 > 2000000000ull) return false;
     }
@@ -427,58 +431,82 @@ __device__ __forceinline__ void far_ring_block(const DirichletParams& p, long lo
 
     const size_t meta0 = (size_t)sky * p.n_sft;
     if (producer) {
-        if (lane == 0) {
-            const int nh = p.n_pos >> 1;
-            const int half = p.w_tab >> 1;
-            const int n0 = (p.w_pairs + 1) >> 1, n1 = p.w_pairs >> 1;
-            const uint32_t bytes = 48u + 32u + (uint32_t)(n0 + n1) * 64u;
-            int a = 0;
-            for (; a < p.n_sft; ++a) {
-                const int slot = a % S, k = a / S;
-                if (k > 0 && !mbar_wait(empty_bar(slot), (uint32_t)((k - 1) & 1))) {
-                    ctrl[1] = 1;
-                    atomicOr(p.err, 4);
-                    break;
-                }
-                if (ctrl[1]) break;
-                const SkySftMeta* gm = p.meta + meta0 + a;
-                int x0 = (int)(((gm->khmin + (long long)j_col0 * gm->dk) >> 32) - p.k_lo) - (D - 1) + p.xoff;
-                if (x0 < 0 || x0 + p.w_pairs > p.n_pos) {   // outside the padded tables: clamp, flag
-                    atomicOr(p.err, 1);
-                    x0 = max(0, min(x0, p.n_pos - p.w_pairs));
-                }
-                unsigned char* st = smem + (size_t)slot * lay.stage;
-                *reinterpret_cast<int*>(st + lay.lo) = x0 - p.xoff;
-                const uint32_t ss = sb + (uint32_t)((size_t)slot * lay.stage);
-                mbar_expect_tx(full_bar(slot), bytes);
-                bulk_g2s(ss + (uint32_t)lay.meta, gm, 48, full_bar(slot));
-                bulk_g2s(ss + (uint32_t)lay.base, p.base + meta0 + a, 32, full_bar(slot));
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int cnt = h ? n1 : n0;
-                    const size_t go = (size_t)a * p.n_pos + (size_t)((x0 + h) & 1) * nh + ((x0 + h) >> 1);
-                    bulk_g2s(ss + (uint32_t)(lay.pairs + (size_t)h * half * 16), p.ptab + go, (uint32_t)cnt * 16u,
-                             full_bar(slot));
-                    bulk_g2s(ss + (uint32_t)(lay.coef + (size_t)h * half * 48), p.pcoef + 3 * go, (uint32_t)cnt * 48u,
-                             full_bar(slot));
-                }
+        // the warp fetches the window bases of 32 SFTs at a time (one per lane,
+        // so the loads overlap); lane 0 then waits, stages and copies each SFT
+        const int nh = p.n_pos >> 1;
+        const int half = p.w_tab >> 1;
+        const int n0 = (p.w_pairs + 1) >> 1, n1 = p.w_pairs >> 1;
+        const uint32_t bytes = 48u + 32u + (uint32_t)(n0 + n1) * 64u;
+        int a = 0;
+        bool stop = false;
+        int pslot = 0;            // slot of SFT a
+        uint32_t pparity = 0;     // parity of the empty phase the next reuse of pslot waits for
+        for (int a0 = 0; a0 < p.n_sft && !stop; a0 += 32) {
+            int x_lane = 0;
+            if (a0 + lane < p.n_sft) {
+                const SkySftMeta* gm = p.meta + meta0 + a0 + lane;
+                x_lane = (int)(((gm->khmin + (long long)j_col0 * gm->dk) >> 32) - p.k_lo) - (D - 1) + p.xoff;
             }
-            ctrl[0] = a;
+            const int n_here = min(32, p.n_sft - a0);
+            for (int j = 0; j < n_here; ++j) {
+                int x0 = __shfl_sync(0xffffffffu, x_lane, j);
+                if (lane == 0) {
+                    a = a0 + j;
+                    if (a >= S && !mbar_wait<128>(empty_bar(pslot), pparity)) {
+                        ctrl[1] = 1;
+                        atomicOr(p.err, 4);
+                        stop = true;
+                    } else if (ctrl[1]) {
+                        stop = true;
+                    } else {
+                        if (x0 < 0 || x0 + p.w_pairs > p.n_pos) {   // outside the padded tables: clamp, flag
+                            atomicOr(p.err, 1);
+                            x0 = max(0, min(x0, p.n_pos - p.w_pairs));
+                        }
+                        unsigned char* st = smem + (size_t)pslot * lay.stage;
+                        *reinterpret_cast<int*>(st + lay.lo) = x0 - p.xoff;
+                        const uint32_t ss = sb + (uint32_t)((size_t)pslot * lay.stage);
+                        const uint32_t fb = full_bar(pslot);
+                        mbar_expect_tx(fb, bytes);
+                        bulk_g2s(ss + (uint32_t)lay.meta, p.meta + meta0 + a, 48, fb);
+                        bulk_g2s(ss + (uint32_t)lay.base, p.base + meta0 + a, 32, fb);
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const int cnt = h ? n1 : n0;
+                            const size_t go = (size_t)a * p.n_pos + (size_t)((x0 + h) & 1) * nh + ((x0 + h) >> 1);
+                            bulk_g2s(ss + (uint32_t)(lay.pairs + (size_t)h * half * 16), p.ptab + go,
+                                     (uint32_t)cnt * 16u, fb);
+                            bulk_g2s(ss + (uint32_t)(lay.coef + (size_t)h * half * 48), p.pcoef + 3 * go,
+                                     (uint32_t)cnt * 48u, fb);
+                        }
+                        ++a;
+                        if (++pslot == S) {   // the next use of slot 0 waits for the phase after this one
+                            pslot = 0;
+                            if (a > S) pparity ^= 1u;
+                        }
+                    }
+                }
+                stop = __shfl_sync(0xffffffffu, stop, 0);
+                if (stop) break;
+            }
         }
+        if (lane == 0) ctrl[0] = a;   // stages issued
     } else {
         float2 fa[M], fb[M];
 #pragma unroll
         for (int q = 0; q < M; ++q) fa[q] = fb[q] = make_float2(0.f, 0.f);
         int bad = 0;
         const int half = p.w_tab >> 1;
+        // ring position kept incrementally: stage slot, its data, its barriers, phase parity
+        int slot = 0;
+        uint32_t parity = 0, fbar = full_bar(0), ebar = empty_bar(0);
+        const unsigned char* st = smem;
         for (int a = 0; a < p.n_sft; ++a) {
-            const int slot = a % S, k = a / S;
-            if (!mbar_wait(full_bar(slot), (uint32_t)(k & 1))) {
+            if (!mbar_wait(fbar, parity)) {
                 ctrl[1] = 1;
                 atomicOr(p.err, 4);
                 break;
             }
-            const unsigned char* st = smem + (size_t)slot * lay.stage;
             if (warp_live) {
                 const SkySftMeta m = *reinterpret_cast<const SkySftMeta*>(st + lay.meta);
                 const SkySftBase bs = *reinterpret_cast<const SkySftBase*>(st + lay.base);
@@ -488,8 +516,19 @@ __device__ __forceinline__ void far_ring_block(const DirichletParams& p, long lo
                               reinterpret_cast<const float4*>(st + lay.coef), half, j_t, fa, fb, bad);
             }
             __syncwarp();
-            if (lane == 0) mbar_arrive(empty_bar(slot));
+            if (lane == 0) mbar_arrive(ebar);
             if (ctrl[1]) break;
+            if (++slot == S) {
+                slot = 0;
+                parity ^= 1u;
+                st = smem;
+                fbar = full_bar(0);
+                ebar = empty_bar(0);
+            } else {
+                st += lay.stage;
+                fbar += 16;
+                ebar += 16;
+            }
         }
         if (bad) atomicOr(p.err, 1);
         if (active) far_store<M>(p, sky, drow, j_t, j_col0 + width, fa, fb);
