@@ -301,7 +301,8 @@ bool make_far_plan(fstat_ctx* c, int P, int L, bool found, Plan& best) {
     // TMA-ring form first: L = 2, compact spindown bases
     // default: 10 compute warps + 1 copy warp (measured fastest on GB300); tile_warps 9 / 11 choose 8 / 10
     if (found && L == 2 && c->fdot_uniform && (c->opts.tile_warps == 0 || c->opts.tile_warps >= 9)) {
-        std::vector<int> Mr = {7, 5, 9};
+        // M = 5 with 8 stages measured fastest on GB300 (1105 ms on the workunit; M = 7: 1139 ms)
+        std::vector<int> Mr = {5};
         if (c->opts.tile_m > 0) Mr = {c->opts.tile_m};
         const int nwc = c->opts.tile_warps ? c->opts.tile_warps - 1 : 10;   // the last warp produces
         double best_r = 1e300;

@@ -112,7 +112,7 @@ template <int M, int L>
 __device__ __forceinline__ void far_sft(const DirichletParams& p, const SkySftMeta& m, long long kh_row,
                                         unsigned int ph0, int lo_rel, const float4* __restrict__ tab,
                                         const float4* __restrict__ cf, int half, int j_t, float2 (&fa)[M],
-                                        float2 (&fb)[M], int& bad) {
+                                        float2 (&fb)[M]) {
     constexpr int D = 8;
     constexpr int STRIDE = (L == 2) ? 1 : 2;
     const long long kh = kh_row + (long long)j_t * m.dk;
@@ -123,7 +123,7 @@ __device__ __forceinline__ void far_sft(const DirichletParams& p, const SkySftMe
     if (fast) {
         int bb = b;
         if (bb < 0 || bb + (M - 1) * L + 2 * (D - 1) >= p.w_pairs) {
-            bad = 1;
+            atomicOr(p.err, 1);   // outside the staged rows (clamped); rare, no register kept for it
             bb = max(0, min(bb, p.w_pairs - 1 - (M - 1) * L - 2 * (D - 1)));
         }
         const float4* pn = tab + tab_pos<L>(bb, half) + 3 * STRIDE;
@@ -156,7 +156,7 @@ __device__ __forceinline__ void far_sft(const DirichletParams& p, const SkySftMe
             __sincosf((float)(int)phq * kPhaseToRad, &s2, &c2);
             int bq = b + (k0q - k0);
             if (bq < 0 || bq + 2 * (D - 1) >= p.w_pairs) {
-                bad = 1;
+                atomicOr(p.err, 1);
                 bq = max(0, min(bq, p.w_pairs - 1 - 2 * (D - 1)));
             }
             const float2 Q = far_window_sum<STRIDE>(tab + tab_pos<L>(bq, half) + 3 * STRIDE,
@@ -280,7 +280,6 @@ __device__ __forceinline__ void far_block(const DirichletParams& p, long long bi
     float2 fa[M], fb[M];
 #pragma unroll
     for (int q = 0; q < M; ++q) fa[q] = fb[q] = make_float2(0.f, 0.f);
-    int bad = 0;
 
     // prologue: constants of rounds 0 and 1, tables of round 0
     issue_consts(0);
@@ -314,10 +313,9 @@ __device__ __forceinline__ void far_block(const DirichletParams& p, long long bi
                 ph0 = s_ph0[(cslot * C + c) * p.n_fdot + row_i];
             }
             far_sft<M, L>(p, m, kh_row, ph0, lo_of(m), s_pair + ((size_t)slot * C + c) * p.w_tab,
-                          s_coef + ((size_t)slot * C + c) * 3 * p.w_tab, half, j_t, fa, fb, bad);
+                          s_coef + ((size_t)slot * C + c) * 3 * p.w_tab, half, j_t, fa, fb);
         }
     }
-    if (bad) atomicOr(p.err, 1);
     if (active) far_store<M>(p, sky, drow, j_t, j_col0 + width, fa, fb);
 }
 
@@ -495,14 +493,14 @@ __device__ __forceinline__ void far_ring_block(const DirichletParams& p, long lo
         float2 fa[M], fb[M];
 #pragma unroll
         for (int q = 0; q < M; ++q) fa[q] = fb[q] = make_float2(0.f, 0.f);
-        int bad = 0;
         const int half = p.w_tab >> 1;
-        // ring position kept incrementally: stage slot, its data, its barriers, phase parity
+        // ring position kept incrementally (slot and phase parity); the stage's
+        // data and barrier addresses follow from the slot
         int slot = 0;
-        uint32_t parity = 0, fbar = full_bar(0), ebar = empty_bar(0);
-        const unsigned char* st = smem;
+        uint32_t parity = 0;
         for (int a = 0; a < p.n_sft; ++a) {
-            if (!mbar_wait(fbar, parity)) {
+            const unsigned char* st = smem + (size_t)slot * lay.stage;
+            if (!mbar_wait(full_bar(slot), parity)) {
                 ctrl[1] = 1;
                 atomicOr(p.err, 4);
                 break;
@@ -513,24 +511,16 @@ __device__ __forceinline__ void far_ring_block(const DirichletParams& p, long lo
                 const int lo_rel = *reinterpret_cast<const int*>(st + lay.lo);
                 far_sft<M, L>(p, m, bs.kh0 + (long long)drow * bs.dkh, bs.ph0 + (unsigned int)drow * bs.dph, lo_rel,
                               reinterpret_cast<const float4*>(st + lay.pairs),
-                              reinterpret_cast<const float4*>(st + lay.coef), half, j_t, fa, fb, bad);
+                              reinterpret_cast<const float4*>(st + lay.coef), half, j_t, fa, fb);
             }
             __syncwarp();
-            if (lane == 0) mbar_arrive(ebar);
+            if (lane == 0) mbar_arrive(empty_bar(slot));
             if (ctrl[1]) break;
             if (++slot == S) {
                 slot = 0;
                 parity ^= 1u;
-                st = smem;
-                fbar = full_bar(0);
-                ebar = empty_bar(0);
-            } else {
-                st += lay.stage;
-                fbar += 16;
-                ebar += 16;
             }
         }
-        if (bad) atomicOr(p.err, 1);
         if (active) far_store<M>(p, sky, drow, j_t, j_col0 + width, fa, fb);
     }
     // after a give-up, wait for the copies still in flight into this block's
