@@ -203,7 +203,7 @@ def run_batch(args):
     rank, local_rank, world = dist_env()
     torch.cuda.set_device(local_rank)
     specs = config3_specs(args.n_wu)
-    ctx = fs.fstat_create(local_rank, dterms=8, topk=100)
+    ctx = fs.fstat_create(local_rank, dterms=8, topk=100, algo=args.algo)
     pairs = []
     t0 = time.perf_counter()
     for sp in specs:

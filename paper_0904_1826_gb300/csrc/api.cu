@@ -1285,9 +1285,7 @@ int fstat_batch_add(fstat_ctx* c, const fstat_workunit* wu, int32_t* wu_id) {
     if (wu->n_det < 1 || wu->n_det > kMaxDet || !wu->det || !wu->n_sft || !wu->t_start || !wu->bins)
         return fail(c, FSTAT_EINVAL, "workunit needs 1..8 detectors with SFTs");
     fstat_ctx* w = nullptr;
-    fstat_opts wo = c->opts;
-    wo.algo = FSTAT_ALGO_DIRECT;   // the persistent batch kernel runs the direct form
-    int rc = fstat_create(&w, c->device, &wo);
+    int rc = fstat_create(&w, c->device, &c->opts);
     if (rc != FSTAT_OK) return fail(c, rc, "workunit context creation failed");
     for (int d = 0; d < wu->n_det; ++d) {
         rc = fstat_set_sfts(w, d, &wu->det[d], wu->Tsft, wu->k_lo, wu->n_bins, wu->n_sft[d], wu->t_start[d],
@@ -1304,6 +1302,12 @@ int fstat_batch_add(fstat_ctx* c, const fstat_workunit* wu, int32_t* wu_id) {
         fstat_destroy(w);
         return rc;
     }
+    // the persistent kernels exist for the direct and the ring forms: a workunit
+    // the far-field form would stage in rounds runs the direct form, alone or batched
+    Plan pl;
+    if (make_plan(w, pl) == FSTAT_OK && pl.far && !pl.ring) w->opts.algo = FSTAT_ALGO_DIRECT;
+    w->plan_valid = false;
+    w->err.clear();
     c->wus.push_back(w);
     c->graph_valid = false;
     c->batch_ran = false;
@@ -1361,11 +1365,12 @@ __global__ void stamp_kernel(unsigned long long* t) {
     *t = v;
 }
 
-// Groups of workunits sharing a kernel variant and block size.
+// Groups of workunits sharing a kernel (direct or far-field ring), variant and block size.
 struct BatchGroup {
     int variant, W, form;
     size_t smem;
     int first, count;   // range in the sorted workunit order
+    bool ring;
 };
 
 // Enqueue the whole batch on stream s (also used inside graph capture).
@@ -1395,6 +1400,14 @@ int enqueue_batch(fstat_ctx* c, const std::vector<int>& order, const std::vector
         b.done_ns = c->d_done + G.first;
         int occ = 1;
         cudaError_t e;
+        if (G.ring) {
+            e = dirichlet_far_batch_occupancy(G.variant, G.W * 32, G.smem, &occ);
+            if (e != cudaSuccess) return fail(c, FSTAT_ECUDA, "occupancy: %s", cudaGetErrorString(e));
+            e = launch_dirichlet_far_batch(G.variant, b, G.W * 32, G.smem, std::max(1, occ) * dev_sms, s);
+            if (e != cudaSuccess) return fail(c, FSTAT_ECUDA, "batch Dirichlet launch: %s", cudaGetErrorString(e));
+            c->launches += 1;
+            continue;
+        }
         if (G.form == FSTAT_BINS_C64) e = dirichlet_occupancy_c64(G.variant, G.W * 32, G.smem, &occ);
         else if (G.form == FSTAT_BINS_F16) e = dirichlet_occupancy_f16(G.variant, G.W * 32, G.smem, &occ);
         else e = dirichlet_occupancy_bf16(G.variant, G.W * 32, G.smem, &occ);
@@ -1430,6 +1443,12 @@ int fstat_batch_compute(fstat_ctx* c, void* cuda_stream) {
         w->stream = s;
         int rc = prepare(w, s);
         if (rc != FSTAT_OK) return fail(c, rc, "workunit: %s", w->err.c_str());
+        if (w->plan.far && !w->plan.ring) {   // the persistent kernels exist for the direct and ring forms
+            w->opts.algo = FSTAT_ALGO_DIRECT;
+            w->plan_valid = false;
+            c->graph_valid = false;
+            if ((rc = prepare(w, s)) != FSTAT_OK) return fail(c, rc, "workunit: %s", w->err.c_str());
+        }
     }
     if (!c->bev0) {
         cudaEventCreate(&c->bev0);
@@ -1438,7 +1457,10 @@ int fstat_batch_compute(fstat_ctx* c, void* cuda_stream) {
     // group workunits by kernel variant and block size (usually one group)
     std::vector<int> order(n);
     for (int i = 0; i < n; ++i) order[i] = i;
-    auto key = [&](int i) { return c->wus[i]->plan.variant * 64 + c->wus[i]->plan.W; };
+    auto key = [&](int i) {
+        const Plan& pl = c->wus[i]->plan;
+        return (pl.ring ? 1 << 20 : 0) + pl.variant * 64 + pl.W;
+    };
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return key(a) < key(b); });
     if (!c->graph_valid) {
         // device tables in grouped order
@@ -1449,7 +1471,7 @@ int fstat_batch_compute(fstat_ctx* c, void* cuda_stream) {
         for (int k = 0; k < n; ++k) {
             fstat_ctx* w = c->wus[order[k]];
             if (groups.empty() || key(order[groups.back().first]) != key(order[k])) {
-                groups.push_back(BatchGroup{w->plan.variant, w->plan.W, w->opts.bins_form, 0, k, 0});
+                groups.push_back(BatchGroup{w->plan.variant, w->plan.W, w->opts.bins_form, 0, k, 0, w->plan.ring});
                 prefix.push_back(0);
             }
             BatchGroup& G = groups.back();

@@ -333,6 +333,9 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
+__device__ __forceinline__ void mbar_inval(uint32_t bar) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+}
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
@@ -524,11 +527,18 @@ __device__ __forceinline__ void far_ring_block(const DirichletParams& p, long lo
         if (active) far_store<M>(p, sky, drow, j_t, j_col0 + width, fa, fb);
     }
     // after a give-up, wait for the copies still in flight into this block's
-    // shared memory (each slot's latest phase) before the block retires
+    // shared memory (each slot's latest phase) before the block retires; then
+    // invalidate the barriers so that a persistent block can set them up again
     __syncthreads();
-    if (threadIdx.x == 0 && ctrl[1]) {
-        const int issued = ctrl[0];
-        for (int a = max(0, issued - S); a < issued; ++a) mbar_wait(full_bar(a % S), (uint32_t)((a / S) & 1));
+    if (threadIdx.x == 0) {
+        if (ctrl[1]) {
+            const int issued = ctrl[0];
+            for (int a = max(0, issued - S); a < issued; ++a) mbar_wait(full_bar(a % S), (uint32_t)((a / S) & 1));
+        }
+        for (int s = 0; s < S; ++s) {
+            mbar_inval(full_bar(s));
+            mbar_inval(empty_bar(s));
+        }
     }
 }
 
@@ -537,6 +547,47 @@ template <int M, int NWC>
 __global__ void __launch_bounds__(32 * (NWC + 1), 2) dirichlet_far_ring_kernel(const DirichletParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
     far_ring_block<M>(p, (long long)blockIdx.x, smem);
+}
+
+// Persistent ring form over many template banks (workunits): every block
+// takes the next (bank, block) item from a device counter until all items of
+// all banks are done, runs it as far_ring_block (whose barriers it sets up and
+// invalidates), and the block that completes a bank's last item stamps its
+// completion time.  At most `total` items per block; no block waits on another.
+template <int M, int NWC>
+__global__ void __launch_bounds__(32 * (NWC + 1), 2)
+    dirichlet_far_ring_batch_kernel(const DirichletParams* __restrict__ banks,
+                                    const long long* __restrict__ item_prefix, int n_wu,
+                                    unsigned long long* __restrict__ queue, int* __restrict__ remaining,
+                                    unsigned long long* __restrict__ done_ns) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ long long s_item;
+    __shared__ int s_wu;
+    const long long total = item_prefix[n_wu];
+    for (long long guard = 0; guard <= total; ++guard) {
+        __syncthreads();   // previous item fully consumed (shared memory and barriers free)
+        if (threadIdx.x == 0) {
+            const long long it = (long long)atomicAdd(queue, 1ULL);
+            int lo = 0, hi = n_wu;   // last bank with item_prefix <= it
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (item_prefix[mid] <= it) lo = mid; else hi = mid;
+            }
+            s_item = it;
+            s_wu = lo;
+        }
+        __syncthreads();
+        const long long it = s_item;
+        if (it >= total) break;
+        const int w = s_wu;
+        const DirichletParams p = banks[w];
+        far_ring_block<M>(p, it - item_prefix[w], smem);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            if (atomicSub(&remaining[w], 1) == 1) done_ns[w] = global_ns();
+        }
+    }
 }
 }  // namespace
 
@@ -580,6 +631,40 @@ cudaError_t launch_dirichlet_far(int v, const DirichletParams& p, int threads, s
     }
         FS_RING_VARIANTS(FS_RCASE)
 #undef FS_RCASE
+        default:
+            return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_dirichlet_far_batch(int v, const DirichletBatch& b, int threads, size_t smem, int grid,
+                                       cudaStream_t s) {
+    switch (v) {
+#define FS_BRCASE(ID, M_, W_)                                                                             \
+    case ID: {                                                                                            \
+        auto fn = dirichlet_far_ring_batch_kernel<M_, W_>;                                                \
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        if (e != cudaSuccess) return e;                                                                   \
+        fn<<<grid, threads, smem, s>>>(b.banks, b.item_prefix, b.n_wu, b.queue, b.remaining, b.done_ns);  \
+        return cudaGetLastError();                                                                        \
+    }
+        FS_RING_VARIANTS(FS_BRCASE)
+#undef FS_BRCASE
+        default:
+            return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t dirichlet_far_batch_occupancy(int v, int threads, size_t smem, int* blocks_per_sm) {
+    switch (v) {
+#define FS_BOCASE(ID, M_, W_)                                                                             \
+    case ID: {                                                                                            \
+        auto fn = dirichlet_far_ring_batch_kernel<M_, W_>;                                                \
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        if (e != cudaSuccess) return e;                                                                   \
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, threads, smem);           \
+    }
+        FS_RING_VARIANTS(FS_BOCASE)
+#undef FS_BOCASE
         default:
             return cudaErrorInvalidValue;
     }

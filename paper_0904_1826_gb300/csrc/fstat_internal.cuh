@@ -227,6 +227,9 @@ cudaError_t launch_far_tables(const void* bins, int form, long long row, int n_s
                               float4* ptab, float4* pcoef, int n_pos, int xoff, cudaStream_t s);
 cudaError_t launch_dirichlet_far(int v, const DirichletParams& p, int threads, size_t smem, long long grid,
                                  cudaStream_t s);
+cudaError_t launch_dirichlet_far_batch(int v, const DirichletBatch& b, int threads, size_t smem, int grid,
+                                       cudaStream_t s);
+cudaError_t dirichlet_far_batch_occupancy(int v, int threads, size_t smem, int* blocks_per_sm);
 cudaError_t launch_topk(const float* v, long long n, int k, TopkWork& w, cudaStream_t s);
 
 }  // namespace fs
