@@ -196,8 +196,18 @@ int fstat_get_bins(fstat_ctx *ctx, int32_t det_index, float *out, int32_t mem);
 
 /* Device-side error flags raised by the last compute (0 = none); synchronises.
  * Bit 0: a template window left the staged SFT range (clamped).
- * Bit 1: a sky point had D = AB - C^2 <= 0 (its 2F set to 0). */
+ * Bit 1: a sky point had D = AB - C^2 <= 0 (its 2F set to 0).
+ * Bit 2: a wait of the far-field ring pipeline gave up (that block's 2F invalid). */
 int fstat_get_error_flags(fstat_ctx *ctx, int32_t *flags);
+
+/* Testing aid for failure detection (no counterpart in the paper): from the
+ * next fstat_compute on, the copy warp of the far-field ring form stops after
+ * `after_sft` SFTs (after_sft < 0 restores normal operation).  The compute
+ * warps' bounded waits then expire after about two seconds per block; each
+ * block raises error flag bit 2, waits for its own copies in flight and
+ * retires, and the context stays usable.  Has no effect on the other forms.
+ * Errors: EINVAL (null context). */
+int fstat_test_ring_stall(fstat_ctx *ctx, int32_t after_sft);
 
 /* Tile configuration chosen for the current bank (after fstat_set_templates):
  * out[8] = (P, L, M, warps, sft_chunk, lane-groups per column row,

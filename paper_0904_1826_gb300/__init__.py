@@ -76,6 +76,7 @@ SIGNATURES = {
     "fstat_get_bins": (ctypes.c_int, [_P, _I32, _P, _I32]),
     "fstat_get_error_flags": (ctypes.c_int, [_P, ctypes.POINTER(_I32)]),
     "fstat_get_plan": (ctypes.c_int, [_P, _P]),
+    "fstat_test_ring_stall": (ctypes.c_int, [_P, _I32]),
     "fstat_get_launch_count": (ctypes.c_int, [_P, ctypes.POINTER(_I64)]),
     "fstat_take_kernel_time": (ctypes.c_int, [_P, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_I32)]),
     "fstat_autotune": (ctypes.c_int, [_P, _P, _P]),
@@ -248,6 +249,10 @@ def fstat_get_error_flags(ctx) -> int:
     v = _I32()
     _check(ctx, _lib.fstat_get_error_flags(ctx, ctypes.byref(v)))
     return int(v.value)
+
+
+def fstat_test_ring_stall(ctx, after_sft: int) -> None:
+    _check(ctx, _lib.fstat_test_ring_stall(ctx, int(after_sft)))
 
 
 def fstat_get_plan(ctx) -> dict:

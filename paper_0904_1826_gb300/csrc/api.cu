@@ -95,6 +95,7 @@ struct fstat_ctx {
     float4* d_ptab = nullptr;       // far-field pair table [n_sft][n_pos]
     float4* d_pcoef = nullptr;      // far-field coefficients [n_sft][4][n_pos]
     size_t cap_ptab = 0, cap_pcoef = 0;
+    int ring_stall = -1;             // testing aid (fstat_test_ring_stall)
     int n_pos = 0, far_xoff = 0;     // table extent of the current plan
     int tab_npos = -1, tab_xoff = -1; // extent the built tables have
     // template bank
@@ -960,6 +961,7 @@ DirichletParams dirichlet_params(const fstat_ctx* c) {
     dp.w_raw = pl.w_raw;
     dp.sft_chunk = pl.C;
     dp.err = c->d_err;
+    dp.ring_stop = c->ring_stall;
     if (pl.far) {
         dp.ptab = c->d_ptab;
         dp.pcoef = c->d_pcoef;
@@ -1145,6 +1147,12 @@ int fstat_get_plan(fstat_ctx* c, int32_t* out) {
     const Plan& p = c->plan;
     const int v[8] = {p.P, p.L, p.M, p.W, p.C, p.lg_row, p.w_pairs, p.far ? kFarIdBase + p.variant : p.variant};
     std::memcpy(out, v, sizeof(v));
+    return FSTAT_OK;
+}
+
+int fstat_test_ring_stall(fstat_ctx* c, int32_t after_sft) {
+    if (!c) return FSTAT_EINVAL;
+    c->ring_stall = after_sft < 0 ? -1 : after_sft;
     return FSTAT_OK;
 }
 

@@ -442,13 +442,14 @@ __device__ __forceinline__ void far_ring_block(const DirichletParams& p, long lo
         bool stop = false;
         int pslot = 0;            // slot of SFT a
         uint32_t pparity = 0;     // parity of the empty phase the next reuse of pslot waits for
-        for (int a0 = 0; a0 < p.n_sft && !stop; a0 += 32) {
+        const int n_issue = p.ring_stop >= 0 ? min(p.ring_stop, p.n_sft) : p.n_sft;
+        for (int a0 = 0; a0 < n_issue && !stop; a0 += 32) {
             int x_lane = 0;
             if (a0 + lane < p.n_sft) {
                 const SkySftMeta* gm = p.meta + meta0 + a0 + lane;
                 x_lane = (int)(((gm->khmin + (long long)j_col0 * gm->dk) >> 32) - p.k_lo) - (D - 1) + p.xoff;
             }
-            const int n_here = min(32, p.n_sft - a0);
+            const int n_here = min(32, n_issue - a0);
             for (int j = 0; j < n_here; ++j) {
                 int x0 = __shfl_sync(0xffffffffu, x_lane, j);
                 if (lane == 0) {

@@ -90,6 +90,7 @@ struct DirichletParams {
     const float4* pcoef;       // [n_sft][n_pos][3]
     int n_pos;                 // positions per SFT row
     int xoff;                  // position of bin k_lo
+    int ring_stop;             // testing aid: the ring's copy warp stops after this many SFTs (< 0: never)
 };
 
 // Far-field polynomial form (D = 8): the window's 12 bins at offsets -7..-2

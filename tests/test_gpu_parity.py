@@ -303,3 +303,26 @@ def test_nonuniform_unsorted_spindowns(lib):
     out = _gpu(lib, w, bins)
     assert out["flags"] == 0
     _assert_parity(out["twoF"], ref, "non-uniform fdot")
+
+
+def test_ring_wait_timeout_is_reported_and_context_survives(lib):
+    """Failure detection without a fault: the ring's copy warp stops after 3
+    SFTs, the compute warps' bounded waits expire (about 2 s), the compute
+    returns with error flag bit 2, and the next compute on the same context
+    is correct again."""
+    w = config_mid(n_sky=1, n_f=40, n_fdot=1)
+    bins = _oracle_bins(w)
+    ref = O.compute_fstat_freq_band(_dets(w, bins), w.T, w.k_lo, w.dterms, w.bank).ravel()
+    g = lib.FStat(0, dterms=w.dterms, topk=5)
+    try:
+        g.load_workload(w, bins_override=bins)
+        assert g.plan()["variant"] >= 107          # the TMA-ring form
+        lib.fstat_test_ring_stall(g.ctx, 3)
+        g.compute()
+        assert g.error_flags() & 4
+        lib.fstat_test_ring_stall(g.ctx, -1)
+        g.compute()
+        assert g.error_flags() == 0
+        _assert_parity(g.twoF(), ref, "after a give-up")
+    finally:
+        g.close()
