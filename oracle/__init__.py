@@ -11,8 +11,11 @@ Pinned functions (see tests/test_oracle_pins.py):
     time-domain demodulation, the noise-free closed form, the chi^2_4 noise law;
   * toplist                                        -- exhaustive sort on ties;
   * quantisation                                   -- exactly representable cases;
-  * the MLP forward/backward                       -- central finite differences.
+  * the MLP forward/backward                       -- central finite differences;
+  * noise floor, whitening, noise weights           -- closed-form medians and weights,
+    stationary invariance, chi^2_4 mean on non-stationary noise.
 """
 from . import fstat_oracle  # noqa: F401
 from . import mlp_oracle  # noqa: F401
+from . import noise_oracle  # noqa: F401
 from . import quantize  # noqa: F401

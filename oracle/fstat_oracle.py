@@ -189,8 +189,14 @@ def some_calculations(bins_row, k_lo: int, kappa_hat, phase_frac, dterms: int):
 def compute_fa_fb(det, T: float, k_lo: int, dterms: int, alpha, delta, f, fdot, t_ref: float):
     """Fa, Fb of one detector summed over its SFTs, and that detector's
     a, b arrays (for A, B, C).  alpha, delta are scalars (one sky position);
-    f, fdot are equal-shape template arrays."""
+    f, fdot are equal-shape template arrays.  A detector with per-SFT noise
+    weights w (attribute `weights`, whitened bins) uses sqrt(w) a, sqrt(w) b."""
     dtau, tdot, a, b = sft_timing_antenna(det, T, alpha, delta, t_ref)
+    w = getattr(det, "weights", None)
+    if w is not None:
+        sw = np.sqrt(np.asarray(w, dtype=np.float64))
+        a = a * sw
+        b = b * sw
     f = np.asarray(f, dtype=np.float64)
     fdot = np.asarray(fdot, dtype=np.float64)
     Fa = np.zeros(f.shape, dtype=np.complex128)
