@@ -200,6 +200,26 @@ int fstat_get_bins(fstat_ctx *ctx, int32_t det_index, float *out, int32_t mem);
  * Bit 2: a wait of the far-field ring pipeline gave up (that block's 2F invalid). */
 int fstat_get_error_flags(fstat_ctx *ctx, int32_t *flags);
 
+/* Noise-floor normalisation and noise weights (no counterpart in the paper's
+ * white-noise client; the step before the path for coloured, non-stationary
+ * noise).  With half_window W in 1..64, from the next fstat_compute on:
+ *   S(k) = median of |X_j|^2 (FP32) over the stored bins j with |j - k| <= W
+ *          (clipped at the band edges; an even count averages its two middle
+ *          values) divided by ln 2;
+ *   every bin the path reads is X_k / sqrt(S(k)) (0 where S(k) = 0); the
+ *          stored SFTs themselves (fstat_get_bins) are unchanged;
+ *   every SFT gets the weight w = (1/Sbar) / mean over all SFTs of (1/Sbar),
+ *          Sbar = the SFT's mean S, applied as sqrt(w) a, sqrt(w) b in A, B,
+ *          C, Fa and Fb (w = 0 where Sbar = 0, left out of the mean).
+ * W = 0 switches it off (the default).  Errors: EINVAL (W outside 0..64). */
+int fstat_set_noise_floor(fstat_ctx *ctx, int32_t half_window);
+
+/* The noise floor S [n_sft][n_bins] (FP32; NULL to skip) and the weights
+ * [n_sft] (FP64; NULL to skip) of the last compute, SFTs in detector order,
+ * host or device per `mem`; synchronises.  Errors: ESTATE (noise floor off or
+ * not computed yet), ECUDA. */
+int fstat_get_noise(fstat_ctx *ctx, float *floor, double *weights, int32_t mem);
+
 /* Testing aid for failure detection (no counterpart in the paper): from the
  * next fstat_compute on, the copy warp of the far-field ring form stops after
  * `after_sft` SFTs (after_sft < 0 restores normal operation).  The compute

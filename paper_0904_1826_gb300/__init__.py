@@ -77,6 +77,8 @@ SIGNATURES = {
     "fstat_get_error_flags": (ctypes.c_int, [_P, ctypes.POINTER(_I32)]),
     "fstat_get_plan": (ctypes.c_int, [_P, _P]),
     "fstat_test_ring_stall": (ctypes.c_int, [_P, _I32]),
+    "fstat_set_noise_floor": (ctypes.c_int, [_P, _I32]),
+    "fstat_get_noise": (ctypes.c_int, [_P, _P, _P, _I32]),
     "fstat_get_launch_count": (ctypes.c_int, [_P, ctypes.POINTER(_I64)]),
     "fstat_take_kernel_time": (ctypes.c_int, [_P, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_I32)]),
     "fstat_autotune": (ctypes.c_int, [_P, _P, _P]),
@@ -249,6 +251,18 @@ def fstat_get_error_flags(ctx) -> int:
     v = _I32()
     _check(ctx, _lib.fstat_get_error_flags(ctx, ctypes.byref(v)))
     return int(v.value)
+
+
+def fstat_set_noise_floor(ctx, half_window: int) -> None:
+    _check(ctx, _lib.fstat_set_noise_floor(ctx, int(half_window)))
+
+
+def fstat_get_noise(ctx, n_sft: int, n_bins: int):
+    """(floor [n_sft, n_bins] float32, weights [n_sft] float64) of the last compute."""
+    fl = np.empty((n_sft, n_bins), dtype=np.float32)
+    w = np.empty(n_sft, dtype=np.float64)
+    _check(ctx, _lib.fstat_get_noise(ctx, _host_ptr(fl), _host_ptr(w), FSTAT_MEM_HOST))
+    return fl, w
 
 
 def fstat_test_ring_stall(ctx, after_sft: int) -> None:

@@ -84,6 +84,12 @@ struct fstat_ctx {
     int n_sft = 0;
     int sft_capacity = 0;
     float2* d_bins = nullptr;       // complex64 master copy
+    int nf_half = 0;                // noise floor: running-median half window (0 = off)
+    float2* d_bins_w = nullptr;     // whitened copy (noise floor on)
+    float* d_floor = nullptr;       // noise floor S [n_sft][n_bins]
+    double* d_sbar = nullptr;       // mean floor per SFT
+    double* d_weight = nullptr;     // noise weight per SFT
+    size_t cap_bins_w = 0, cap_floor = 0, cap_sbar = 0, cap_weight = 0;
     void* d_bins16 = nullptr;       // 16-bit copy (precision forms)
     float* d_scale = nullptr;       // per-SFT storage scale
     SftState* d_state = nullptr;
@@ -614,6 +620,9 @@ int sync_ctx(fstat_ctx* c) {
     return FSTAT_OK;
 }
 
+// The bins the path reads: the whitened copy when the noise floor is on.
+const float2* work_bins(const fstat_ctx* c) { return c->nf_half > 0 ? c->d_bins_w : c->d_bins; }
+
 int refresh_sft_state(fstat_ctx* c, cudaStream_t s) {
     if (!c->sft_dirty) return FSTAT_OK;
     std::vector<double> ts;
@@ -632,11 +641,21 @@ int refresh_sft_state(fstat_ctx* c, cudaStream_t s) {
     CUDA_TRY(c, cudaMemcpyAsync(c->d_det_of, det_of.data(), det_of.size() * sizeof(int), cudaMemcpyHostToDevice, s));
     CUDA_TRY(c, launch_sft_state(c->d_tstart, c->d_det_of, g, c->n_sft, c->T, c->d_state, s));
     c->launches += 2;   // detector state + scale fill / quantisation
+    if (c->nf_half > 0) {
+        int rc;
+        if ((rc = grow(c, &c->d_bins_w, c->cap_bins_w, (size_t)c->n_sft * c->row)) != FSTAT_OK) return rc;
+        if ((rc = grow(c, &c->d_floor, c->cap_floor, (size_t)c->n_sft * c->n_bins)) != FSTAT_OK) return rc;
+        if ((rc = grow(c, &c->d_sbar, c->cap_sbar, (size_t)c->n_sft)) != FSTAT_OK) return rc;
+        if ((rc = grow(c, &c->d_weight, c->cap_weight, (size_t)c->n_sft)) != FSTAT_OK) return rc;
+        CUDA_TRY(c, launch_noise_floor(c->d_bins, c->row, c->n_sft, c->n_bins, c->nf_half, c->d_floor, c->d_bins_w,
+                                       c->d_sbar, c->d_weight, s));
+        c->launches += 2;
+    }
     if (c->opts.bins_form == FSTAT_BINS_C64) {
         fill_kernel<<<64, 256, 0, s>>>(c->d_scale, c->n_sft, 1.0f);
         CUDA_TRY(c, cudaGetLastError());
     } else {
-        CUDA_TRY(c, launch_quantize(c->d_bins, c->row, c->n_sft, c->n_bins, c->opts.bins_form, c->d_bins16,
+        CUDA_TRY(c, launch_quantize(work_bins(c), c->row, c->n_sft, c->n_bins, c->opts.bins_form, c->d_bins16,
                                     c->d_scale, s));
     }
     // the host vectors are copied asynchronously: wait before they go out of scope
@@ -705,7 +724,8 @@ void fstat_destroy(fstat_ctx* c) {
     void* ptrs[] = {c->d_fstart, c->d_base, c->d_bins, c->d_bins16, c->d_scale, c->d_state, c->d_tstart, c->d_det_of, c->d_sky,
                     c->d_fdot, c->d_meta, c->d_kh0, c->d_ph0, c->d_abcd, c->d_comb, c->d_twoF, c->d_err,
                     c->tw.hist, c->tw.state, c->tw.tie_count, c->tw.cand_idx, c->tw.cand_val, c->tw.n_cand,
-                    c->tw.out_idx, c->tw.out_val, c->d_inj_work, c->d_sig, c->d_ptab, c->d_pcoef};
+                    c->tw.out_idx, c->tw.out_val, c->d_inj_work, c->d_sig, c->d_ptab, c->d_pcoef,
+                    c->d_bins_w, c->d_floor, c->d_sbar, c->d_weight};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (int i = 0; i < kTimedRing; ++i) {
@@ -895,7 +915,7 @@ int prepare(fstat_ctx* c, cudaStream_t s) {
         const size_t n_tab = (size_t)c->n_sft * c->n_pos;
         if ((rc = grow(c, &c->d_ptab, c->cap_ptab, n_tab)) != FSTAT_OK) return rc;
         if ((rc = grow(c, &c->d_pcoef, c->cap_pcoef, 3 * n_tab)) != FSTAT_OK) return rc;
-        const void* bins = c->opts.bins_form == FSTAT_BINS_C64 ? (const void*)c->d_bins : (const void*)c->d_bins16;
+        const void* bins = c->opts.bins_form == FSTAT_BINS_C64 ? (const void*)work_bins(c) : (const void*)c->d_bins16;
         CUDA_TRY(c, launch_far_tables(bins, c->opts.bins_form, c->row, c->n_sft, c->n_bins, c->gam, c->d_ptab,
                                       c->d_pcoef, c->n_pos, c->far_xoff, s));
         c->launches += 1;
@@ -912,6 +932,7 @@ TimingParams timing_params(const fstat_ctx* c, int n_sky) {
     tp.sky = c->d_sky;
     tp.fdot = c->d_fdot;
     tp.scale = c->d_scale;
+    tp.weight = c->nf_half > 0 ? c->d_weight : nullptr;
     tp.n_sky = n_sky;
     tp.n_sft = c->n_sft;
     tp.n_fdot = c->n_fdot;
@@ -937,7 +958,7 @@ TimingParams timing_params(const fstat_ctx* c, int n_sky) {
 DirichletParams dirichlet_params(const fstat_ctx* c) {
     const Plan& pl = c->plan;
     DirichletParams dp{};
-    dp.bins = c->opts.bins_form == FSTAT_BINS_C64 ? (const void*)c->d_bins : (const void*)c->d_bins16;
+    dp.bins = c->opts.bins_form == FSTAT_BINS_C64 ? (const void*)work_bins(c) : (const void*)c->d_bins16;
     dp.row = c->row;
     dp.k_lo = c->k_lo;
     dp.n_bins = c->n_bins;
@@ -1148,6 +1169,30 @@ int fstat_get_plan(fstat_ctx* c, int32_t* out) {
     const int v[8] = {p.P, p.L, p.M, p.W, p.C, p.lg_row, p.w_pairs, p.far ? kFarIdBase + p.variant : p.variant};
     std::memcpy(out, v, sizeof(v));
     return FSTAT_OK;
+}
+
+int fstat_set_noise_floor(fstat_ctx* c, int32_t half_window) {
+    if (!c) return FSTAT_EINVAL;
+    c->err.clear();
+    if (half_window < 0 || half_window > 64) return fail(c, FSTAT_EINVAL, "half window %d outside 0..64", half_window);
+    if (half_window != c->nf_half) {
+        c->nf_half = half_window;
+        c->sft_dirty = true;
+        c->computed = false;
+    }
+    return FSTAT_OK;
+}
+
+int fstat_get_noise(fstat_ctx* c, float* floor, double* weights, int32_t mem) {
+    if (!c) return FSTAT_EINVAL;
+    c->err.clear();
+    if (c->nf_half <= 0) return fail(c, FSTAT_ESTATE, "noise floor is off");
+    if (c->sft_dirty || !c->d_floor) return fail(c, FSTAT_ESTATE, "noise floor not computed yet (run fstat_compute)");
+    if (set_device(c) != FSTAT_OK) return FSTAT_ECUDA;
+    const cudaMemcpyKind k = mem == FSTAT_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (floor) CUDA_TRY(c, cudaMemcpyAsync(floor, c->d_floor, sizeof(float) * (size_t)c->n_sft * c->n_bins, k, c->stream));
+    if (weights) CUDA_TRY(c, cudaMemcpyAsync(weights, c->d_weight, sizeof(double) * (size_t)c->n_sft, k, c->stream));
+    return sync_ctx(c);
 }
 
 int fstat_test_ring_stall(fstat_ctx* c, int32_t after_sft) {

@@ -150,6 +150,11 @@ __global__ void __launch_bounds__(kTimingBlock) timing_kernel(const TimingParams
         const SftState s = p.st[i];
         double dtau, tdot, a, b;
         timing_antenna(s, fr, p.t_ref, dtau, tdot, a, b);
+        if (p.weight) {   // noise weights: sqrt(w) a, sqrt(w) b in A, B, C and in Fa, Fb
+            const double sw = sqrt(p.weight[i]);
+            a *= sw;
+            b *= sw;
+        }
         sAA += a * a;
         sBB += b * b;
         sAB += a * b;

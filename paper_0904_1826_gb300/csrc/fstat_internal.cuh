@@ -180,6 +180,7 @@ struct TimingParams {
     const double* sky;         // [n_sky][2]
     const double* fdot;        // [n_fdot]
     const float* scale;        // [n_sft] storage scale (1 for complex64)
+    const double* weight;      // [n_sft] noise weights (null: all 1)
     int n_sky, n_sft, n_fdot;
     double f0, df, T, t_ref;
     int P, L, M;
@@ -203,6 +204,8 @@ cudaError_t launch_sft_timing_one(const SftState* st, int n_sft, double alpha, d
 cudaError_t launch_inject(const SftState* st, int n_sft, const fstat_signal* sig_dev, int n_sig,
                           double T, double t_ref, long long k_lo, int n_bins, long long row,
                           float2* bins, double* work, cudaStream_t s);
+cudaError_t launch_noise_floor(const float2* bins, long long row, int n_sft, int n_bins, int half, float* floor,
+                               float2* white, double* sbar, double* weight, cudaStream_t s);
 cudaError_t launch_quantize(const float2* src, long long row, int n_sft, int n_bins, int form,
                             void* dst, float* scale, cudaStream_t s);
 
