@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--proposal-sft", type=int, default=800, help="SFTs per detector (proposal mode)")
     ap.add_argument("--algo", default="auto", choices=["auto", "direct", "farpoly"],
                     help="evaluation of the D-term kernel sum")
+    ap.add_argument("--noise-floor", type=int, default=0,
+                    help="running-median half window of the noise-floor normalisation (0 = off)")
     ap.add_argument("--tile-m", type=int, default=0, help="templates per thread (0 = planner)")
     ap.add_argument("--tile-warps", type=int, default=0, help="warps per block (0 = planner)")
     ap.add_argument("--sft-chunk", type=int, default=0, help="SFTs per staging round (0 = planner)")
@@ -352,6 +354,8 @@ def main():
                      algo=args.algo if algo is None else algo)
         g.load_workload(w)
         g.inject(w.injections, w.bank.t_ref)
+        if args.noise_floor:
+            fs.fstat_set_noise_floor(g.ctx, args.noise_floor)
         return g
 
     def barrier():
@@ -476,6 +480,7 @@ def main():
             "config": {"workload": "plain workunit: 2 det x 1200 gapped SFT (T=1800 s), 1 Hz band at 100 Hz, "
                                    "8 injected signals; 10000 sky x 1800 f x 10 fdot, D=8, top-1000",
                        "form": args.form, "algo": algo_used, "pairs_per_step_per_gpu": n_pairs,
+                       "noise_floor_half_window": args.noise_floor,
                        "l2": "per-step working set ~5 GB (bases, 2F array) > 129 MB L2; L2 flushed before timing",
                        "plan": plan},
             "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": int(h2d),
