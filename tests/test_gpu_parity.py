@@ -326,3 +326,16 @@ def test_ring_wait_timeout_is_reported_and_context_survives(lib):
         _assert_parity(g.twoF(), ref, "after a give-up")
     finally:
         g.close()
+
+
+@pytest.mark.parametrize("n_sft,n_f", [(3, 37), (1, 23), (5, 203)])
+def test_ring_form_edges(lib, n_sft, n_f):
+    """TMA-ring form with fewer SFTs than ring stages, one SFT per detector,
+    and frequency counts that leave ragged lane-groups and columns."""
+    w = config_mid(n_sft=n_sft, n_sky=2, n_f=n_f, n_fdot=3, n_bins=260)
+    bins = _oracle_bins(w)
+    ref = O.compute_fstat_freq_band(_dets(w, bins), w.T, w.k_lo, w.dterms, w.bank).ravel()
+    out = _gpu(lib, w, bins)
+    assert out["plan"]["variant"] >= 107
+    assert out["flags"] & 1 == 0
+    _assert_parity(out["twoF"], ref, f"ring n_sft={n_sft} n_f={n_f}")
