@@ -36,8 +36,10 @@ N_SM = 152
 FP32_LANES = 128
 METRIC = "template·SFT pairs/s (2F) on 1 GB300, chosen vs plain FP32 form at stated 2F error"
 KERNEL_SOURCES = {"direct": ["dirichlet.cuh", "dirichlet_c64.cu", "dirichlet_f16.cu", "dirichlet_bf16.cu"],
-                  "farpoly": ["dirichlet.cuh", "dirichlet_far.cu"]}
-KERNEL_NAMES = {"direct": "dirichlet_kernel", "farpoly": "dirichlet_far_kernel"}
+                  "farpoly": ["dirichlet.cuh", "dirichlet_far.cu"],
+                  "sincpoly": ["dirichlet.cuh", "dirichlet_far.cu"]}
+KERNEL_NAMES = {"direct": "dirichlet_kernel", "farpoly": "dirichlet_far_kernel",
+                "sincpoly": "dirichlet_far_ring_kernel"}
 
 
 def parse():
@@ -59,7 +61,7 @@ def parse():
     ap.add_argument("--n-refine", type=int, default=8, help="patches refined per workunit (proposal mode)")
     ap.add_argument("--train-steps", type=int, default=6000, help="Adam steps (proposal mode)")
     ap.add_argument("--proposal-sft", type=int, default=800, help="SFTs per detector (proposal mode)")
-    ap.add_argument("--algo", default="auto", choices=["auto", "direct", "farpoly"],
+    ap.add_argument("--algo", default="auto", choices=["auto", "direct", "farpoly", "sincpoly"],
                     help="evaluation of the D-term kernel sum")
     ap.add_argument("--noise-floor", type=int, default=0,
                     help="running-median half window of the noise-floor normalisation (0 = off)")
@@ -445,7 +447,8 @@ def main():
 
     forms = {}
     if args.compare_forms and rank == 0:
-        for f, kahan, algo in (("c64", False, "auto"), ("c64", False, "direct"), ("f16", False, "auto"),
+        for f, kahan, algo in (("c64", False, "auto"), ("c64", False, "farpoly"), ("c64", False, "direct"),
+                               ("f16", False, "auto"),
                                ("bf16", False, "auto"), ("c64", True, "direct"), ("f16", True, "direct"),
                                ("bf16", True, "direct")):
             if (f, kahan, algo) == (args.form, False, args.algo):
@@ -454,7 +457,8 @@ def main():
             ms2, kd2, _, _ = timed_run(g2, args.steps, 1)
             name = f + ("+kahan" if kahan else "") + ("" if kahan or algo == "auto" else "/" + algo)
             forms[name] = {"value": n_pairs * args.steps / (ms2 / 1e3), "dirichlet_ms": kd2,
-                           "algo": "farpoly" if g2.plan()["variant"] >= 100 else "direct"}
+                           "algo": ("direct" if g2.plan()["variant"] < 100 else
+                                    "sincpoly" if g2.plan()["variant"] >= 112 else "farpoly")}
             g2.close()
 
     if rank != 0:
@@ -465,8 +469,9 @@ def main():
     clock_mhz = 2070.0
     peak = N_SM * FP32_LANES * 2 * clock_mhz * 1e6 / 1e12       # TFLOP/s, recipe unit counts, max clock
     achieved = FLOP_PER_PAIR * n_pairs / (k_dir / 1e3) / 1e12
-    algo_used = "farpoly" if plan.get("variant", 0) >= 100 else "direct"
-    kernel_name = KERNEL_NAMES[algo_used] if plan.get("variant", 0) < 107 else "dirichlet_far_ring_kernel"
+    vid = plan.get("variant", 0)
+    algo_used = "direct" if vid < 100 else ("sincpoly" if vid >= 112 else "farpoly")
+    kernel_name = KERNEL_NAMES[algo_used] if vid < 107 else "dirichlet_far_ring_kernel"
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": ncu_traffic(args.form, algo_used), "kernel": kernel_name,
                 "dirichlet_ms": k_dir, "step_ms_device": k_step,

@@ -89,8 +89,20 @@ typedef struct {
  *   are precomputed per SFT and window position (interpolation error below
  *   5e-6 of each term); needs two tables of 16 and 48 bytes per stored bin
  *   and SFT.  Batched workunits always use DIRECT.
- * AUTO: FARPOLY where it applies, else DIRECT. */
-typedef enum { FSTAT_ALGO_AUTO = 0, FSTAT_ALGO_DIRECT = 1, FSTAT_ALGO_FARPOLY = 2 } fstat_algo;
+ * SINCPOLY (D = 8, no Kahan): the whole window term, sin(pi kappa) times the
+ *   2D-bin sum, is entire in kappa and is evaluated as one degree-9
+ *   polynomial in kappa - 1/2 with coefficients precomputed per SFT and window
+ *   position (80 bytes per stored bin and SFT; no reciprocal, sine or clamp
+ *   per template).  It runs in the TMA-ring staging (uniform spindown grid,
+ *   P df T = 2); elsewhere it falls back to FARPOLY.
+ * AUTO: SINCPOLY where the TMA ring applies, else FARPOLY where it applies,
+ *   else DIRECT. */
+typedef enum {
+    FSTAT_ALGO_AUTO = 0,
+    FSTAT_ALGO_DIRECT = 1,
+    FSTAT_ALGO_FARPOLY = 2,
+    FSTAT_ALGO_SINCPOLY = 3
+} fstat_algo;
 
 typedef struct {
     double lat_rad;       /* geodetic latitude of the vertex */
@@ -231,8 +243,8 @@ int fstat_test_ring_stall(fstat_ctx *ctx, int32_t after_sft);
 
 /* Tile configuration chosen for the current bank (after fstat_set_templates):
  * out[8] = (P, L, M, warps, sft_chunk, lane-groups per column row,
- *           staged pairs per SFT, kernel variant id; ids from 100 up are the
- *           far-field polynomial form). */
+ *           staged pairs per SFT, kernel variant id; ids 100..111 are the
+ *           far-field polynomial form, 112..115 the sinc-polynomial form). */
 int fstat_get_plan(fstat_ctx *ctx, int32_t *out);
 
 /* Number of CUDA kernels this context has launched since it was created. */

@@ -45,9 +45,12 @@ constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 struct FarRow {
     int M, L;
     int ring;   // compute warps of the TMA-ring staging (L = 2, uniform spindown grid), 0 = cp.async rounds
+    bool sinc;  // sinc-polynomial form (whole window as one polynomial), else near pairs + far polynomial
 };
-const FarRow kFarVariants[] = {{7, 2, 0}, {5, 2, 0}, {9, 2, 0}, {7, 1, 0}, {9, 1, 0}, {5, 1, 0},
-                               {1, 1, 0}, {5, 2, 8}, {7, 2, 8}, {9, 2, 8}, {5, 2, 10}, {7, 2, 10}};
+const FarRow kFarVariants[] = {{7, 2, 0, false},  {5, 2, 0, false},  {9, 2, 0, false},  {7, 1, 0, false},
+                               {9, 1, 0, false},  {5, 1, 0, false},  {1, 1, 0, false},  {5, 2, 8, false},
+                               {7, 2, 8, false},  {9, 2, 8, false},  {5, 2, 10, false}, {7, 2, 10, false},
+                               {5, 2, 10, true},  {7, 2, 10, true},  {5, 2, 8, true},   {7, 2, 8, true}};
 constexpr int kNumFar = sizeof(kFarVariants) / sizeof(kFarVariants[0]);
 constexpr int kFarIdBase = 100;   // variant ids reported for the far-field form
 
@@ -58,6 +61,7 @@ struct Plan {
     int w_pairs = 0, w_tab = 0, w_raw = 0, variant = 5;
     bool far = false;   // far-field polynomial form (variant indexes kFarVariants)
     bool ring = false;  // far-field form with TMA-ring staging; C = stages, W includes the producer warp
+    bool sinc = false;  // sinc-polynomial form (TMA ring only)
     size_t smem = 0;
     long long grid = 0;
 };
@@ -98,6 +102,8 @@ struct fstat_ctx {
     bool sft_dirty = true;          // state / quantisation need refresh
     bool tab_dirty = true;          // far-field tables need a rebuild
     FarGamma gam{};                 // far-field interpolation weights
+    SincGamma sgam{};               // sinc-polynomial interpolation weights
+    bool tab_sinc = false;          // kind of the built tables
     float4* d_ptab = nullptr;       // far-field pair table [n_sft][n_pos]
     float4* d_pcoef = nullptr;      // far-field coefficients [n_sft][4][n_pos]
     size_t cap_ptab = 0, cap_pcoef = 0;
@@ -258,6 +264,42 @@ FarGamma far_gamma() {
     return G;
 }
 
+// Weights of the sinc-polynomial form: for each window offset k = -7..8, the
+// monomial coefficients in u = kappa - 1/2 of the degree-kSincDeg polynomial
+// interpolating sin(pi kappa) / (2 (kappa - k)) at the Chebyshev points of
+// u in [-1/2, 1/2] (FP64 Gaussian elimination, stored FP32).
+SincGamma sinc_gamma() {
+    SincGamma G{};
+    constexpr int N = kSincDeg + 1;
+    for (int i = 0; i < kSincTerms; ++i) {
+        const double k = i - 7;
+        double A[N][N + 1];
+        for (int j = 0; j < N; ++j) {
+            const double u = 0.5 * std::cos((2.0 * j + 1.0) * kPi / (2.0 * N));
+            const double kap = u + 0.5;
+            double pw = 1.0;
+            for (int n = 0; n < N; ++n) {
+                A[j][n] = pw;
+                pw *= u;
+            }
+            A[j][N] = std::sin(kPi * kap) / (2.0 * (kap - k));
+        }
+        for (int col = 0; col < N; ++col) {
+            int piv = col;
+            for (int r = col + 1; r < N; ++r)
+                if (std::fabs(A[r][col]) > std::fabs(A[piv][col])) piv = r;
+            for (int t = 0; t <= N; ++t) std::swap(A[col][t], A[piv][t]);
+            for (int r = 0; r < N; ++r) {
+                if (r == col) continue;
+                const double f = A[r][col] / A[col][col];
+                for (int t = col; t <= N; ++t) A[r][t] -= f * A[col][t];
+            }
+        }
+        for (int n = 0; n < N; ++n) G.g[i][n] = (float)(A[n][N] / A[n][n]);
+    }
+    return G;
+}
+
 bool far_eligible(const fstat_ctx* c) {
     return c->opts.dterms == 8 && !c->opts.kahan && c->opts.algo != FSTAT_ALGO_DIRECT;
 }
@@ -307,6 +349,9 @@ bool make_far_plan(fstat_ctx* c, int P, int L, bool found, Plan& best) {
     bool have_ring = false;
     // TMA-ring form first: L = 2, compact spindown bases
     // default: 10 compute warps + 1 copy warp (measured fastest on GB300); tile_warps 9 / 11 choose 8 / 10
+    // AUTO takes the sinc-polynomial form where the ring applies (1027 ms per
+    // workunit launch on GB300 against 1105 ms for near pairs + far polynomial)
+    const bool want_sinc = c->opts.algo == FSTAT_ALGO_SINCPOLY || c->opts.algo == FSTAT_ALGO_AUTO;
     if (found && L == 2 && c->fdot_uniform && (c->opts.tile_warps == 0 || c->opts.tile_warps >= 9)) {
         // M = 5 with 8 stages measured fastest on GB300 (1105 ms on the workunit; M = 7: 1139 ms)
         std::vector<int> Mr = {5};
@@ -316,7 +361,7 @@ bool make_far_plan(fstat_ctx* c, int P, int L, bool found, Plan& best) {
         for (int M_ : Mr) {
             int fid = -1;
             for (int i = 0; i < kNumFar; ++i)
-                if (kFarVariants[i].ring == nwc && kFarVariants[i].M == M_) fid = i;
+                if (kFarVariants[i].ring == nwc && kFarVariants[i].M == M_ && kFarVariants[i].sinc == want_sinc) fid = i;
             if (fid < 0) continue;
             const int PM = P * M_;
             const int lg_cta = 32 * nwc / P;
@@ -328,9 +373,10 @@ bool make_far_plan(fstat_ctx* c, int P, int L, bool found, Plan& best) {
                 int hf = (w_pairs + 1) / 2;
                 hf += ((4 - hf % 8) + 8) % 8;
                 const int w_tab = 2 * hf;
+                const int rec = want_sinc ? 80 : 48;
                 int S = c->opts.sft_chunk > 0 ? c->opts.sft_chunk : 8;
-                while (S > 3 && ring_smem(S, w_tab).total > 110 * 1024) --S;
-                const size_t smem = ring_smem(S, w_tab).total;
+                while (S > 3 && ring_smem(S, w_tab, rec).total > 110 * 1024) --S;
+                const size_t smem = ring_smem(S, w_tab, rec).total;
                 if (smem > 220 * 1024) continue;
                 double cost = 0.0;
                 int chunks_max = 0;
@@ -364,6 +410,7 @@ bool make_far_plan(fstat_ctx* c, int P, int L, bool found, Plan& best) {
                     best.variant = fid;
                     best.far = true;
                     best.ring = true;
+                    best.sinc = want_sinc;
                     best.smem = smem;
                     best.grid = (long long)c->n_sky * n_col * chunks_max;
                     have_ring = true;
@@ -385,7 +432,7 @@ bool make_far_plan(fstat_ctx* c, int P, int L, bool found, Plan& best) {
         if (M_ > 1 && !found) continue;
         int fid = -1;
         for (int i = 0; i < kNumFar; ++i)
-            if (kFarVariants[i].ring == 0 && kFarVariants[i].M == M_ && kFarVariants[i].L == Lq) fid = i;
+            if (kFarVariants[i].ring == 0 && !kFarVariants[i].sinc && kFarVariants[i].M == M_ && kFarVariants[i].L == Lq) fid = i;
         if (fid < 0) continue;
         const int Pv = found ? P : 1;
         const int PM = Pv * M_;
@@ -684,14 +731,16 @@ int fstat_create(fstat_ctx** out, int device, const fstat_opts* opts) {
     if (o.bins_form < 0 || o.bins_form > 2) return FSTAT_EINVAL;
     if (o.tile_m < 0 || o.tile_warps < 0 || o.tile_warps > 11 || o.sft_chunk < 0 || o.sft_chunk > 64)
         return FSTAT_EINVAL;
-    if (o.algo < FSTAT_ALGO_AUTO || o.algo > FSTAT_ALGO_FARPOLY) return FSTAT_EINVAL;
-    if (o.algo == FSTAT_ALGO_FARPOLY && (o.dterms != 8 || o.kahan)) return FSTAT_EINVAL;
+    if (o.algo < FSTAT_ALGO_AUTO || o.algo > FSTAT_ALGO_SINCPOLY) return FSTAT_EINVAL;
+    if ((o.algo == FSTAT_ALGO_FARPOLY || o.algo == FSTAT_ALGO_SINCPOLY) && (o.dterms != 8 || o.kahan))
+        return FSTAT_EINVAL;
     int n_dev = 0;
     if (cudaGetDeviceCount(&n_dev) != cudaSuccess || device < 0 || device >= n_dev) return FSTAT_ECUDA;
     fstat_ctx* c = new fstat_ctx();
     c->device = device;
     c->opts = o;
     c->gam = far_gamma();
+    c->sgam = sinc_gamma();
     if (set_device(c) != FSTAT_OK) {
         delete c;
         return FSTAT_ECUDA;
@@ -911,17 +960,25 @@ int prepare(fstat_ctx* c, cudaStream_t s) {
     if ((rc = grow(c, &c->d_twoF, c->cap_twoF, n_twoF)) != FSTAT_OK) return rc;
     if ((rc = ensure_topk(c)) != FSTAT_OK) return rc;
     if (c->plan.far) far_extent(c, c->plan.w_pairs, &c->far_xoff, &c->n_pos);
-    if (c->plan.far && (c->tab_dirty || c->tab_npos != c->n_pos || c->tab_xoff != c->far_xoff)) {
+    if (c->plan.far &&
+        (c->tab_dirty || c->tab_npos != c->n_pos || c->tab_xoff != c->far_xoff || c->tab_sinc != c->plan.sinc)) {
         const size_t n_tab = (size_t)c->n_sft * c->n_pos;
-        if ((rc = grow(c, &c->d_ptab, c->cap_ptab, n_tab)) != FSTAT_OK) return rc;
-        if ((rc = grow(c, &c->d_pcoef, c->cap_pcoef, 3 * n_tab)) != FSTAT_OK) return rc;
         const void* bins = c->opts.bins_form == FSTAT_BINS_C64 ? (const void*)work_bins(c) : (const void*)c->d_bins16;
-        CUDA_TRY(c, launch_far_tables(bins, c->opts.bins_form, c->row, c->n_sft, c->n_bins, c->gam, c->d_ptab,
-                                      c->d_pcoef, c->n_pos, c->far_xoff, s));
+        if (c->plan.sinc) {
+            if ((rc = grow(c, &c->d_pcoef, c->cap_pcoef, 5 * n_tab)) != FSTAT_OK) return rc;
+            CUDA_TRY(c, launch_sinc_tables(bins, c->opts.bins_form, c->row, c->n_sft, c->n_bins, c->sgam, c->d_pcoef,
+                                           c->n_pos, c->far_xoff, s));
+        } else {
+            if ((rc = grow(c, &c->d_ptab, c->cap_ptab, n_tab)) != FSTAT_OK) return rc;
+            if ((rc = grow(c, &c->d_pcoef, c->cap_pcoef, 3 * n_tab)) != FSTAT_OK) return rc;
+            CUDA_TRY(c, launch_far_tables(bins, c->opts.bins_form, c->row, c->n_sft, c->n_bins, c->gam, c->d_ptab,
+                                          c->d_pcoef, c->n_pos, c->far_xoff, s));
+        }
         c->launches += 1;
         c->tab_dirty = false;
         c->tab_npos = c->n_pos;
         c->tab_xoff = c->far_xoff;
+        c->tab_sinc = c->plan.sinc;
     }
     return FSTAT_OK;
 }

@@ -104,6 +104,112 @@ __device__ __forceinline__ float2 far_window_sum(const float4* __restrict__ pn, 
     return __ffma2_rn(S4, make_float2(r4, r4), F);
 }
 
+// Sinc-polynomial form of one SFT for one thread's M templates: cf is the
+// staged row of 80-byte records (c0..c9 complex, in u = kappa - 1/2),
+// parity-split for L = 2.  P(u) already carries sin(pi kappa)/2, so the
+// template's term is the twiddle times P, with no reciprocal, sine or clamp.
+template <int M, int L>
+__device__ __forceinline__ void sinc_sft(const DirichletParams& p, const SkySftMeta& m, long long kh_row,
+                                         unsigned int ph0, int lo_rel, const float4* __restrict__ cf, int half,
+                                         int j_t, float2 (&fa)[M], float2 (&fb)[M]) {
+    constexpr int D = 8;
+    const long long kh = kh_row + (long long)j_t * m.dk;
+    const int k0 = (int)(kh >> 32);
+    const int b = (k0 - (int)p.k_lo) - (D - 1) - lo_rel;
+    const float2 a2 = make_float2(m.a, m.a), b2 = make_float2(m.b, m.b);
+    auto poly = [&](const float4* __restrict__ r, float u) -> float2 {
+        const float4 e0 = r[0], e1 = r[1], e2 = r[2], e3 = r[3], e4 = r[4];
+        const float2 uu = make_float2(u, u);
+        float2 P = make_float2(e4.z, e4.w);
+        P = __ffma2_rn(P, uu, make_float2(e4.x, e4.y));
+        P = __ffma2_rn(P, uu, make_float2(e3.z, e3.w));
+        P = __ffma2_rn(P, uu, make_float2(e3.x, e3.y));
+        P = __ffma2_rn(P, uu, make_float2(e2.z, e2.w));
+        P = __ffma2_rn(P, uu, make_float2(e2.x, e2.y));
+        P = __ffma2_rn(P, uu, make_float2(e1.z, e1.w));
+        P = __ffma2_rn(P, uu, make_float2(e1.x, e1.y));
+        P = __ffma2_rn(P, uu, make_float2(e0.z, e0.w));
+        return __ffma2_rn(P, uu, make_float2(e0.x, e0.y));
+    };
+    auto add = [&](float tw_re, float tw_im, float2 P, float2& fa_q, float2& fb_q) {
+        const float2 z = make_float2(fmaf(tw_re, P.x, -tw_im * P.y), fmaf(tw_re, P.y, tw_im * P.x));
+        fa_q = __ffma2_rn(a2, z, fa_q);
+        fb_q = __ffma2_rn(b2, z, fb_q);
+    };
+    const bool fast = ((int)((kh + m.span) >> 32) == k0 + (M - 1) * L);
+    if (fast) {
+        int bb = b;
+        if (bb < 0 || bb + (M - 1) * L + 2 * (D - 1) >= p.w_pairs) {
+            atomicOr(p.err, 1);
+            bb = max(0, min(bb, p.w_pairs - 1 - (M - 1) * L - 2 * (D - 1)));
+        }
+        const float4* cp = cf + 5 * tab_pos<L>(bb + 7, half);
+        const unsigned int ph = ph0 + (unsigned int)j_t * m.dphi + ((unsigned int)k0 << 31);
+        float sn, cs;
+        __sincosf((float)(int)ph * kPhaseToRad, &sn, &cs);
+        float tw_re = cs, tw_im = -sn;
+        const float u0 = frac_to_float((unsigned int)kh) - 0.5f;
+#pragma unroll
+        for (int q = 0; q < M; ++q) {
+            add(tw_re, tw_im, poly(cp + 5 * q, fmaf((float)q, m.eps, u0)), fa[q], fb[q]);
+            if (q + 1 < M) {
+                const float t = fmaf(tw_re, m.rot_re, -tw_im * m.rot_im);
+                tw_im = fmaf(tw_re, m.rot_im, tw_im * m.rot_re);
+                tw_re = t;
+            }
+        }
+    } else {
+        const long long pdk = (long long)p.P * m.dk;
+#pragma unroll
+        for (int q = 0; q < M; ++q) {
+            const long long khq = kh + (long long)q * pdk;
+            const int k0q = (int)(khq >> 32);
+            const unsigned int phq = ph0 + (unsigned int)(j_t + q * p.P) * m.dphi + ((unsigned int)k0q << 31);
+            float s2, c2;
+            __sincosf((float)(int)phq * kPhaseToRad, &s2, &c2);
+            int bq = b + (k0q - k0);
+            if (bq < 0 || bq + 2 * (D - 1) >= p.w_pairs) {
+                atomicOr(p.err, 1);
+                bq = max(0, min(bq, p.w_pairs - 1 - 2 * (D - 1)));
+            }
+            add(c2, -s2, poly(cf + 5 * tab_pos<L>(bq + 7, half), frac_to_float((unsigned int)khq) - 0.5f), fa[q],
+                fb[q]);
+        }
+    }
+}
+
+template <int FORM>
+__global__ void __launch_bounds__(256) sinc_tables_kernel(const typename RawT<FORM>::T* __restrict__ bins,
+                                                          long long row, int n_sft, int n_bins, const SincGamma gam,
+                                                          float4* __restrict__ pcoef, int n_pos, int xoff) {
+    using RT = RawT<FORM>;
+    const long long total = (long long)n_sft * n_pos;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int s = (int)(t / n_pos);
+        const int x = (int)(t - (long long)s * n_pos);
+        const int r = x - xoff;
+        const size_t o = (size_t)s * n_pos + (size_t)(x & 1) * (n_pos >> 1) + (x >> 1);   // parity-split slot
+        const typename RT::T* rp = bins + (size_t)s * row;
+        float cr[kSincDeg + 1], ci[kSincDeg + 1];
+#pragma unroll
+        for (int n = 0; n <= kSincDeg; ++n) cr[n] = ci[n] = 0.f;
+#pragma unroll
+        for (int i = 0; i < kSincTerms; ++i) {
+            const int j = r + i - 7;
+            const float2 v = (j >= 0 && j < n_bins) ? RT::f2(rp[j]) : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int n = 0; n <= kSincDeg; ++n) {
+                cr[n] = fmaf(v.x, gam.g[i][n], cr[n]);
+                ci[n] = fmaf(v.y, gam.g[i][n], ci[n]);
+            }
+        }
+        float4* cp = pcoef + o * 5;
+#pragma unroll
+        for (int h = 0; h < 5; ++h) cp[h] = make_float4(cr[2 * h], ci[2 * h], cr[2 * h + 1], ci[2 * h + 1]);
+    }
+}
+
 // One SFT of one thread's M templates: kh_row / ph0 are the fixed-point bin
 // and phase bases of the thread's spindown row, lo_rel the bin of the staged
 // rows' entry 0 relative to k_lo, tab / cf the staged pair and coefficient
@@ -382,11 +488,12 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
 
 // L = 2, uniform spindown grid.  Warps 0..NW-1 compute, warp NW produces.
 // Error flag bit 2: a pipeline wait gave up (results of the block invalid).
-template <int M>
+template <int M, bool SINC>
 __device__ __forceinline__ void far_ring_block(const DirichletParams& p, long long bid, unsigned char* smem) {
     constexpr int D = 8, L = 2;
+    constexpr int REC = SINC ? 80 : 48;   // bytes per coefficient record
     const int S = p.sft_chunk;
-    const RingSmem lay = ring_smem(S, p.w_tab);
+    const RingSmem lay = ring_smem(S, p.w_tab, REC);
     const int NW = (int)(blockDim.x >> 5) - 1;
 
     const int chunk = (int)(bid % p.chunks_per_col);
@@ -437,7 +544,7 @@ __device__ __forceinline__ void far_ring_block(const DirichletParams& p, long lo
         const int nh = p.n_pos >> 1;
         const int half = p.w_tab >> 1;
         const int n0 = (p.w_pairs + 1) >> 1, n1 = p.w_pairs >> 1;
-        const uint32_t bytes = 48u + 32u + (uint32_t)(n0 + n1) * 64u;
+        const uint32_t bytes = 48u + 32u + (uint32_t)(n0 + n1) * (SINC ? 80u : 64u);
         int a = 0;
         bool stop = false;
         int pslot = 0;            // slot of SFT a
@@ -476,10 +583,11 @@ __device__ __forceinline__ void far_ring_block(const DirichletParams& p, long lo
                         for (int h = 0; h < 2; ++h) {
                             const int cnt = h ? n1 : n0;
                             const size_t go = (size_t)a * p.n_pos + (size_t)((x0 + h) & 1) * nh + ((x0 + h) >> 1);
-                            bulk_g2s(ss + (uint32_t)(lay.pairs + (size_t)h * half * 16), p.ptab + go,
-                                     (uint32_t)cnt * 16u, fb);
-                            bulk_g2s(ss + (uint32_t)(lay.coef + (size_t)h * half * 48), p.pcoef + 3 * go,
-                                     (uint32_t)cnt * 48u, fb);
+                            if (!SINC)
+                                bulk_g2s(ss + (uint32_t)(lay.pairs + (size_t)h * half * 16), p.ptab + go,
+                                         (uint32_t)cnt * 16u, fb);
+                            bulk_g2s(ss + (uint32_t)(lay.coef + (size_t)h * half * REC),
+                                     p.pcoef + (size_t)(REC / 16) * go, (uint32_t)cnt * REC, fb);
                         }
                         ++a;
                         if (++pslot == S) {   // the next use of slot 0 waits for the phase after this one
@@ -513,9 +621,13 @@ __device__ __forceinline__ void far_ring_block(const DirichletParams& p, long lo
                 const SkySftMeta m = *reinterpret_cast<const SkySftMeta*>(st + lay.meta);
                 const SkySftBase bs = *reinterpret_cast<const SkySftBase*>(st + lay.base);
                 const int lo_rel = *reinterpret_cast<const int*>(st + lay.lo);
-                far_sft<M, L>(p, m, bs.kh0 + (long long)drow * bs.dkh, bs.ph0 + (unsigned int)drow * bs.dph, lo_rel,
-                              reinterpret_cast<const float4*>(st + lay.pairs),
-                              reinterpret_cast<const float4*>(st + lay.coef), half, j_t, fa, fb);
+                if (SINC)
+                    sinc_sft<M, L>(p, m, bs.kh0 + (long long)drow * bs.dkh, bs.ph0 + (unsigned int)drow * bs.dph,
+                                   lo_rel, reinterpret_cast<const float4*>(st + lay.coef), half, j_t, fa, fb);
+                else
+                    far_sft<M, L>(p, m, bs.kh0 + (long long)drow * bs.dkh, bs.ph0 + (unsigned int)drow * bs.dph,
+                                  lo_rel, reinterpret_cast<const float4*>(st + lay.pairs),
+                                  reinterpret_cast<const float4*>(st + lay.coef), half, j_t, fa, fb);
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(empty_bar(slot));
@@ -544,10 +656,10 @@ __device__ __forceinline__ void far_ring_block(const DirichletParams& p, long lo
 }
 
 // NWC compute warps plus the producer; two resident blocks per SM.
-template <int M, int NWC>
+template <int M, int NWC, bool SINC>
 __global__ void __launch_bounds__(32 * (NWC + 1), 2) dirichlet_far_ring_kernel(const DirichletParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
-    far_ring_block<M>(p, (long long)blockIdx.x, smem);
+    far_ring_block<M, SINC>(p, (long long)blockIdx.x, smem);
 }
 
 // Persistent ring form over many template banks (workunits): every block
@@ -555,7 +667,7 @@ __global__ void __launch_bounds__(32 * (NWC + 1), 2) dirichlet_far_ring_kernel(c
 // all banks are done, runs it as far_ring_block (whose barriers it sets up and
 // invalidates), and the block that completes a bank's last item stamps its
 // completion time.  At most `total` items per block; no block waits on another.
-template <int M, int NWC>
+template <int M, int NWC, bool SINC>
 __global__ void __launch_bounds__(32 * (NWC + 1), 2)
     dirichlet_far_ring_batch_kernel(const DirichletParams* __restrict__ banks,
                                     const long long* __restrict__ item_prefix, int n_wu,
@@ -582,7 +694,7 @@ __global__ void __launch_bounds__(32 * (NWC + 1), 2)
         if (it >= total) break;
         const int w = s_wu;
         const DirichletParams p = banks[w];
-        far_ring_block<M>(p, it - item_prefix[w], smem);
+        far_ring_block<M, SINC>(p, it - item_prefix[w], smem);
         __syncthreads();
         if (threadIdx.x == 0) {
             __threadfence();
@@ -603,11 +715,15 @@ __global__ void __launch_bounds__(32 * (NWC + 1), 2)
     X(5, 5, 1)             \
     X(6, 1, 1)
 #define FS_RING_VARIANTS(X) \
-    X(7, 5, 8)              \
-    X(8, 7, 8)              \
-    X(9, 9, 8)              \
-    X(10, 5, 10)            \
-    X(11, 7, 10)
+    X(7, 5, 8, false)       \
+    X(8, 7, 8, false)       \
+    X(9, 9, 8, false)       \
+    X(10, 5, 10, false)     \
+    X(11, 7, 10, false)     \
+    X(12, 5, 10, true)      \
+    X(13, 7, 10, true)      \
+    X(14, 5, 8, true)       \
+    X(15, 7, 8, true)
 
 cudaError_t launch_dirichlet_far(int v, const DirichletParams& p, int threads, size_t smem, long long grid,
                                  cudaStream_t s) {
@@ -622,9 +738,9 @@ cudaError_t launch_dirichlet_far(int v, const DirichletParams& p, int threads, s
     }
         FS_FAR_VARIANTS(FS_FCASE)
 #undef FS_FCASE
-#define FS_RCASE(ID, M_, W_)                                                                              \
+#define FS_RCASE(ID, M_, W_, S_)                                                                          \
     case ID: {                                                                                            \
-        auto fn = dirichlet_far_ring_kernel<M_, W_>;                                                      \
+        auto fn = dirichlet_far_ring_kernel<M_, W_, S_>;                                                  \
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
         if (e != cudaSuccess) return e;                                                                   \
         fn<<<(unsigned)grid, threads, smem, s>>>(p);                                                      \
@@ -640,9 +756,9 @@ cudaError_t launch_dirichlet_far(int v, const DirichletParams& p, int threads, s
 cudaError_t launch_dirichlet_far_batch(int v, const DirichletBatch& b, int threads, size_t smem, int grid,
                                        cudaStream_t s) {
     switch (v) {
-#define FS_BRCASE(ID, M_, W_)                                                                             \
+#define FS_BRCASE(ID, M_, W_, S_)                                                                         \
     case ID: {                                                                                            \
-        auto fn = dirichlet_far_ring_batch_kernel<M_, W_>;                                                \
+        auto fn = dirichlet_far_ring_batch_kernel<M_, W_, S_>;                                            \
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
         if (e != cudaSuccess) return e;                                                                   \
         fn<<<grid, threads, smem, s>>>(b.banks, b.item_prefix, b.n_wu, b.queue, b.remaining, b.done_ns);  \
@@ -657,9 +773,9 @@ cudaError_t launch_dirichlet_far_batch(int v, const DirichletBatch& b, int threa
 
 cudaError_t dirichlet_far_batch_occupancy(int v, int threads, size_t smem, int* blocks_per_sm) {
     switch (v) {
-#define FS_BOCASE(ID, M_, W_)                                                                             \
+#define FS_BOCASE(ID, M_, W_, S_)                                                                         \
     case ID: {                                                                                            \
-        auto fn = dirichlet_far_ring_batch_kernel<M_, W_>;                                                \
+        auto fn = dirichlet_far_ring_batch_kernel<M_, W_, S_>;                                            \
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
         if (e != cudaSuccess) return e;                                                                   \
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, threads, smem);           \
@@ -669,6 +785,22 @@ cudaError_t dirichlet_far_batch_occupancy(int v, int threads, size_t smem, int* 
         default:
             return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_sinc_tables(const void* bins, int form, long long row, int n_sft, int n_bins,
+                               const SincGamma& gam, float4* pcoef, int n_pos, int xoff, cudaStream_t s) {
+    const long long total = (long long)n_sft * n_pos;
+    const int grid = (int)std::min<long long>((total + 255) / 256, 152LL * 16);
+    if (form == FSTAT_BINS_C64)
+        sinc_tables_kernel<FSTAT_BINS_C64><<<grid, 256, 0, s>>>(static_cast<const float2*>(bins), row, n_sft, n_bins,
+                                                                 gam, pcoef, n_pos, xoff);
+    else if (form == FSTAT_BINS_F16)
+        sinc_tables_kernel<FSTAT_BINS_F16><<<grid, 256, 0, s>>>(static_cast<const __half2*>(bins), row, n_sft,
+                                                                 n_bins, gam, pcoef, n_pos, xoff);
+    else
+        sinc_tables_kernel<FSTAT_BINS_BF16><<<grid, 256, 0, s>>>(static_cast<const __nv_bfloat162*>(bins), row, n_sft,
+                                                                  n_bins, gam, pcoef, n_pos, xoff);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_far_tables(const void* bins, int form, long long row, int n_sft, int n_bins, const FarGamma& gam,

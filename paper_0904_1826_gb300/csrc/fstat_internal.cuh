@@ -106,6 +106,17 @@ struct FarGamma {
 };
 __host__ __device__ constexpr int far_offset(int i) { return i < 6 ? i - 7 : i - 3; }
 
+// Sinc-polynomial form (D = 8): the whole window term
+//   P(kappa) = (sin(pi kappa) / 2) sum_{k=-7..8} X_{k0+k} / (kappa - k)
+// is entire in kappa (sin vanishes at every integer), so it is replaced by
+// its degree-9 interpolant in u = kappa - 1/2, sum_n c_n u^n, with
+// c_n = sum_k X_{k0+k} gamma[k][n]; no reciprocal, sine or clamp remains.
+constexpr int kSincDeg = 9;
+constexpr int kSincTerms = 16;
+struct SincGamma {
+    float g[kSincTerms][kSincDeg + 1];   // [offset k + 7][power]
+};
+
 // Shared-memory layout of the far-field kernel (offsets in bytes).
 struct PolySmem {
     size_t pairs, coef, meta, base, kh0, ph0, total;
@@ -151,11 +162,13 @@ __host__ __device__ inline PolySmem farpoly_smem(int sft_chunk, int w_tab, int n
 struct RingSmem {
     size_t stage, pairs, coef, meta, base, lo, bars, ctrl, total;
 };
-__host__ __device__ inline RingSmem ring_smem(int stages, int w_tab) {
+// rec = bytes per coefficient record (48 far-field, 80 sinc); the sinc form
+// stages no pair table.
+__host__ __device__ inline RingSmem ring_smem(int stages, int w_tab, int rec = 48) {
     RingSmem r;
     r.pairs = 0;
-    r.coef = (size_t)w_tab * 16;
-    r.meta = r.coef + (size_t)w_tab * 48;
+    r.coef = rec == 48 ? (size_t)w_tab * 16 : 0;
+    r.meta = r.coef + (size_t)w_tab * rec;
     r.base = r.meta + 48;
     r.lo = r.base + 32;
     r.stage = (r.lo + 16 + 127) & ~(size_t)127;
@@ -229,6 +242,8 @@ struct TopkWork {
 };
 cudaError_t launch_far_tables(const void* bins, int form, long long row, int n_sft, int n_bins, const FarGamma& gam,
                               float4* ptab, float4* pcoef, int n_pos, int xoff, cudaStream_t s);
+cudaError_t launch_sinc_tables(const void* bins, int form, long long row, int n_sft, int n_bins,
+                               const SincGamma& gam, float4* pcoef, int n_pos, int xoff, cudaStream_t s);
 cudaError_t launch_dirichlet_far(int v, const DirichletParams& p, int threads, size_t smem, long long grid,
                                  cudaStream_t s);
 cudaError_t launch_dirichlet_far_batch(int v, const DirichletBatch& b, int threads, size_t smem, int grid,

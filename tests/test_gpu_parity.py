@@ -99,7 +99,7 @@ def test_sft_timing_and_abcd_match_oracle(lib):
 
 # ---------------------------------------------------------------- kernels (b)-(d): 2F and toplist
 
-ALGOS = ["farpoly", "direct"]
+ALGOS = ["farpoly", "direct", "sincpoly"]
 
 
 @pytest.mark.parametrize("algo", ALGOS)
@@ -108,7 +108,7 @@ def test_config0_parity_and_recovery(lib, algo):
     bins = _oracle_bins(w)
     ref = O.compute_fstat_freq_band(_dets(w, bins), w.T, w.k_lo, w.dterms, w.bank).ravel()
     out = _gpu(lib, w, bins, algo=algo)
-    assert (out["plan"]["variant"] >= 100) == (algo == "farpoly")
+    assert (out["plan"]["variant"] >= 100) == (algo != "direct")
     assert out["flags"] == 0
     _assert_parity(out["twoF"], ref, "config0")
     _check_toplist(out["top"], out["twoF"], ref, w.topk)
@@ -266,7 +266,8 @@ def test_errors_are_reported_not_raised_on_device(lib):
         assert e.value.code == lib.FSTAT_EINVAL
         with pytest.raises(lib.FstatError):
             lib.fstat_create(0, dterms=0)
-        for bad_opts in (dict(algo=3), dict(algo="farpoly", dterms=5), dict(algo="farpoly", kahan=True)):
+        for bad_opts in (dict(algo=4), dict(algo="farpoly", dterms=5), dict(algo="farpoly", kahan=True),
+                         dict(algo="sincpoly", dterms=5)):
             with pytest.raises(lib.FstatError) as e:
                 lib.fstat_create(0, **bad_opts)
             assert e.value.code == lib.FSTAT_EINVAL

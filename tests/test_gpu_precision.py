@@ -44,7 +44,7 @@ def case():
     return w, bins, ref.ravel()
 
 
-FORMS = [("c64", False, "farpoly"), ("c64", False, "direct"), ("c64", True, "direct"),
+FORMS = [("c64", False, "sincpoly"), ("c64", False, "farpoly"), ("c64", False, "direct"), ("c64", True, "direct"),
          ("f16", False, "farpoly"), ("f16", True, "direct"), ("bf16", False, "farpoly"), ("bf16", True, "direct")]
 
 
