@@ -103,8 +103,10 @@ struct fstat_ctx {
     bool tab_dirty = true;          // far-field tables need a rebuild
     FarGamma gam{};                 // far-field interpolation weights
     SincGamma sgam{};               // sinc-polynomial interpolation weights
+    float* d_hscale = nullptr;      // sinc form: per-SFT scale of the FP16 coefficients
+    size_t cap_hscale = 0;
     bool tab_sinc = false;          // kind of the built tables
-    float4* d_ptab = nullptr;       // far-field pair table [n_sft][n_pos]
+    float4* d_ptab = nullptr;       // far-field pair table, or the sinc FP16 part [n_sft][n_pos]
     float4* d_pcoef = nullptr;      // far-field coefficients [n_sft][4][n_pos]
     size_t cap_ptab = 0, cap_pcoef = 0;
     int ring_stall = -1;             // testing aid (fstat_test_ring_stall)
@@ -297,6 +299,12 @@ SincGamma sinc_gamma() {
         }
         for (int n = 0; n < N; ++n) G.g[i][n] = (float)(A[n][N] / A[n][n]);
     }
+    G.hbound = 0.f;
+    for (int n = kSincHalf; n <= kSincDeg; ++n) {
+        float b = 0.f;
+        for (int i = 0; i < kSincTerms; ++i) b += std::fabs(G.g[i][n]);
+        G.hbound = std::max(G.hbound, b);
+    }
     return G;
 }
 
@@ -373,10 +381,9 @@ bool make_far_plan(fstat_ctx* c, int P, int L, bool found, Plan& best) {
                 int hf = (w_pairs + 1) / 2;
                 hf += ((4 - hf % 8) + 8) % 8;
                 const int w_tab = 2 * hf;
-                const int rec = want_sinc ? 80 : 48;
                 int S = c->opts.sft_chunk > 0 ? c->opts.sft_chunk : 8;
-                while (S > 3 && ring_smem(S, w_tab, rec).total > 110 * 1024) --S;
-                const size_t smem = ring_smem(S, w_tab, rec).total;
+                while (S > 3 && ring_smem(S, w_tab).total > 110 * 1024) --S;
+                const size_t smem = ring_smem(S, w_tab).total;
                 if (smem > 220 * 1024) continue;
                 double cost = 0.0;
                 int chunks_max = 0;
@@ -774,7 +781,7 @@ void fstat_destroy(fstat_ctx* c) {
                     c->d_fdot, c->d_meta, c->d_kh0, c->d_ph0, c->d_abcd, c->d_comb, c->d_twoF, c->d_err,
                     c->tw.hist, c->tw.state, c->tw.tie_count, c->tw.cand_idx, c->tw.cand_val, c->tw.n_cand,
                     c->tw.out_idx, c->tw.out_val, c->d_inj_work, c->d_sig, c->d_ptab, c->d_pcoef,
-                    c->d_bins_w, c->d_floor, c->d_sbar, c->d_weight};
+                    c->d_bins_w, c->d_floor, c->d_sbar, c->d_weight, c->d_hscale};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (int i = 0; i < kTimedRing; ++i) {
@@ -965,9 +972,11 @@ int prepare(fstat_ctx* c, cudaStream_t s) {
         const size_t n_tab = (size_t)c->n_sft * c->n_pos;
         const void* bins = c->opts.bins_form == FSTAT_BINS_C64 ? (const void*)work_bins(c) : (const void*)c->d_bins16;
         if (c->plan.sinc) {
-            if ((rc = grow(c, &c->d_pcoef, c->cap_pcoef, 5 * n_tab)) != FSTAT_OK) return rc;
-            CUDA_TRY(c, launch_sinc_tables(bins, c->opts.bins_form, c->row, c->n_sft, c->n_bins, c->sgam, c->d_pcoef,
-                                           c->n_pos, c->far_xoff, s));
+            if ((rc = grow(c, &c->d_ptab, c->cap_ptab, n_tab)) != FSTAT_OK) return rc;
+            if ((rc = grow(c, &c->d_pcoef, c->cap_pcoef, 3 * n_tab)) != FSTAT_OK) return rc;
+            if ((rc = grow(c, &c->d_hscale, c->cap_hscale, (size_t)c->n_sft)) != FSTAT_OK) return rc;
+            CUDA_TRY(c, launch_sinc_tables(bins, c->opts.bins_form, c->row, c->n_sft, c->n_bins, c->sgam, c->d_ptab,
+                                           c->d_pcoef, c->d_hscale, c->n_pos, c->far_xoff, s));
         } else {
             if ((rc = grow(c, &c->d_ptab, c->cap_ptab, n_tab)) != FSTAT_OK) return rc;
             if ((rc = grow(c, &c->d_pcoef, c->cap_pcoef, 3 * n_tab)) != FSTAT_OK) return rc;
@@ -1045,6 +1054,7 @@ DirichletParams dirichlet_params(const fstat_ctx* c) {
         dp.pcoef = c->d_pcoef;
         dp.n_pos = c->n_pos;
         dp.xoff = c->far_xoff;
+        dp.hscale = c->d_hscale;
     }
     return dp;
 }

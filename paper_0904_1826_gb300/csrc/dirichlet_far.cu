@@ -105,26 +105,34 @@ __device__ __forceinline__ float2 far_window_sum(const float4* __restrict__ pn, 
 }
 
 // Sinc-polynomial form of one SFT for one thread's M templates: cf is the
-// staged row of 80-byte records (c0..c9 complex, in u = kappa - 1/2),
-// parity-split for L = 2.  P(u) already carries sin(pi kappa)/2, so the
-// template's term is the twiddle times P, with no reciprocal, sine or clamp.
+// staged row of c0..c5 (FP32, 48 bytes per position), ch the row of
+// c6..c9 / hs (FP16, 16 bytes per position), in u = kappa - 1/2, both
+// parity-split for L = 2.  Two planes of 48 and 16 bytes keep the quarter-warp
+// loads on distinct banks where one 64-byte record would not.  P(u) already
+// carries sin(pi kappa)/2, so the template's term is the twiddle times P,
+// with no reciprocal, sine or clamp.
 template <int M, int L>
 __device__ __forceinline__ void sinc_sft(const DirichletParams& p, const SkySftMeta& m, long long kh_row,
-                                         unsigned int ph0, int lo_rel, const float4* __restrict__ cf, int half,
-                                         int j_t, float2 (&fa)[M], float2 (&fb)[M]) {
+                                         unsigned int ph0, int lo_rel, float hs, const float4* __restrict__ ch,
+                                         const float4* __restrict__ cf, int half, int j_t, float2 (&fa)[M],
+                                         float2 (&fb)[M]) {
     constexpr int D = 8;
     const long long kh = kh_row + (long long)j_t * m.dk;
     const int k0 = (int)(kh >> 32);
     const int b = (k0 - (int)p.k_lo) - (D - 1) - lo_rel;
     const float2 a2 = make_float2(m.a, m.a), b2 = make_float2(m.b, m.b);
-    auto poly = [&](const float4* __restrict__ r, float u) -> float2 {
-        const float4 e0 = r[0], e1 = r[1], e2 = r[2], e3 = r[3], e4 = r[4];
+    auto poly = [&](int pos, float u) -> float2 {
+        const float4* r = cf + 3 * pos;
+        const float4 e0 = r[0], e1 = r[1], e2 = r[2];
+        const uint4 eh = *reinterpret_cast<const uint4*>(ch + pos);
         const float2 uu = make_float2(u, u);
-        float2 P = make_float2(e4.z, e4.w);
-        P = __ffma2_rn(P, uu, make_float2(e4.x, e4.y));
-        P = __ffma2_rn(P, uu, make_float2(e3.z, e3.w));
-        P = __ffma2_rn(P, uu, make_float2(e3.x, e3.y));
-        P = __ffma2_rn(P, uu, make_float2(e2.z, e2.w));
+        // high part c6..c9 in units of hs (FP16), then one step rescales it
+        float2 H = __half22float2(*reinterpret_cast<const __half2*>(&eh.w));
+        H = __ffma2_rn(H, uu, __half22float2(*reinterpret_cast<const __half2*>(&eh.z)));
+        H = __ffma2_rn(H, uu, __half22float2(*reinterpret_cast<const __half2*>(&eh.y)));
+        H = __ffma2_rn(H, uu, __half22float2(*reinterpret_cast<const __half2*>(&eh.x)));
+        const float us = u * hs;
+        float2 P = __ffma2_rn(H, make_float2(us, us), make_float2(e2.z, e2.w));
         P = __ffma2_rn(P, uu, make_float2(e2.x, e2.y));
         P = __ffma2_rn(P, uu, make_float2(e1.z, e1.w));
         P = __ffma2_rn(P, uu, make_float2(e1.x, e1.y));
@@ -143,7 +151,7 @@ __device__ __forceinline__ void sinc_sft(const DirichletParams& p, const SkySftM
             atomicOr(p.err, 1);
             bb = max(0, min(bb, p.w_pairs - 1 - (M - 1) * L - 2 * (D - 1)));
         }
-        const float4* cp = cf + 5 * tab_pos<L>(bb + 7, half);
+        const int pos0 = tab_pos<L>(bb + 7, half);
         const unsigned int ph = ph0 + (unsigned int)j_t * m.dphi + ((unsigned int)k0 << 31);
         float sn, cs;
         __sincosf((float)(int)ph * kPhaseToRad, &sn, &cs);
@@ -151,7 +159,7 @@ __device__ __forceinline__ void sinc_sft(const DirichletParams& p, const SkySftM
         const float u0 = frac_to_float((unsigned int)kh) - 0.5f;
 #pragma unroll
         for (int q = 0; q < M; ++q) {
-            add(tw_re, tw_im, poly(cp + 5 * q, fmaf((float)q, m.eps, u0)), fa[q], fb[q]);
+            add(tw_re, tw_im, poly(pos0 + q, fmaf((float)q, m.eps, u0)), fa[q], fb[q]);
             if (q + 1 < M) {
                 const float t = fmaf(tw_re, m.rot_re, -tw_im * m.rot_im);
                 tw_im = fmaf(tw_re, m.rot_im, tw_im * m.rot_re);
@@ -172,15 +180,40 @@ __device__ __forceinline__ void sinc_sft(const DirichletParams& p, const SkySftM
                 atomicOr(p.err, 1);
                 bq = max(0, min(bq, p.w_pairs - 1 - 2 * (D - 1)));
             }
-            add(c2, -s2, poly(cf + 5 * tab_pos<L>(bq + 7, half), frac_to_float((unsigned int)khq) - 0.5f), fa[q],
-                fb[q]);
+            add(c2, -s2, poly(tab_pos<L>(bq + 7, half), frac_to_float((unsigned int)khq) - 0.5f), fa[q], fb[q]);
         }
+    }
+}
+
+// Per SFT, the power of two s with max|Re|, |Im| of the bins * hbound / s <= 2^14,
+// so every FP16 coefficient of the SFT's records stays below 2^14.
+template <int FORM>
+__global__ void __launch_bounds__(256) sinc_scale_kernel(const typename RawT<FORM>::T* __restrict__ bins, long long row,
+                                                         int n_bins, float hbound, float* __restrict__ hscale) {
+    using RT = RawT<FORM>;
+    __shared__ float red[8];
+    const typename RT::T* rp = bins + (size_t)blockIdx.x * row;
+    float mx = 0.f;
+    for (int k = threadIdx.x; k < n_bins; k += blockDim.x) {
+        const float2 v = RT::f2(rp[k]);
+        mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = fmaxf(mx, red[w]);
+        int e = 0;
+        const float need = mx * hbound * (1.0f / 16384.0f);
+        if (need > 0.f) frexpf(need, &e);
+        hscale[blockIdx.x] = need > 0.f ? ldexpf(1.0f, e) : 1.0f;
     }
 }
 
 template <int FORM>
 __global__ void __launch_bounds__(256) sinc_tables_kernel(const typename RawT<FORM>::T* __restrict__ bins,
                                                           long long row, int n_sft, int n_bins, const SincGamma gam,
+                                                          const float* __restrict__ hscale, float4* __restrict__ phigh,
                                                           float4* __restrict__ pcoef, int n_pos, int xoff) {
     using RT = RawT<FORM>;
     const long long total = (long long)n_sft * n_pos;
@@ -204,9 +237,18 @@ __global__ void __launch_bounds__(256) sinc_tables_kernel(const typename RawT<FO
                 ci[n] = fmaf(v.y, gam.g[i][n], ci[n]);
             }
         }
-        float4* cp = pcoef + o * 5;
+        float4* cp = pcoef + o * 3;
 #pragma unroll
-        for (int h = 0; h < 5; ++h) cp[h] = make_float4(cr[2 * h], ci[2 * h], cr[2 * h + 1], ci[2 * h + 1]);
+        for (int h = 0; h < 3; ++h) cp[h] = make_float4(cr[2 * h], ci[2 * h], cr[2 * h + 1], ci[2 * h + 1]);
+        const float inv = 1.0f / hscale[s];   // a power of two: exact
+        uint4 hw;
+        unsigned int* hwp = reinterpret_cast<unsigned int*>(&hw);
+#pragma unroll
+        for (int n = kSincHalf; n <= kSincDeg; ++n) {
+            const __half2 v = __floats2half2_rn(cr[n] * inv, ci[n] * inv);
+            hwp[n - kSincHalf] = *reinterpret_cast<const unsigned int*>(&v);
+        }
+        *reinterpret_cast<uint4*>(phigh + o) = hw;
     }
 }
 
@@ -491,9 +533,8 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
 template <int M, bool SINC>
 __device__ __forceinline__ void far_ring_block(const DirichletParams& p, long long bid, unsigned char* smem) {
     constexpr int D = 8, L = 2;
-    constexpr int REC = SINC ? 80 : 48;   // bytes per coefficient record
     const int S = p.sft_chunk;
-    const RingSmem lay = ring_smem(S, p.w_tab, REC);
+    const RingSmem lay = ring_smem(S, p.w_tab);
     const int NW = (int)(blockDim.x >> 5) - 1;
 
     const int chunk = (int)(bid % p.chunks_per_col);
@@ -544,7 +585,7 @@ __device__ __forceinline__ void far_ring_block(const DirichletParams& p, long lo
         const int nh = p.n_pos >> 1;
         const int half = p.w_tab >> 1;
         const int n0 = (p.w_pairs + 1) >> 1, n1 = p.w_pairs >> 1;
-        const uint32_t bytes = 48u + 32u + (uint32_t)(n0 + n1) * (SINC ? 80u : 64u);
+        const uint32_t bytes = 48u + 32u + (uint32_t)(n0 + n1) * 64u;   // 16 + 48 bytes per position
         int a = 0;
         bool stop = false;
         int pslot = 0;            // slot of SFT a
@@ -552,6 +593,8 @@ __device__ __forceinline__ void far_ring_block(const DirichletParams& p, long lo
         const int n_issue = p.ring_stop >= 0 ? min(p.ring_stop, p.n_sft) : p.n_sft;
         for (int a0 = 0; a0 < n_issue && !stop; a0 += 32) {
             int x_lane = 0;
+            float hs_lane = 1.0f;
+            if (SINC && a0 + lane < n_issue) hs_lane = p.hscale[a0 + lane];
             if (a0 + lane < p.n_sft) {
                 const SkySftMeta* gm = p.meta + meta0 + a0 + lane;
                 x_lane = (int)(((gm->khmin + (long long)j_col0 * gm->dk) >> 32) - p.k_lo) - (D - 1) + p.xoff;
@@ -559,6 +602,7 @@ __device__ __forceinline__ void far_ring_block(const DirichletParams& p, long lo
             const int n_here = min(32, n_issue - a0);
             for (int j = 0; j < n_here; ++j) {
                 int x0 = __shfl_sync(0xffffffffu, x_lane, j);
+                const float hs = __shfl_sync(0xffffffffu, hs_lane, j);
                 if (lane == 0) {
                     a = a0 + j;
                     if (a >= S && !mbar_wait<128>(empty_bar(pslot), pparity)) {
@@ -574,6 +618,7 @@ __device__ __forceinline__ void far_ring_block(const DirichletParams& p, long lo
                         }
                         unsigned char* st = smem + (size_t)pslot * lay.stage;
                         *reinterpret_cast<int*>(st + lay.lo) = x0 - p.xoff;
+                        if (SINC) *reinterpret_cast<float*>(st + lay.lo + 4) = hs;
                         const uint32_t ss = sb + (uint32_t)((size_t)pslot * lay.stage);
                         const uint32_t fb = full_bar(pslot);
                         mbar_expect_tx(fb, bytes);
@@ -583,11 +628,10 @@ __device__ __forceinline__ void far_ring_block(const DirichletParams& p, long lo
                         for (int h = 0; h < 2; ++h) {
                             const int cnt = h ? n1 : n0;
                             const size_t go = (size_t)a * p.n_pos + (size_t)((x0 + h) & 1) * nh + ((x0 + h) >> 1);
-                            if (!SINC)
-                                bulk_g2s(ss + (uint32_t)(lay.pairs + (size_t)h * half * 16), p.ptab + go,
-                                         (uint32_t)cnt * 16u, fb);
-                            bulk_g2s(ss + (uint32_t)(lay.coef + (size_t)h * half * REC),
-                                     p.pcoef + (size_t)(REC / 16) * go, (uint32_t)cnt * REC, fb);
+                            bulk_g2s(ss + (uint32_t)(lay.pairs + (size_t)h * half * 16), p.ptab + go,
+                                     (uint32_t)cnt * 16u, fb);
+                            bulk_g2s(ss + (uint32_t)(lay.coef + (size_t)h * half * 48), p.pcoef + 3 * go,
+                                     (uint32_t)cnt * 48u, fb);
                         }
                         ++a;
                         if (++pslot == S) {   // the next use of slot 0 waits for the phase after this one
@@ -623,7 +667,9 @@ __device__ __forceinline__ void far_ring_block(const DirichletParams& p, long lo
                 const int lo_rel = *reinterpret_cast<const int*>(st + lay.lo);
                 if (SINC)
                     sinc_sft<M, L>(p, m, bs.kh0 + (long long)drow * bs.dkh, bs.ph0 + (unsigned int)drow * bs.dph,
-                                   lo_rel, reinterpret_cast<const float4*>(st + lay.coef), half, j_t, fa, fb);
+                                   lo_rel, *reinterpret_cast<const float*>(st + lay.lo + 4),
+                                   reinterpret_cast<const float4*>(st + lay.pairs),
+                                   reinterpret_cast<const float4*>(st + lay.coef), half, j_t, fa, fb);
                 else
                     far_sft<M, L>(p, m, bs.kh0 + (long long)drow * bs.dkh, bs.ph0 + (unsigned int)drow * bs.dph,
                                   lo_rel, reinterpret_cast<const float4*>(st + lay.pairs),
@@ -788,18 +834,24 @@ cudaError_t dirichlet_far_batch_occupancy(int v, int threads, size_t smem, int* 
 }
 
 cudaError_t launch_sinc_tables(const void* bins, int form, long long row, int n_sft, int n_bins,
-                               const SincGamma& gam, float4* pcoef, int n_pos, int xoff, cudaStream_t s) {
+                               const SincGamma& gam, float4* phigh, float4* pcoef, float* hscale, int n_pos,
+                               int xoff, cudaStream_t s) {
     const long long total = (long long)n_sft * n_pos;
     const int grid = (int)std::min<long long>((total + 255) / 256, 152LL * 16);
-    if (form == FSTAT_BINS_C64)
-        sinc_tables_kernel<FSTAT_BINS_C64><<<grid, 256, 0, s>>>(static_cast<const float2*>(bins), row, n_sft, n_bins,
-                                                                 gam, pcoef, n_pos, xoff);
-    else if (form == FSTAT_BINS_F16)
-        sinc_tables_kernel<FSTAT_BINS_F16><<<grid, 256, 0, s>>>(static_cast<const __half2*>(bins), row, n_sft,
-                                                                 n_bins, gam, pcoef, n_pos, xoff);
-    else
-        sinc_tables_kernel<FSTAT_BINS_BF16><<<grid, 256, 0, s>>>(static_cast<const __nv_bfloat162*>(bins), row, n_sft,
-                                                                  n_bins, gam, pcoef, n_pos, xoff);
+    if (form == FSTAT_BINS_C64) {
+        auto b = static_cast<const float2*>(bins);
+        sinc_scale_kernel<FSTAT_BINS_C64><<<n_sft, 256, 0, s>>>(b, row, n_bins, gam.hbound, hscale);
+        sinc_tables_kernel<FSTAT_BINS_C64><<<grid, 256, 0, s>>>(b, row, n_sft, n_bins, gam, hscale, phigh, pcoef, n_pos, xoff);
+    } else if (form == FSTAT_BINS_F16) {
+        auto b = static_cast<const __half2*>(bins);
+        sinc_scale_kernel<FSTAT_BINS_F16><<<n_sft, 256, 0, s>>>(b, row, n_bins, gam.hbound, hscale);
+        sinc_tables_kernel<FSTAT_BINS_F16><<<grid, 256, 0, s>>>(b, row, n_sft, n_bins, gam, hscale, phigh, pcoef, n_pos, xoff);
+    } else {
+        auto b = static_cast<const __nv_bfloat162*>(bins);
+        sinc_scale_kernel<FSTAT_BINS_BF16><<<n_sft, 256, 0, s>>>(b, row, n_bins, gam.hbound, hscale);
+        sinc_tables_kernel<FSTAT_BINS_BF16><<<grid, 256, 0, s>>>(b, row, n_sft, n_bins, gam, hscale, phigh, pcoef, n_pos,
+                                                                  xoff);
+    }
     return cudaGetLastError();
 }
 

@@ -91,6 +91,7 @@ struct DirichletParams {
     int n_pos;                 // positions per SFT row
     int xoff;                  // position of bin k_lo
     int ring_stop;             // testing aid: the ring's copy warp stops after this many SFTs (< 0: never)
+    const float* hscale;       // sinc form: [n_sft] scale of the FP16 part of the coefficient records
 };
 
 // Far-field polynomial form (D = 8): the window's 12 bins at offsets -7..-2
@@ -111,10 +112,15 @@ __host__ __device__ constexpr int far_offset(int i) { return i < 6 ? i - 7 : i -
 // is entire in kappa (sin vanishes at every integer), so it is replaced by
 // its degree-9 interpolant in u = kappa - 1/2, sum_n c_n u^n, with
 // c_n = sum_k X_{k0+k} gamma[k][n]; no reciprocal, sine or clamp remains.
+// Per (SFT, position) the tables hold c0..c5 in FP32 (48 bytes, in the
+// coefficient table) and c6..c9 / s in FP16 (16 bytes, in the pair table's
+// place), s a power of two per SFT with max |c_n| / s <= 2^14 (n >= 6).
 constexpr int kSincDeg = 9;
 constexpr int kSincTerms = 16;
+constexpr int kSincHalf = 6;             // first coefficient stored in FP16
 struct SincGamma {
     float g[kSincTerms][kSincDeg + 1];   // [offset k + 7][power]
+    float hbound;                        // max over n >= 6 of sum_k |gamma[k][n]|
 };
 
 // Shared-memory layout of the far-field kernel (offsets in bytes).
@@ -162,13 +168,13 @@ __host__ __device__ inline PolySmem farpoly_smem(int sft_chunk, int w_tab, int n
 struct RingSmem {
     size_t stage, pairs, coef, meta, base, lo, bars, ctrl, total;
 };
-// rec = bytes per coefficient record (48 far-field, 80 sinc); the sinc form
-// stages no pair table.
-__host__ __device__ inline RingSmem ring_smem(int stages, int w_tab, int rec = 48) {
+// Both forms stage 16 + 48 bytes per position (far field: pair table and
+// degree-5 coefficients; sinc: FP16 and FP32 parts of the coefficients).
+__host__ __device__ inline RingSmem ring_smem(int stages, int w_tab) {
     RingSmem r;
     r.pairs = 0;
-    r.coef = rec == 48 ? (size_t)w_tab * 16 : 0;
-    r.meta = r.coef + (size_t)w_tab * rec;
+    r.coef = (size_t)w_tab * 16;
+    r.meta = r.coef + (size_t)w_tab * 48;
     r.base = r.meta + 48;
     r.lo = r.base + 32;
     r.stage = (r.lo + 16 + 127) & ~(size_t)127;
@@ -243,7 +249,8 @@ struct TopkWork {
 cudaError_t launch_far_tables(const void* bins, int form, long long row, int n_sft, int n_bins, const FarGamma& gam,
                               float4* ptab, float4* pcoef, int n_pos, int xoff, cudaStream_t s);
 cudaError_t launch_sinc_tables(const void* bins, int form, long long row, int n_sft, int n_bins,
-                               const SincGamma& gam, float4* pcoef, int n_pos, int xoff, cudaStream_t s);
+                               const SincGamma& gam, float4* phigh, float4* pcoef, float* hscale, int n_pos,
+                               int xoff, cudaStream_t s);
 cudaError_t launch_dirichlet_far(int v, const DirichletParams& p, int threads, size_t smem, long long grid,
                                  cudaStream_t s);
 cudaError_t launch_dirichlet_far_batch(int v, const DirichletBatch& b, int threads, size_t smem, int grid,
