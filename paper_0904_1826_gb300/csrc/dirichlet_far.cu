@@ -126,11 +126,14 @@ __device__ __forceinline__ void sinc_sft(const DirichletParams& p, const SkySftM
         const float4 e0 = r[0], e1 = r[1], e2 = r[2];
         const uint4 eh = *reinterpret_cast<const uint4*>(ch + pos);
         const float2 uu = make_float2(u, u);
-        // high part c6..c9 in units of hs (FP16), then one step rescales it
-        float2 H = __half22float2(*reinterpret_cast<const __half2*>(&eh.w));
-        H = __ffma2_rn(H, uu, __half22float2(*reinterpret_cast<const __half2*>(&eh.z)));
-        H = __ffma2_rn(H, uu, __half22float2(*reinterpret_cast<const __half2*>(&eh.y)));
-        H = __ffma2_rn(H, uu, __half22float2(*reinterpret_cast<const __half2*>(&eh.x)));
+        // high part c6..c9 in units of hs, by Horner in FP16 (|u| <= 1/2 and
+        // |c_n| / hs <= 2^14 keep every step below 2^15), then one step
+        // rescales it into the FP32 part
+        const __half2 uh = __float2half2_rn(u);
+        __half2 Hh = __hfma2(*reinterpret_cast<const __half2*>(&eh.w), uh, *reinterpret_cast<const __half2*>(&eh.z));
+        Hh = __hfma2(Hh, uh, *reinterpret_cast<const __half2*>(&eh.y));
+        Hh = __hfma2(Hh, uh, *reinterpret_cast<const __half2*>(&eh.x));
+        const float2 H = __half22float2(Hh);
         const float us = u * hs;
         float2 P = __ffma2_rn(H, make_float2(us, us), make_float2(e2.z, e2.w));
         P = __ffma2_rn(P, uu, make_float2(e2.x, e2.y));
