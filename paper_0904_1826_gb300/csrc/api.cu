@@ -103,10 +103,8 @@ struct fstat_ctx {
     bool tab_dirty = true;          // far-field tables need a rebuild
     FarGamma gam{};                 // far-field interpolation weights
     SincGamma sgam{};               // sinc-polynomial interpolation weights
-    float* d_hscale = nullptr;      // sinc form: per-SFT scale of the FP16 coefficients
-    size_t cap_hscale = 0;
     bool tab_sinc = false;          // kind of the built tables
-    float4* d_ptab = nullptr;       // far-field pair table, or the sinc FP16 part [n_sft][n_pos]
+    float4* d_ptab = nullptr;       // far-field pair table [n_sft][n_pos]
     float4* d_pcoef = nullptr;      // far-field coefficients [n_sft][4][n_pos]
     size_t cap_ptab = 0, cap_pcoef = 0;
     int ring_stall = -1;             // testing aid (fstat_test_ring_stall)
@@ -273,37 +271,34 @@ FarGamma far_gamma() {
 SincGamma sinc_gamma() {
     SincGamma G{};
     constexpr int N = kSincDeg + 1;
-    for (int i = 0; i < kSincTerms; ++i) {
-        const double k = i - 7;
-        double A[N][N + 1];
-        for (int j = 0; j < N; ++j) {
-            const double u = 0.5 * std::cos((2.0 * j + 1.0) * kPi / (2.0 * N));
-            const double kap = u + 0.5;
-            double pw = 1.0;
-            for (int n = 0; n < N; ++n) {
-                A[j][n] = pw;
-                pw *= u;
+    for (int h = 0; h < 2; ++h) {
+        const double centre = 0.25 + 0.5 * h;
+        for (int i = 0; i < kSincTerms; ++i) {
+            const double k = i - 7;
+            double A[N][N + 1];
+            for (int j = 0; j < N; ++j) {
+                const double v = 0.25 * std::cos((2.0 * j + 1.0) * kPi / (2.0 * N));
+                const double kap = centre + v;
+                double pw = 1.0;
+                for (int n = 0; n < N; ++n) {
+                    A[j][n] = pw;
+                    pw *= v;
+                }
+                A[j][N] = std::sin(kPi * kap) / (2.0 * (kap - k));
             }
-            A[j][N] = std::sin(kPi * kap) / (2.0 * (kap - k));
-        }
-        for (int col = 0; col < N; ++col) {
-            int piv = col;
-            for (int r = col + 1; r < N; ++r)
-                if (std::fabs(A[r][col]) > std::fabs(A[piv][col])) piv = r;
-            for (int t = 0; t <= N; ++t) std::swap(A[col][t], A[piv][t]);
-            for (int r = 0; r < N; ++r) {
-                if (r == col) continue;
-                const double f = A[r][col] / A[col][col];
-                for (int t = col; t <= N; ++t) A[r][t] -= f * A[col][t];
+            for (int col = 0; col < N; ++col) {
+                int piv = col;
+                for (int r = col + 1; r < N; ++r)
+                    if (std::fabs(A[r][col]) > std::fabs(A[piv][col])) piv = r;
+                for (int t = 0; t <= N; ++t) std::swap(A[col][t], A[piv][t]);
+                for (int r = 0; r < N; ++r) {
+                    if (r == col) continue;
+                    const double f = A[r][col] / A[col][col];
+                    for (int t = col; t <= N; ++t) A[r][t] -= f * A[col][t];
+                }
             }
+            for (int n = 0; n < N; ++n) G.g[h][i][n] = (float)(A[n][N] / A[n][n]);
         }
-        for (int n = 0; n < N; ++n) G.g[i][n] = (float)(A[n][N] / A[n][n]);
-    }
-    G.hbound = 0.f;
-    for (int n = kSincHalf; n <= kSincDeg; ++n) {
-        float b = 0.f;
-        for (int i = 0; i < kSincTerms; ++i) b += std::fabs(G.g[i][n]);
-        G.hbound = std::max(G.hbound, b);
     }
     return G;
 }
@@ -382,8 +377,8 @@ bool make_far_plan(fstat_ctx* c, int P, int L, bool found, Plan& best) {
                 hf += ((4 - hf % 8) + 8) % 8;
                 const int w_tab = 2 * hf;
                 int S = c->opts.sft_chunk > 0 ? c->opts.sft_chunk : 8;
-                while (S > 3 && ring_smem(S, w_tab).total > 110 * 1024) --S;
-                const size_t smem = ring_smem(S, w_tab).total;
+                while (S > 3 && ring_smem(S, w_tab, want_sinc).total > 110 * 1024) --S;
+                const size_t smem = ring_smem(S, w_tab, want_sinc).total;
                 if (smem > 220 * 1024) continue;
                 double cost = 0.0;
                 int chunks_max = 0;
@@ -781,7 +776,7 @@ void fstat_destroy(fstat_ctx* c) {
                     c->d_fdot, c->d_meta, c->d_kh0, c->d_ph0, c->d_abcd, c->d_comb, c->d_twoF, c->d_err,
                     c->tw.hist, c->tw.state, c->tw.tie_count, c->tw.cand_idx, c->tw.cand_val, c->tw.n_cand,
                     c->tw.out_idx, c->tw.out_val, c->d_inj_work, c->d_sig, c->d_ptab, c->d_pcoef,
-                    c->d_bins_w, c->d_floor, c->d_sbar, c->d_weight, c->d_hscale};
+                    c->d_bins_w, c->d_floor, c->d_sbar, c->d_weight};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (int i = 0; i < kTimedRing; ++i) {
@@ -972,11 +967,9 @@ int prepare(fstat_ctx* c, cudaStream_t s) {
         const size_t n_tab = (size_t)c->n_sft * c->n_pos;
         const void* bins = c->opts.bins_form == FSTAT_BINS_C64 ? (const void*)work_bins(c) : (const void*)c->d_bins16;
         if (c->plan.sinc) {
-            if ((rc = grow(c, &c->d_ptab, c->cap_ptab, n_tab)) != FSTAT_OK) return rc;
-            if ((rc = grow(c, &c->d_pcoef, c->cap_pcoef, 3 * n_tab)) != FSTAT_OK) return rc;
-            if ((rc = grow(c, &c->d_hscale, c->cap_hscale, (size_t)c->n_sft)) != FSTAT_OK) return rc;
-            CUDA_TRY(c, launch_sinc_tables(bins, c->opts.bins_form, c->row, c->n_sft, c->n_bins, c->sgam, c->d_ptab,
-                                           c->d_pcoef, c->d_hscale, c->n_pos, c->far_xoff, s));
+            if ((rc = grow(c, &c->d_pcoef, c->cap_pcoef, 6 * n_tab)) != FSTAT_OK) return rc;
+            CUDA_TRY(c, launch_sinc_tables(bins, c->opts.bins_form, c->row, c->n_sft, c->n_bins, c->sgam, c->d_pcoef,
+                                           c->n_pos, c->far_xoff, s));
         } else {
             if ((rc = grow(c, &c->d_ptab, c->cap_ptab, n_tab)) != FSTAT_OK) return rc;
             if ((rc = grow(c, &c->d_pcoef, c->cap_pcoef, 3 * n_tab)) != FSTAT_OK) return rc;
@@ -1054,7 +1047,6 @@ DirichletParams dirichlet_params(const fstat_ctx* c) {
         dp.pcoef = c->d_pcoef;
         dp.n_pos = c->n_pos;
         dp.xoff = c->far_xoff;
-        dp.hscale = c->d_hscale;
     }
     return dp;
 }

@@ -105,42 +105,31 @@ __device__ __forceinline__ float2 far_window_sum(const float4* __restrict__ pn, 
 }
 
 // Sinc-polynomial form of one SFT for one thread's M templates: cf is the
-// staged row of c0..c5 (FP32, 48 bytes per position), ch the row of
-// c6..c9 / hs (FP16, 16 bytes per position), in u = kappa - 1/2, both
-// parity-split for L = 2.  Two planes of 48 and 16 bytes keep the quarter-warp
-// loads on distinct banks where one 64-byte record would not.  P(u) already
-// carries sin(pi kappa)/2, so the template's term is the twiddle times P,
-// with no reciprocal, sine or clamp.
+// staged row of 48-byte records c_{0..5} (FP32) of the half bin kappa < 1/2,
+// cf + plane4 that of the half kappa >= 1/2, both parity-split for L = 2.
+// P already carries sin(pi kappa)/2, so the template's term is the twiddle
+// times P, with no reciprocal, sine or clamp.
 template <int M, int L>
 __device__ __forceinline__ void sinc_sft(const DirichletParams& p, const SkySftMeta& m, long long kh_row,
-                                         unsigned int ph0, int lo_rel, float hs, const float4* __restrict__ ch,
-                                         const float4* __restrict__ cf, int half, int j_t, float2 (&fa)[M],
-                                         float2 (&fb)[M]) {
+                                         unsigned int ph0, int lo_rel, const float4* __restrict__ cf, int plane4,
+                                         int half, int j_t, float2 (&fa)[M], float2 (&fb)[M]) {
     constexpr int D = 8;
     const long long kh = kh_row + (long long)j_t * m.dk;
     const int k0 = (int)(kh >> 32);
     const int b = (k0 - (int)p.k_lo) - (D - 1) - lo_rel;
     const float2 a2 = make_float2(m.a, m.a), b2 = make_float2(m.b, m.b);
+    // u = kappa - 1/2; the half bin is u >= 0, v = u -+ 1/4 its local variable
     auto poly = [&](int pos, float u) -> float2 {
-        const float4* r = cf + 3 * pos;
+        const bool up = u >= 0.f;
+        const float v = u + (up ? -0.25f : 0.25f);
+        const float4* r = cf + (up ? plane4 : 0) + 3 * pos;
         const float4 e0 = r[0], e1 = r[1], e2 = r[2];
-        const uint4 eh = *reinterpret_cast<const uint4*>(ch + pos);
-        const float2 uu = make_float2(u, u);
-        // high part c6..c9 in units of hs, by Horner in FP16 (|u| <= 1/2 and
-        // |c_n| / hs <= 2^14 keep every step below 2^15), then one step
-        // rescales it into the FP32 part
-        const __half2 uh = __float2half2_rn(u);
-        __half2 Hh = __hfma2(*reinterpret_cast<const __half2*>(&eh.w), uh, *reinterpret_cast<const __half2*>(&eh.z));
-        Hh = __hfma2(Hh, uh, *reinterpret_cast<const __half2*>(&eh.y));
-        Hh = __hfma2(Hh, uh, *reinterpret_cast<const __half2*>(&eh.x));
-        const float2 H = __half22float2(Hh);
-        const float us = u * hs;
-        float2 P = __ffma2_rn(H, make_float2(us, us), make_float2(e2.z, e2.w));
-        P = __ffma2_rn(P, uu, make_float2(e2.x, e2.y));
-        P = __ffma2_rn(P, uu, make_float2(e1.z, e1.w));
-        P = __ffma2_rn(P, uu, make_float2(e1.x, e1.y));
-        P = __ffma2_rn(P, uu, make_float2(e0.z, e0.w));
-        return __ffma2_rn(P, uu, make_float2(e0.x, e0.y));
+        const float2 vv = make_float2(v, v);
+        float2 P = __ffma2_rn(make_float2(e2.z, e2.w), vv, make_float2(e2.x, e2.y));
+        P = __ffma2_rn(P, vv, make_float2(e1.z, e1.w));
+        P = __ffma2_rn(P, vv, make_float2(e1.x, e1.y));
+        P = __ffma2_rn(P, vv, make_float2(e0.z, e0.w));
+        return __ffma2_rn(P, vv, make_float2(e0.x, e0.y));
     };
     auto add = [&](float tw_re, float tw_im, float2 P, float2& fa_q, float2& fb_q) {
         const float2 z = make_float2(fmaf(tw_re, P.x, -tw_im * P.y), fmaf(tw_re, P.y, tw_im * P.x));
@@ -188,35 +177,12 @@ __device__ __forceinline__ void sinc_sft(const DirichletParams& p, const SkySftM
     }
 }
 
-// Per SFT, the power of two s with max|Re|, |Im| of the bins * hbound / s <= 2^14,
-// so every FP16 coefficient of the SFT's records stays below 2^14.
-template <int FORM>
-__global__ void __launch_bounds__(256) sinc_scale_kernel(const typename RawT<FORM>::T* __restrict__ bins, long long row,
-                                                         int n_bins, float hbound, float* __restrict__ hscale) {
-    using RT = RawT<FORM>;
-    __shared__ float red[8];
-    const typename RT::T* rp = bins + (size_t)blockIdx.x * row;
-    float mx = 0.f;
-    for (int k = threadIdx.x; k < n_bins; k += blockDim.x) {
-        const float2 v = RT::f2(rp[k]);
-        mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
-    }
-    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = fmaxf(mx, red[w]);
-        int e = 0;
-        const float need = mx * hbound * (1.0f / 16384.0f);
-        if (need > 0.f) frexpf(need, &e);
-        hscale[blockIdx.x] = need > 0.f ? ldexpf(1.0f, e) : 1.0f;
-    }
-}
-
+// Sinc tables: per (SFT, position x) and half bin h, the six complex
+// coefficients c_{h,n} = sum_k X_{x - xoff + k} gamma[h][k + 7][n] (bins outside
+// the band count as zero), stored at [SFT][h][parity-split position].
 template <int FORM>
 __global__ void __launch_bounds__(256) sinc_tables_kernel(const typename RawT<FORM>::T* __restrict__ bins,
                                                           long long row, int n_sft, int n_bins, const SincGamma gam,
-                                                          const float* __restrict__ hscale, float4* __restrict__ phigh,
                                                           float4* __restrict__ pcoef, int n_pos, int xoff) {
     using RT = RawT<FORM>;
     const long long total = (long long)n_sft * n_pos;
@@ -225,33 +191,30 @@ __global__ void __launch_bounds__(256) sinc_tables_kernel(const typename RawT<FO
         const int s = (int)(t / n_pos);
         const int x = (int)(t - (long long)s * n_pos);
         const int r = x - xoff;
-        const size_t o = (size_t)s * n_pos + (size_t)(x & 1) * (n_pos >> 1) + (x >> 1);   // parity-split slot
+        const size_t slot = (size_t)(x & 1) * (n_pos >> 1) + (x >> 1);   // parity-split position
         const typename RT::T* rp = bins + (size_t)s * row;
-        float cr[kSincDeg + 1], ci[kSincDeg + 1];
-#pragma unroll
-        for (int n = 0; n <= kSincDeg; ++n) cr[n] = ci[n] = 0.f;
+        float2 v[kSincTerms];
 #pragma unroll
         for (int i = 0; i < kSincTerms; ++i) {
             const int j = r + i - 7;
-            const float2 v = (j >= 0 && j < n_bins) ? RT::f2(rp[j]) : make_float2(0.f, 0.f);
-#pragma unroll
-            for (int n = 0; n <= kSincDeg; ++n) {
-                cr[n] = fmaf(v.x, gam.g[i][n], cr[n]);
-                ci[n] = fmaf(v.y, gam.g[i][n], ci[n]);
-            }
+            v[i] = (j >= 0 && j < n_bins) ? RT::f2(rp[j]) : make_float2(0.f, 0.f);
         }
-        float4* cp = pcoef + o * 3;
 #pragma unroll
-        for (int h = 0; h < 3; ++h) cp[h] = make_float4(cr[2 * h], ci[2 * h], cr[2 * h + 1], ci[2 * h + 1]);
-        const float inv = 1.0f / hscale[s];   // a power of two: exact
-        uint4 hw;
-        unsigned int* hwp = reinterpret_cast<unsigned int*>(&hw);
+        for (int h = 0; h < 2; ++h) {
+            float cr[kSincDeg + 1], ci[kSincDeg + 1];
 #pragma unroll
-        for (int n = kSincHalf; n <= kSincDeg; ++n) {
-            const __half2 v = __floats2half2_rn(cr[n] * inv, ci[n] * inv);
-            hwp[n - kSincHalf] = *reinterpret_cast<const unsigned int*>(&v);
+            for (int n = 0; n <= kSincDeg; ++n) cr[n] = ci[n] = 0.f;
+#pragma unroll
+            for (int i = 0; i < kSincTerms; ++i)
+#pragma unroll
+                for (int n = 0; n <= kSincDeg; ++n) {
+                    cr[n] = fmaf(v[i].x, gam.g[h][i][n], cr[n]);
+                    ci[n] = fmaf(v[i].y, gam.g[h][i][n], ci[n]);
+                }
+            float4* cp = pcoef + 3 * (((size_t)s * 2 + h) * n_pos + slot);
+#pragma unroll
+            for (int e = 0; e < 3; ++e) cp[e] = make_float4(cr[2 * e], ci[2 * e], cr[2 * e + 1], ci[2 * e + 1]);
         }
-        *reinterpret_cast<uint4*>(phigh + o) = hw;
     }
 }
 
@@ -537,7 +500,7 @@ template <int M, bool SINC>
 __device__ __forceinline__ void far_ring_block(const DirichletParams& p, long long bid, unsigned char* smem) {
     constexpr int D = 8, L = 2;
     const int S = p.sft_chunk;
-    const RingSmem lay = ring_smem(S, p.w_tab);
+    const RingSmem lay = ring_smem(S, p.w_tab, SINC);
     const int NW = (int)(blockDim.x >> 5) - 1;
 
     const int chunk = (int)(bid % p.chunks_per_col);
@@ -588,7 +551,8 @@ __device__ __forceinline__ void far_ring_block(const DirichletParams& p, long lo
         const int nh = p.n_pos >> 1;
         const int half = p.w_tab >> 1;
         const int n0 = (p.w_pairs + 1) >> 1, n1 = p.w_pairs >> 1;
-        const uint32_t bytes = 48u + 32u + (uint32_t)(n0 + n1) * 64u;   // 16 + 48 bytes per position
+        // per position 16 + 48 bytes (far field) or 2 x 48 bytes (sinc)
+        const uint32_t bytes = 48u + 32u + (uint32_t)(n0 + n1) * (SINC ? 96u : 64u);
         int a = 0;
         bool stop = false;
         int pslot = 0;            // slot of SFT a
@@ -596,8 +560,6 @@ __device__ __forceinline__ void far_ring_block(const DirichletParams& p, long lo
         const int n_issue = p.ring_stop >= 0 ? min(p.ring_stop, p.n_sft) : p.n_sft;
         for (int a0 = 0; a0 < n_issue && !stop; a0 += 32) {
             int x_lane = 0;
-            float hs_lane = 1.0f;
-            if (SINC && a0 + lane < n_issue) hs_lane = p.hscale[a0 + lane];
             if (a0 + lane < p.n_sft) {
                 const SkySftMeta* gm = p.meta + meta0 + a0 + lane;
                 x_lane = (int)(((gm->khmin + (long long)j_col0 * gm->dk) >> 32) - p.k_lo) - (D - 1) + p.xoff;
@@ -605,7 +567,6 @@ __device__ __forceinline__ void far_ring_block(const DirichletParams& p, long lo
             const int n_here = min(32, n_issue - a0);
             for (int j = 0; j < n_here; ++j) {
                 int x0 = __shfl_sync(0xffffffffu, x_lane, j);
-                const float hs = __shfl_sync(0xffffffffu, hs_lane, j);
                 if (lane == 0) {
                     a = a0 + j;
                     if (a >= S && !mbar_wait<128>(empty_bar(pslot), pparity)) {
@@ -621,7 +582,6 @@ __device__ __forceinline__ void far_ring_block(const DirichletParams& p, long lo
                         }
                         unsigned char* st = smem + (size_t)pslot * lay.stage;
                         *reinterpret_cast<int*>(st + lay.lo) = x0 - p.xoff;
-                        if (SINC) *reinterpret_cast<float*>(st + lay.lo + 4) = hs;
                         const uint32_t ss = sb + (uint32_t)((size_t)pslot * lay.stage);
                         const uint32_t fb = full_bar(pslot);
                         mbar_expect_tx(fb, bytes);
@@ -631,10 +591,19 @@ __device__ __forceinline__ void far_ring_block(const DirichletParams& p, long lo
                         for (int h = 0; h < 2; ++h) {
                             const int cnt = h ? n1 : n0;
                             const size_t go = (size_t)a * p.n_pos + (size_t)((x0 + h) & 1) * nh + ((x0 + h) >> 1);
-                            bulk_g2s(ss + (uint32_t)(lay.pairs + (size_t)h * half * 16), p.ptab + go,
-                                     (uint32_t)cnt * 16u, fb);
-                            bulk_g2s(ss + (uint32_t)(lay.coef + (size_t)h * half * 48), p.pcoef + 3 * go,
-                                     (uint32_t)cnt * 48u, fb);
+                            if (SINC) {
+                                const size_t gx = go - (size_t)a * p.n_pos;   // position within the SFT's row
+#pragma unroll
+                                for (int hb = 0; hb < 2; ++hb)
+                                    bulk_g2s(ss + (uint32_t)(hb * lay.plane + (size_t)h * half * 48),
+                                             p.pcoef + 3 * (((size_t)a * 2 + hb) * p.n_pos + gx),
+                                             (uint32_t)cnt * 48u, fb);
+                            } else {
+                                bulk_g2s(ss + (uint32_t)(lay.pairs + (size_t)h * half * 16), p.ptab + go,
+                                         (uint32_t)cnt * 16u, fb);
+                                bulk_g2s(ss + (uint32_t)(lay.coef + (size_t)h * half * 48), p.pcoef + 3 * go,
+                                         (uint32_t)cnt * 48u, fb);
+                            }
                         }
                         ++a;
                         if (++pslot == S) {   // the next use of slot 0 waits for the phase after this one
@@ -670,9 +639,8 @@ __device__ __forceinline__ void far_ring_block(const DirichletParams& p, long lo
                 const int lo_rel = *reinterpret_cast<const int*>(st + lay.lo);
                 if (SINC)
                     sinc_sft<M, L>(p, m, bs.kh0 + (long long)drow * bs.dkh, bs.ph0 + (unsigned int)drow * bs.dph,
-                                   lo_rel, *reinterpret_cast<const float*>(st + lay.lo + 4),
-                                   reinterpret_cast<const float4*>(st + lay.pairs),
-                                   reinterpret_cast<const float4*>(st + lay.coef), half, j_t, fa, fb);
+                                   lo_rel, reinterpret_cast<const float4*>(st + lay.coef), (int)(lay.plane >> 4), half,
+                                   j_t, fa, fb);
                 else
                     far_sft<M, L>(p, m, bs.kh0 + (long long)drow * bs.dkh, bs.ph0 + (unsigned int)drow * bs.dph,
                                   lo_rel, reinterpret_cast<const float4*>(st + lay.pairs),
@@ -837,24 +805,18 @@ cudaError_t dirichlet_far_batch_occupancy(int v, int threads, size_t smem, int* 
 }
 
 cudaError_t launch_sinc_tables(const void* bins, int form, long long row, int n_sft, int n_bins,
-                               const SincGamma& gam, float4* phigh, float4* pcoef, float* hscale, int n_pos,
-                               int xoff, cudaStream_t s) {
+                               const SincGamma& gam, float4* pcoef, int n_pos, int xoff, cudaStream_t s) {
     const long long total = (long long)n_sft * n_pos;
     const int grid = (int)std::min<long long>((total + 255) / 256, 152LL * 16);
-    if (form == FSTAT_BINS_C64) {
-        auto b = static_cast<const float2*>(bins);
-        sinc_scale_kernel<FSTAT_BINS_C64><<<n_sft, 256, 0, s>>>(b, row, n_bins, gam.hbound, hscale);
-        sinc_tables_kernel<FSTAT_BINS_C64><<<grid, 256, 0, s>>>(b, row, n_sft, n_bins, gam, hscale, phigh, pcoef, n_pos, xoff);
-    } else if (form == FSTAT_BINS_F16) {
-        auto b = static_cast<const __half2*>(bins);
-        sinc_scale_kernel<FSTAT_BINS_F16><<<n_sft, 256, 0, s>>>(b, row, n_bins, gam.hbound, hscale);
-        sinc_tables_kernel<FSTAT_BINS_F16><<<grid, 256, 0, s>>>(b, row, n_sft, n_bins, gam, hscale, phigh, pcoef, n_pos, xoff);
-    } else {
-        auto b = static_cast<const __nv_bfloat162*>(bins);
-        sinc_scale_kernel<FSTAT_BINS_BF16><<<n_sft, 256, 0, s>>>(b, row, n_bins, gam.hbound, hscale);
-        sinc_tables_kernel<FSTAT_BINS_BF16><<<grid, 256, 0, s>>>(b, row, n_sft, n_bins, gam, hscale, phigh, pcoef, n_pos,
-                                                                  xoff);
-    }
+    if (form == FSTAT_BINS_C64)
+        sinc_tables_kernel<FSTAT_BINS_C64><<<grid, 256, 0, s>>>(static_cast<const float2*>(bins), row, n_sft, n_bins,
+                                                                 gam, pcoef, n_pos, xoff);
+    else if (form == FSTAT_BINS_F16)
+        sinc_tables_kernel<FSTAT_BINS_F16><<<grid, 256, 0, s>>>(static_cast<const __half2*>(bins), row, n_sft,
+                                                                 n_bins, gam, pcoef, n_pos, xoff);
+    else
+        sinc_tables_kernel<FSTAT_BINS_BF16><<<grid, 256, 0, s>>>(static_cast<const __nv_bfloat162*>(bins), row, n_sft,
+                                                                  n_bins, gam, pcoef, n_pos, xoff);
     return cudaGetLastError();
 }
 

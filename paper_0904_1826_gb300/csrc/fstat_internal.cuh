@@ -91,7 +91,6 @@ struct DirichletParams {
     int n_pos;                 // positions per SFT row
     int xoff;                  // position of bin k_lo
     int ring_stop;             // testing aid: the ring's copy warp stops after this many SFTs (< 0: never)
-    const float* hscale;       // sinc form: [n_sft] scale of the FP16 part of the coefficient records
 };
 
 // Far-field polynomial form (D = 8): the window's 12 bins at offsets -7..-2
@@ -109,18 +108,16 @@ __host__ __device__ constexpr int far_offset(int i) { return i < 6 ? i - 7 : i -
 
 // Sinc-polynomial form (D = 8): the whole window term
 //   P(kappa) = (sin(pi kappa) / 2) sum_{k=-7..8} X_{k0+k} / (kappa - k)
-// is entire in kappa (sin vanishes at every integer), so it is replaced by
-// its degree-9 interpolant in u = kappa - 1/2, sum_n c_n u^n, with
-// c_n = sum_k X_{k0+k} gamma[k][n]; no reciprocal, sine or clamp remains.
-// Per (SFT, position) the tables hold c0..c5 in FP32 (48 bytes, in the
-// coefficient table) and c6..c9 / s in FP16 (16 bytes, in the pair table's
-// place), s a power of two per SFT with max |c_n| / s <= 2^14 (n >= 6).
-constexpr int kSincDeg = 9;
+// is entire in kappa (sin vanishes at every integer), so on each half of the
+// bin, kappa in [0, 1/2) (h = 0) and [1/2, 1) (h = 1), it is replaced by its
+// degree-5 interpolant in v = kappa - 1/4 - h/2 (|v| <= 1/4),
+// sum_n c_{h,n} v^n with c_{h,n} = sum_k X_{k0+k} gamma[h][k][n]; no
+// reciprocal, sine or clamp remains.  One 48-byte record per (SFT, position,
+// half) holds c_{h,0..5} in FP32.
+constexpr int kSincDeg = 5;
 constexpr int kSincTerms = 16;
-constexpr int kSincHalf = 6;             // first coefficient stored in FP16
 struct SincGamma {
-    float g[kSincTerms][kSincDeg + 1];   // [offset k + 7][power]
-    float hbound;                        // max over n >= 6 of sum_k |gamma[k][n]|
+    float g[2][kSincTerms][kSincDeg + 1];   // [half][offset k + 7][power]
 };
 
 // Shared-memory layout of the far-field kernel (offsets in bytes).
@@ -161,20 +158,24 @@ __host__ __device__ inline PolySmem farpoly_smem(int sft_chunk, int w_tab, int n
     return m;
 }
 
-// Shared-memory layout of the far-field ring kernel: S stages of
-// [pairs w_tab x 16 B][coefficient records w_tab x 48 B][meta 48 B][base 32 B]
+// Shared-memory layout of the ring kernel: S stages of
+// [pairs w_tab x 16 B][coefficient records w_tab x 48 B] (far field) or
+// [half-bin plane 0][half-bin plane 1] (sinc), then [meta 48 B][base 32 B]
 // [window base 16 B] (128-byte aligned), then a full and an empty mbarrier
 // per stage, then two control words (stages issued, abort).
 struct RingSmem {
-    size_t stage, pairs, coef, meta, base, lo, bars, ctrl, total;
+    size_t stage, pairs, coef, plane, meta, base, lo, bars, ctrl, total;
 };
-// Both forms stage 16 + 48 bytes per position (far field: pair table and
-// degree-5 coefficients; sinc: FP16 and FP32 parts of the coefficients).
-__host__ __device__ inline RingSmem ring_smem(int stages, int w_tab) {
+// The far-field form stages a 16-byte pair and a 48-byte coefficient record
+// per position; the sinc form two 48-byte records (one per half bin) in two
+// planes whose distance is a multiple of 128 bytes, so that the half a
+// template picks does not change its shared-memory bank.
+__host__ __device__ inline RingSmem ring_smem(int stages, int w_tab, bool sinc = false) {
     RingSmem r;
     r.pairs = 0;
-    r.coef = (size_t)w_tab * 16;
-    r.meta = r.coef + (size_t)w_tab * 48;
+    r.plane = ((size_t)w_tab * 48 + 127) & ~(size_t)127;
+    r.coef = sinc ? 0 : (size_t)w_tab * 16;
+    r.meta = sinc ? 2 * r.plane : r.coef + (size_t)w_tab * 48;
     r.base = r.meta + 48;
     r.lo = r.base + 32;
     r.stage = (r.lo + 16 + 127) & ~(size_t)127;
@@ -249,8 +250,7 @@ struct TopkWork {
 cudaError_t launch_far_tables(const void* bins, int form, long long row, int n_sft, int n_bins, const FarGamma& gam,
                               float4* ptab, float4* pcoef, int n_pos, int xoff, cudaStream_t s);
 cudaError_t launch_sinc_tables(const void* bins, int form, long long row, int n_sft, int n_bins,
-                               const SincGamma& gam, float4* phigh, float4* pcoef, float* hscale, int n_pos,
-                               int xoff, cudaStream_t s);
+                               const SincGamma& gam, float4* pcoef, int n_pos, int xoff, cudaStream_t s);
 cudaError_t launch_dirichlet_far(int v, const DirichletParams& p, int threads, size_t smem, long long grid,
                                  cudaStream_t s);
 cudaError_t launch_dirichlet_far_batch(int v, const DirichletBatch& b, int threads, size_t smem, int grid,
