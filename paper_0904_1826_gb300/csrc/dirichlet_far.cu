@@ -119,10 +119,7 @@ __device__ __forceinline__ void sinc_sft(const DirichletParams& p, const SkySftM
     const int b = (k0 - (int)p.k_lo) - (D - 1) - lo_rel;
     const float2 a2 = make_float2(m.a, m.a), b2 = make_float2(m.b, m.b);
     // u = kappa - 1/2; the half bin is u >= 0, v = u -+ 1/4 its local variable
-    auto poly = [&](int pos, float u) -> float2 {
-        const bool up = u >= 0.f;
-        const float v = u + (up ? -0.25f : 0.25f);
-        const float4* r = cf + (up ? plane4 : 0) + 3 * pos;
+    auto horner = [&](const float4* __restrict__ r, float v) -> float2 {
         const float4 e0 = r[0], e1 = r[1], e2 = r[2];
         const float2 vv = make_float2(v, v);
         float2 P = __ffma2_rn(make_float2(e2.z, e2.w), vv, make_float2(e2.x, e2.y));
@@ -130,6 +127,10 @@ __device__ __forceinline__ void sinc_sft(const DirichletParams& p, const SkySftM
         P = __ffma2_rn(P, vv, make_float2(e1.x, e1.y));
         P = __ffma2_rn(P, vv, make_float2(e0.z, e0.w));
         return __ffma2_rn(P, vv, make_float2(e0.x, e0.y));
+    };
+    auto poly = [&](int pos, float u) -> float2 {
+        const bool up = u >= 0.f;
+        return horner(cf + (up ? plane4 : 0) + 3 * pos, u + (up ? -0.25f : 0.25f));
     };
     auto add = [&](float tw_re, float tw_im, float2 P, float2& fa_q, float2& fb_q) {
         const float2 z = make_float2(fmaf(tw_re, P.x, -tw_im * P.y), fmaf(tw_re, P.y, tw_im * P.x));
@@ -149,13 +150,31 @@ __device__ __forceinline__ void sinc_sft(const DirichletParams& p, const SkySftM
         __sincosf((float)(int)ph * kPhaseToRad, &sn, &cs);
         float tw_re = cs, tw_im = -sn;
         const float u0 = frac_to_float((unsigned int)kh) - 0.5f;
+        if (fabsf(m.eps) * (float)(M - 1) <= kSincSlack) {
+            // kappa drifts by at most kSincSlack over the M templates: one half
+            // bin, chosen at the middle template, serves all of them (at most
+            // kSincSlack / 2 outside it, where the interpolant still holds)
+            const bool up = fmaf(0.5f * (float)(M - 1), m.eps, u0) >= 0.f;
+            const float4* cq = cf + (up ? plane4 : 0) + 3 * pos0;
+            const float v0 = u0 + (up ? -0.25f : 0.25f);
 #pragma unroll
-        for (int q = 0; q < M; ++q) {
-            add(tw_re, tw_im, poly(pos0 + q, fmaf((float)q, m.eps, u0)), fa[q], fb[q]);
-            if (q + 1 < M) {
-                const float t = fmaf(tw_re, m.rot_re, -tw_im * m.rot_im);
-                tw_im = fmaf(tw_re, m.rot_im, tw_im * m.rot_re);
-                tw_re = t;
+            for (int q = 0; q < M; ++q) {
+                add(tw_re, tw_im, horner(cq + 3 * q, fmaf((float)q, m.eps, v0)), fa[q], fb[q]);
+                if (q + 1 < M) {
+                    const float t = fmaf(tw_re, m.rot_re, -tw_im * m.rot_im);
+                    tw_im = fmaf(tw_re, m.rot_im, tw_im * m.rot_re);
+                    tw_re = t;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < M; ++q) {
+                add(tw_re, tw_im, poly(pos0 + q, fmaf((float)q, m.eps, u0)), fa[q], fb[q]);
+                if (q + 1 < M) {
+                    const float t = fmaf(tw_re, m.rot_re, -tw_im * m.rot_im);
+                    tw_im = fmaf(tw_re, m.rot_im, tw_im * m.rot_re);
+                    tw_re = t;
+                }
             }
         }
     } else {

@@ -116,6 +116,9 @@ __host__ __device__ constexpr int far_offset(int i) { return i < 6 ? i - 7 : i -
 // half) holds c_{h,0..5} in FP32.
 constexpr int kSincDeg = 5;
 constexpr int kSincTerms = 16;
+// Largest kappa drift over one thread's templates for which one half bin
+// serves them all (the interpolant's error grows by < 30 % at 1e-3 outside).
+constexpr float kSincSlack = 2e-3f;
 struct SincGamma {
     float g[2][kSincTerms][kSincDeg + 1];   // [half][offset k + 7][power]
 };
