@@ -88,13 +88,16 @@ typedef struct {
  *   other twelve through a degree-5 polynomial in kappa whose coefficients
  *   are precomputed per SFT and window position (interpolation error below
  *   5e-6 of each term); needs two tables of 16 and 48 bytes per stored bin
- *   and SFT.  Batched workunits always use DIRECT.
- * SINCPOLY (D = 8, no Kahan): the whole window term, sin(pi kappa) times the
- *   2D-bin sum, is entire in kappa and is evaluated as one degree-9
- *   polynomial in kappa - 1/2 with coefficients precomputed per SFT and window
- *   position (80 bytes per stored bin and SFT; no reciprocal, sine or clamp
- *   per template).  It runs in the TMA-ring staging (uniform spindown grid,
- *   P df T = 2); elsewhere it falls back to FARPOLY.
+ *   and SFT.
+ * SINCPOLY (D = 8, no Kahan): the whole window term, sin(pi kappa)/2 times
+ *   the 2D-bin sum, is entire in kappa; on each half of the bin (kappa < 1/2
+ *   and kappa >= 1/2) it is evaluated as a degree-5 polynomial whose
+ *   coefficients are precomputed per SFT, window position and half (two
+ *   48-byte records per stored bin and SFT; interpolation error below 2.1e-6
+ *   of each term; no reciprocal, sine or clamp per template).  It runs in the
+ *   TMA-ring staging (uniform spindown grid, P df T = 2, 5 or 7 templates per
+ *   thread); elsewhere it falls back to FARPOLY.
+ * Batched workunits use the TMA-ring form where it applies, else DIRECT.
  * AUTO: SINCPOLY where the TMA ring applies, else FARPOLY where it applies,
  *   else DIRECT. */
 typedef enum {

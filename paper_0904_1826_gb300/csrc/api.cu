@@ -940,6 +940,8 @@ int fstat_set_templates(fstat_ctx* c, const double* sky, int32_t n_sky, double f
 namespace {
 
 // Refresh the per-SFT state, plan the tiles and size every buffer of one bank.
+int ensure_tables(fstat_ctx* c, cudaStream_t s);
+
 int prepare(fstat_ctx* c, cudaStream_t s) {
     int rc;
     if ((rc = refresh_sft_state(c, s)) != FSTAT_OK) return rc;
@@ -961,6 +963,13 @@ int prepare(fstat_ctx* c, cudaStream_t s) {
     if ((rc = grow(c, &c->d_comb, c->cap_comb, (size_t)c->n_sky)) != FSTAT_OK) return rc;
     if ((rc = grow(c, &c->d_twoF, c->cap_twoF, n_twoF)) != FSTAT_OK) return rc;
     if ((rc = ensure_topk(c)) != FSTAT_OK) return rc;
+    return ensure_tables(c, s);
+}
+
+// The far-field or sinc tables for the current plan: their kind and extent
+// follow the plan (form, window width), so a new plan may need a rebuild.
+int ensure_tables(fstat_ctx* c, cudaStream_t s) {
+    int rc;
     if (c->plan.far) far_extent(c, c->plan.w_pairs, &c->far_xoff, &c->n_pos);
     if (c->plan.far &&
         (c->tab_dirty || c->tab_npos != c->n_pos || c->tab_xoff != c->far_xoff || c->tab_sinc != c->plan.sinc)) {
@@ -1051,10 +1060,23 @@ DirichletParams dirichlet_params(const fstat_ctx* c) {
     return dp;
 }
 
+// True when the built tables are the ones the plan's kernel reads (kind and
+// extent); the far-field and sinc kernels are never launched otherwise.
+bool tables_match(const fstat_ctx* c, const Plan& pl) {
+    if (!pl.far) return true;
+    int xoff = 0, n_pos = 0;
+    far_extent(c, pl.w_pairs, &xoff, &n_pos);
+    return !c->tab_dirty && c->tab_sinc == pl.sinc && c->tab_npos == n_pos && c->tab_xoff == xoff &&
+           c->n_pos == n_pos && c->far_xoff == xoff;
+}
+
 cudaError_t launch_dir(const fstat_ctx* c, const DirichletParams& dp, long long grid, cudaStream_t s) {
     const Plan& pl = c->plan;
     const int threads = pl.W * 32;
-    if (pl.far) return launch_dirichlet_far(pl.variant, dp, threads, pl.smem, grid, s);
+    if (pl.far) {
+        if (!tables_match(c, pl)) return cudaErrorInvalidValue;
+        return launch_dirichlet_far(pl.variant, dp, threads, pl.smem, grid, s);
+    }
     if (c->opts.bins_form == FSTAT_BINS_C64)
         return launch_dirichlet_c64(pl.variant, dp, c->opts.dterms, threads, pl.smem, grid, s);
     if (c->opts.bins_form == FSTAT_BINS_F16)
@@ -1345,6 +1367,7 @@ int fstat_autotune(fstat_ctx* c, void* cuda_stream, int32_t* out) {
             if (make_plan(c, c->plan) != FSTAT_OK) continue;
             c->plan_valid = true;
             if (c->plan.C != C) continue;   // round size capped by shared memory
+            if (ensure_tables(c, s) != FSTAT_OK) continue;   // tables for this plan's form and width
             // a slice of the bank: the first sky points, about four waves of blocks
             const long long per_sky = (long long)c->plan.n_col * c->plan.chunks_per_col;
             int occ = 2;

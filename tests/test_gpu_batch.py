@@ -86,7 +86,8 @@ def test_batch_with_two_kernel_variants(lib):
         g.close()
 
 
-@pytest.mark.parametrize("algo,chunks", [("direct", (6, 8, 10)), ("farpoly", (2, 3, 4, 6, 8))])
+@pytest.mark.parametrize("algo,chunks", [("direct", (6, 8, 10)), ("farpoly", (2, 3, 4, 6, 8)),
+                                         ("sincpoly", (2, 3, 4, 6, 8)), ("auto", (2, 3, 4, 6, 8))])
 def test_autotune_picks_a_valid_tiling_and_keeps_parity(lib, algo, chunks):
     w = config_mid(n_sky=40, n_f=150, n_fdot=3)
     b = _with_signals(w)
@@ -98,7 +99,7 @@ def test_autotune_picks_a_valid_tiling_and_keeps_parity(lib, algo, chunks):
         t = g.autotune()
         assert t["M"] in (5, 7, 9) and t["sft_chunk"] in chunks and t["slice_us"] > 0
         g.compute()
-        assert g.plan()["M"] == t["M"]
+        assert g.plan()["M"] == t["M"] and g.error_flags() == 0
         got = g.twoF(0, ref.size).astype(np.float64)
         assert np.all(np.abs(got - ref) <= REL * ref + ABS)
     finally:

@@ -45,7 +45,8 @@ def case():
 
 
 FORMS = [("c64", False, "sincpoly"), ("c64", False, "farpoly"), ("c64", False, "direct"), ("c64", True, "direct"),
-         ("f16", False, "farpoly"), ("f16", True, "direct"), ("bf16", False, "farpoly"), ("bf16", True, "direct")]
+         ("f16", False, "sincpoly"), ("f16", False, "farpoly"), ("f16", True, "direct"),
+         ("bf16", False, "sincpoly"), ("bf16", False, "farpoly"), ("bf16", True, "direct")]
 
 
 def test_precision_forms_on_workunit_data(lib, case):
