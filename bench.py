@@ -35,9 +35,10 @@ FLOP_PER_PAIR = 100.0          # direct-sum FP32 work of one template.SFT pair: 
 N_SM = 152
 FP32_LANES = 128
 METRIC = "template·SFT pairs/s (2F) on 1 GB300, chosen vs plain FP32 form at stated 2F error"
-KERNEL_SOURCES = {"direct": ["dirichlet.cuh", "dirichlet_c64.cu", "dirichlet_f16.cu", "dirichlet_bf16.cu"],
-                  "farpoly": ["dirichlet.cuh", "dirichlet_far.cu"],
-                  "sincpoly": ["dirichlet.cuh", "dirichlet_far.cu"]}
+KERNEL_SOURCES = {"direct": ["fstat_internal.cuh", "dirichlet.cuh", "dirichlet_c64.cu", "dirichlet_f16.cu",
+                             "dirichlet_bf16.cu"],
+                  "farpoly": ["fstat_internal.cuh", "dirichlet.cuh", "dirichlet_far.cu"],
+                  "sincpoly": ["fstat_internal.cuh", "dirichlet.cuh", "dirichlet_far.cu"]}
 KERNEL_NAMES = {"direct": "dirichlet_kernel", "farpoly": "dirichlet_far_kernel",
                 "sincpoly": "dirichlet_far_ring_kernel"}
 
