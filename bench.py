@@ -365,6 +365,8 @@ def main():
         if world > 1:
             torch.distributed.barrier()
 
+    per_step = []   # per-step event times of the latest timed run (ms)
+
     def timed_run(g, steps, warmup, launch_mark=None):
         for _ in range(warmup):
             g.compute(stream)
@@ -379,15 +381,16 @@ def main():
         torch.cuda.synchronize()
         if launch_mark is not None:
             launch_mark[0] = g.launch_count()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(steps):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        ev[0].record(stream)
+        for i in range(steps):
             g.compute(stream)
-        e1.record(stream)
+            ev[i + 1].record(stream)
         torch.cuda.synchronize()
         barrier()
-        ms = e0.elapsed_time(e1)
+        ms = ev[0].elapsed_time(ev[-1])
+        per_step.clear()
+        per_step.extend(ev[i].elapsed_time(ev[i + 1]) for i in range(steps))
         kd, kt, nk = g.take_kernel_time()
         return ms, kd, kt, nk
 
@@ -398,6 +401,7 @@ def main():
     n_launch0 = [0]
 
     ms, k_dir, k_step, n_k = timed_run(g, args.steps, args.warmup, n_launch0)
+    steps_ms = sorted(per_step)
     clocks = sampler.stop()
     launches = g.launch_count() - n_launch0[0]
     if world > 1:
@@ -480,7 +484,9 @@ def main():
     if clocks and clocks.get("sm_mhz"):
         roofline["frac_at_sampled_clock"] = achieved / (N_SM * FP32_LANES * 2 * clocks["sm_mhz"] * 1e6 / 1e12)
     line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "step_ms": {"best": steps_ms[0], "median": steps_ms[len(steps_ms) // 2]} if steps_ms else None,
+            "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": {"c64": "f32", "f16": "f16-storage/f32", "bf16": "bf16-storage/f32"}[args.form],
             "data": "synthetic",
             "config": {"workload": "plain workunit: 2 det x 1200 gapped SFT (T=1800 s), 1 Hz band at 100 Hz, "

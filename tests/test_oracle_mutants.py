@@ -97,3 +97,42 @@ def test_noise_pin_catches_wrong_normalisation(monkeypatch):
     monkeypatch.setattr(O, "normalized", lambda Fa, Fb, A, B, C, D, s=1.0: orig(Fa, Fb, A, B, C, D, 2.0))
     with pytest.raises(AssertionError):
         P.test_noise_mean_matches_finite_dterms_prediction()
+
+
+# ------------------------------------------------------------ stack-slide
+
+def _slide_mutant(kind):
+    from oracle import semicoherent_oracle as S
+    orig = S.slide_constants
+
+    def f(f0, df, fdot, t_ref, f0_s, df_s, t_s):
+        if kind == "sign":          # slide the wrong way
+            return orig(f0, df, fdot, t_s, f0_s, df_s, t_ref)
+        if kind == "no_slide":      # forget the spindown term
+            return orig(f0, df, np.zeros_like(np.asarray(fdot, dtype=np.float64)), t_ref, f0_s, df_s, t_s)
+        A_fx, B_fx = orig(f0, df, fdot, t_ref, f0_s, df_s, t_s)
+        if kind == "truncate":      # nearest bin taken as floor
+            return A_fx - (1 << 31), B_fx
+        if kind == "inverse_ratio":  # df_s / df instead of df / df_s
+            return A_fx, int(round(2.0 ** 64 / B_fx))
+        raise ValueError(kind)
+    return f
+
+
+@pytest.mark.parametrize("kind", ["sign", "no_slide", "truncate", "inverse_ratio"])
+def test_stack_slide_pins_catch_mutants(monkeypatch, kind):
+    from oracle import semicoherent_oracle as S
+    import tests.test_oracle_semicoherent as SP
+    pins = [SP.test_exactly_representable_slides_move_by_whole_bins, SP.test_half_bin_slides_round_up,
+            SP.test_finer_semicoherent_grid_maps_four_to_one,
+            SP.test_signal_with_spindown_peaks_at_its_template_only_when_slid]
+    for pin in pins:
+        pin()
+    monkeypatch.setattr(S, "slide_constants", _slide_mutant(kind))
+    failed = 0
+    for pin in pins:
+        try:
+            pin()
+        except AssertionError:
+            failed += 1
+    assert failed >= 1, kind
