@@ -54,7 +54,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--compare-forms", action="store_true", help="also time the other storage forms")
-    ap.add_argument("--config", default="workunit", choices=["workunit", "batch", "proposal"],
+    ap.add_argument("--n-seg", type=int, default=8, help="time segments (semicoherent mode)")
+    ap.add_argument("--config", default="workunit", choices=["workunit", "batch", "proposal", "semicoherent"],
                     help="workunit: one workunit-sized bank (default); batch: 64 heterogeneous workunits")
     ap.add_argument("--n-wu", type=int, default=64, help="workunits in the batch mode")
     ap.add_argument("--n-train", type=int, default=512, help="training workunits (proposal mode)")
@@ -197,6 +198,119 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_semicoherent(args):
+    """Semicoherent search over the workunit: its SFTs split into time
+    segments, each segment's coherent 2F at the segment's midpoint (bands
+    padded for the slide), then the stack-slide sum over segments and the
+    top-K of the sum, every step."""
+    import torch
+    import paper_0904_1826_gb300 as fs
+    from workload import TemplateBank, DetectorData, Workload
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    w = workload(rank, world, args.n_sky)
+    # signals added to the whole data set on the GPU (model-exact), read back
+    full = fs.FStat(local_rank, topk=10, algo=args.algo)
+    full.load_workload(w)
+    full.inject(w.injections, w.bank.t_ref)
+    bins = [fs.fstat_get_bins(full.ctx, i, d.n_sft, w.n_bins) for i, d in enumerate(w.detectors)]
+    full.close()
+    t_all = np.concatenate([d.t_start for d in w.detectors])
+    t0, t1 = float(t_all.min()), float(t_all.max()) + w.T
+    edges = t0 + (t1 - t0) * np.arange(args.n_seg + 1) / args.n_seg
+    edges[-1] += 1.0
+    bank, pad = w.bank, 8
+    segs, seg_pairs, seg_bytes = [], 0, 0
+    for s in range(args.n_seg):
+        dets = []
+        for i, d in enumerate(w.detectors):
+            sel = (d.t_start >= edges[s]) & (d.t_start < edges[s + 1])
+            dets.append(DetectorData(d.lat, d.lon, d.az, d.t_start[sel], bins[i][sel]))
+        bs = TemplateBank(sky=bank.sky, f0=bank.f0 - pad * bank.df, df=bank.df, n_f=bank.n_f + 2 * pad,
+                          fdot=bank.fdot, t_ref=0.5 * (edges[s] + edges[s + 1]))
+        g = fs.FStat(local_rank, topk=10, algo=args.algo)
+        g.load_workload(Workload(w.name, w.T, w.k_lo, w.n_bins, w.dterms, 10, dets, bs))
+        segs.append(g)
+        seg_pairs += bs.n_sky * bs.n_fdot * bs.n_f * sum(d.n_sft for d in dets)
+        seg_bytes += 4 * bs.n_sky * bs.n_fdot * bs.n_f
+    n_t = bank.n_sky * bank.n_fdot * bank.n_f
+    out = torch.empty(n_t, dtype=torch.float32, device="cuda")
+    k = w.topk
+    idx = torch.empty(k, dtype=torch.int64, device="cuda")
+    val = torch.empty(k, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.Stream()
+    ctxs = [g.ctx for g in segs]
+    ss = []
+
+    def step(timed):
+        for g in segs:
+            g.compute(stream)
+        if timed:
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+        fs.fstat_stackslide(ctxs, bank.f0, bank.df, bank.n_f, bank.t_ref, out, stream, want_outside=False)
+        if timed:
+            b.record(stream)
+            ss.append((a, b))
+        fs.fstat_toplist_noalloc(out, k, idx, val, stream)
+
+    for _ in range(args.warmup):
+        step(False)
+    torch.cuda.synchronize()
+    for g in segs:
+        g.take_kernel_time()
+    junk = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    junk.fill_(1)
+    del junk
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step(True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    clocks = sampler.stop()
+    ss_ms = sum(a.elapsed_time(b) for a, b in ss) / args.steps
+    k_dir = sum(g.take_kernel_time()[0] for g in segs)   # per step: each is a per-compute average
+    n_outside = fs.fstat_stackslide(ctxs, bank.f0, bank.df, bank.n_f, bank.t_ref, out, stream)
+    torch.cuda.synchronize()
+    top_i, top_v = int(idx[0].item()), float(val[0].item())
+    ss_bytes = seg_bytes + 4 * n_t
+    peak_gbs = 6797.9
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peak_gbs = float(json.load(fh)["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        pass
+    achieved = FLOP_PER_PAIR * seg_pairs / (k_dir / 1e3) / 1e12
+    peak = N_SM * FP32_LANES * 2 * 2070.0 * 1e6 / 1e12
+    line = {"metric": METRIC, "value": seg_pairs * args.steps / (ms / 1e3), "unit": "pairs/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"semicoherent: the workunit's 2 det x 1200 SFTs in {args.n_seg} time segments, "
+                                   f"coherent 2F per segment ({bank.n_sky} sky x {bank.n_f + 2 * pad} f x "
+                                   f"{bank.n_fdot} fdot at the segment midpoint), stack-slide sum over segments, "
+                                   f"top-{k} of the sum",
+                       "n_seg": args.n_seg, "coherent_pairs_per_step": seg_pairs,
+                       "semicoherent_templates": n_t},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": "dirichlet (all segments)",
+                         "dirichlet_ms": k_dir},
+            "stackslide": {"ms_per_step": ss_ms, "bytes_per_step": ss_bytes,
+                           "roofline": {"bound": "hbm", "achieved": ss_bytes / (ss_ms / 1e3) / 1e9,
+                                        "peak": peak_gbs, "unit": "GB/s",
+                                        "frac": ss_bytes / (ss_ms / 1e3) / 1e9 / peak_gbs, "traffic": None,
+                                        "kernel": "stackslide_kernel"},
+                           "n_outside": n_outside},
+            "clocks": clocks, "top": {"sum_2F": top_v, "idx": top_i}}
+    print(json.dumps(line))
+    for g in segs:
+        g.close()
+
+
 def run_batch(args):
     """64 heterogeneous workunits (SFT counts 200-2400 over 1-2 detectors,
     bands 0.1-2 Hz, 100-20 000 sky points, 1-20 spindowns, 0-4 signals) in
@@ -337,6 +451,9 @@ def main():
         return
     if args.config == "batch":
         run_batch(args)
+        return
+    if args.config == "semicoherent":
+        run_semicoherent(args)
         return
     import torch
     rank, local_rank, world = dist_env()

@@ -95,6 +95,8 @@ SIGNATURES = {
                                              ctypes.c_float, _P]),
     "fstat_extract_windows": (ctypes.c_int, [_P, _I32, _I32, _I32, _I32, _I32, _P, _I32, ctypes.c_float,
                                              ctypes.c_float, _P]),
+    # include/fstat_semi.h
+    "fstat_stackslide": (ctypes.c_int, [ctypes.POINTER(_P), _I32, _D, _D, _I32, _D, _P, ctypes.POINTER(_I64), _P]),
     # include/fstat_noalloc.h
     "fstat_toplist_noalloc": (ctypes.c_int, [ctypes.c_int, _P, _I64, _I32, _P, _P, _P, ctypes.c_char_p, _I32]),
     # include/fstat_mlp.h
@@ -396,6 +398,20 @@ def fstat_toplist_noalloc(v, k: int, idx_out, val_out, stream=None) -> None:
                                     _stream_handle(stream), msg, len(msg))
     if rc != FSTAT_OK:
         raise FstatError(rc, msg.value.decode())
+
+
+def fstat_stackslide(segs, f0: float, df: float, n_f: int, t_ref: float, out, stream=None,
+                     want_outside: bool = True):
+    """Semicoherent stack-slide (include/fstat_semi.h) of the computed
+    segment contexts `segs` into the caller's CUDA FP32 tensor `out`
+    ([n_sky * n_fdot * n_f]); returns the out-of-band lookup count (or None,
+    asynchronous, when want_outside is False)."""
+    arr = (_P * len(segs))(*[ctypes.c_void_p(c) if isinstance(c, int) else c for c in segs])
+    n_out = _I64(0)
+    rc = _lib.fstat_stackslide(arr, len(segs), f0, df, int(n_f), t_ref, ctypes.c_void_p(out.data_ptr()),
+                               ctypes.byref(n_out) if want_outside else None, _stream_handle(stream))
+    _check(segs[0], rc)
+    return int(n_out.value) if want_outside else None
 
 
 MLP_NAMES = ("W1", "b1", "W2", "b2", "w3", "b3")

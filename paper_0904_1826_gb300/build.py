@@ -12,7 +12,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfstat.so")
 SOURCES = ["api.cu", "ephemeris.cu", "toplist.cu", "mlp.cu", "dirichlet_c64.cu", "dirichlet_f16.cu", "dirichlet_bf16.cu",
-           "dirichlet_far.cu", "noise.cu"]
+           "dirichlet_far.cu", "noise.cu", "semicoherent.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -93,6 +93,16 @@ struct fstat_ctx {
     float* d_floor = nullptr;       // noise floor S [n_sft][n_bins]
     double* d_sbar = nullptr;       // mean floor per SFT
     double* d_weight = nullptr;     // noise weight per SFT
+    // stack-slide scratch (held by the first segment of a call)
+    SlideSeg* d_slide_seg = nullptr;
+    long long* d_slide_A = nullptr;
+    long long* d_slide_B = nullptr;
+    unsigned long long* d_slide_out = nullptr;
+    size_t cap_slide_seg = 0, cap_slide_A = 0, cap_slide_B = 0, cap_slide_out = 0;
+    std::vector<SlideSeg> slide_last;   // segment table, grid and spindowns of the last call (reused when equal)
+    std::vector<double> slide_fdot;
+    double slide_grid[3] = {0, 0, 0};
+    const long long* slide_A_at = nullptr;
     size_t cap_bins_w = 0, cap_floor = 0, cap_sbar = 0, cap_weight = 0;
     void* d_bins16 = nullptr;       // 16-bit copy (precision forms)
     float* d_scale = nullptr;       // per-SFT storage scale
@@ -776,7 +786,8 @@ void fstat_destroy(fstat_ctx* c) {
                     c->d_fdot, c->d_meta, c->d_kh0, c->d_ph0, c->d_abcd, c->d_comb, c->d_twoF, c->d_err,
                     c->tw.hist, c->tw.state, c->tw.tie_count, c->tw.cand_idx, c->tw.cand_val, c->tw.n_cand,
                     c->tw.out_idx, c->tw.out_val, c->d_inj_work, c->d_sig, c->d_ptab, c->d_pcoef,
-                    c->d_bins_w, c->d_floor, c->d_sbar, c->d_weight};
+                    c->d_bins_w, c->d_floor, c->d_sbar, c->d_weight, c->d_slide_seg, c->d_slide_A,
+                    c->d_slide_B, c->d_slide_out};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (int i = 0; i < kTimedRing; ++i) {
@@ -789,6 +800,70 @@ void fstat_destroy(fstat_ctx* c) {
 }
 
 const char* fstat_last_error(const fstat_ctx* c) { return c ? c->err.c_str() : ""; }
+
+int fstat_stackslide(fstat_ctx* const* seg, int32_t n_seg, double f0, double df, int32_t n_f, double t_ref,
+                     float* out, int64_t* n_outside, void* cuda_stream) {
+    if (!seg || n_seg < 1 || n_seg > FSTAT_SEMI_MAX_SEG || !seg[0]) return FSTAT_EINVAL;
+    fstat_ctx* c = seg[0];
+    c->err.clear();
+    if (!out) return fail(c, FSTAT_EINVAL, "null output");
+    if (n_f < 1) return fail(c, FSTAT_EINVAL, "n_f must be >= 1");
+    if (!std::isfinite(f0) || !(df > 0) || !std::isfinite(df) || !std::isfinite(t_ref))
+        return fail(c, FSTAT_EINVAL, "f0, df, t_ref must be finite and df > 0");
+    std::vector<SlideSeg> h(n_seg);
+    for (int s = 0; s < n_seg; ++s) {
+        const fstat_ctx* g = seg[s];
+        if (!g) return fail(c, FSTAT_EINVAL, "segment %d is null", s);
+        if (g->device != c->device) return fail(c, FSTAT_EINVAL, "segment %d is on another device", s);
+        if (!g->have_templates || !g->computed || !g->d_twoF)
+            return fail(c, FSTAT_ESTATE, "segment %d has no computed 2F", s);
+        if (g->n_sky != c->n_sky || g->h_sky != c->h_sky) return fail(c, FSTAT_EINVAL, "segment %d: other sky list", s);
+        if (g->h_fdot != c->h_fdot) return fail(c, FSTAT_EINVAL, "segment %d: other spindown list", s);
+        const double r = df / g->df;
+        if (!(r >= 0x1p-20 && r <= 0x1p20)) return fail(c, FSTAT_EINVAL, "segment %d: df / df_s outside 2^-20..2^20", s);
+        h[s] = SlideSeg{g->d_twoF, (long long)g->n_f, g->f0, g->df, g->t_ref};
+    }
+    if (set_device(c) != FSTAT_OK) return FSTAT_ECUDA;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    int rc;
+    const int n_fdot = c->n_fdot;
+    if ((rc = grow(c, &c->d_slide_seg, c->cap_slide_seg, (size_t)n_seg)) != FSTAT_OK) return rc;
+    if ((rc = grow(c, &c->d_slide_A, c->cap_slide_A, (size_t)n_seg * n_fdot)) != FSTAT_OK) return rc;
+    if ((rc = grow(c, &c->d_slide_B, c->cap_slide_B, (size_t)n_seg)) != FSTAT_OK) return rc;
+    if ((rc = grow(c, &c->d_slide_out, c->cap_slide_out, 1)) != FSTAT_OK) return rc;
+    // the segment table and the fixed-point slide constants are rebuilt only
+    // when the segments or the grid change
+    bool same = c->slide_last.size() == h.size() && c->slide_grid[0] == f0 && c->slide_grid[1] == df &&
+                c->slide_grid[2] == t_ref && c->slide_fdot == c->h_fdot && c->slide_A_at == c->d_slide_A;
+    for (int s = 0; same && s < n_seg; ++s)
+        same = h[s].twoF == c->slide_last[s].twoF && h[s].n_f == c->slide_last[s].n_f && h[s].f0 == c->slide_last[s].f0 &&
+               h[s].df == c->slide_last[s].df && h[s].t == c->slide_last[s].t;
+    if (!same) {
+        c->slide_last.clear();   // invalid until the new table is in place
+        CUDA_TRY(c, cudaMemcpyAsync(c->d_slide_seg, h.data(), (size_t)n_seg * sizeof(SlideSeg), cudaMemcpyHostToDevice,
+                                    st));
+    }
+    if (n_outside) CUDA_TRY(c, cudaMemsetAsync(c->d_slide_out, 0, sizeof(unsigned long long), st));
+    CUDA_TRY(c, launch_stackslide(c->d_slide_seg, n_seg, c->d_fdot, n_fdot, f0, df, t_ref, c->d_slide_A, c->d_slide_B,
+                                  !same, (long long)c->n_sky * n_fdot, n_f, out, n_outside ? c->d_slide_out : nullptr,
+                                  st));
+    c->launches += same ? 1 : 2;
+    if (!same) {
+        c->slide_last = h;
+        c->slide_fdot = c->h_fdot;
+        c->slide_A_at = c->d_slide_A;
+        c->slide_grid[0] = f0;
+        c->slide_grid[1] = df;
+        c->slide_grid[2] = t_ref;
+    }
+    if (n_outside) {
+        unsigned long long v = 0;
+        CUDA_TRY(c, cudaMemcpyAsync(&v, c->d_slide_out, sizeof(v), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(c, cudaStreamSynchronize(st));
+        *n_outside = (int64_t)v;
+    }
+    return FSTAT_OK;
+}
 
 int fstat_set_sfts(fstat_ctx* c, int32_t det_index, const fstat_detector* det, double Tsft, int64_t k_lo,
                    int32_t n_bins, int32_t n_sft, const double* t_start, const float* bins, int32_t mem) {

@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include "../../include/fstat.h"
+#include "../../include/fstat_semi.h"
 
 namespace fs {
 
@@ -260,5 +261,16 @@ cudaError_t launch_dirichlet_far_batch(int v, const DirichletBatch& b, int threa
                                        cudaStream_t s);
 cudaError_t dirichlet_far_batch_occupancy(int v, int threads, size_t smem, int* blocks_per_sm);
 cudaError_t launch_topk(const float* v, long long n, int k, TopkWork& w, cudaStream_t s);
+
+// One segment of a stack-slide: its device 2F [n_sky][n_fdot][n_f] and grid.
+struct SlideSeg {
+    const float* twoF;
+    long long n_f;
+    double f0, df, t;
+};
+// prep = false reuses A_fx, B_fx of an earlier call with the same segments and grid.
+cudaError_t launch_stackslide(const SlideSeg* seg, int n_seg, const double* fdot, int n_fdot, double f0, double df,
+                              double t_ref, long long* A_fx, long long* B_fx, bool prep, long long n_rows, int n_f,
+                              float* out, unsigned long long* n_outside, cudaStream_t s);
 
 }  // namespace fs
