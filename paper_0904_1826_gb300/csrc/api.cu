@@ -823,6 +823,9 @@ int fstat_stackslide(fstat_ctx* const* seg, int32_t n_seg, double f0, double df,
         if (!(r >= 0x1p-20 && r <= 0x1p20)) return fail(c, FSTAT_EINVAL, "segment %d: df / df_s outside 2^-20..2^20", s);
         h[s] = SlideSeg{g->d_twoF, (long long)g->n_f, g->f0, g->df, g->t_ref};
     }
+    // B = df / df_s rounds to exactly 1 on the device iff it does here (IEEE division)
+    bool unit = true;
+    for (int s = 0; s < n_seg; ++s) unit = unit && df / h[s].df == 1.0 && h[s].n_f < (1LL << 30);
     if (set_device(c) != FSTAT_OK) return FSTAT_ECUDA;
     cudaStream_t st = (cudaStream_t)cuda_stream;
     int rc;
@@ -845,8 +848,8 @@ int fstat_stackslide(fstat_ctx* const* seg, int32_t n_seg, double f0, double df,
     }
     if (n_outside) CUDA_TRY(c, cudaMemsetAsync(c->d_slide_out, 0, sizeof(unsigned long long), st));
     CUDA_TRY(c, launch_stackslide(c->d_slide_seg, n_seg, c->d_fdot, n_fdot, f0, df, t_ref, c->d_slide_A, c->d_slide_B,
-                                  !same, (long long)c->n_sky * n_fdot, n_f, out, n_outside ? c->d_slide_out : nullptr,
-                                  st));
+                                  !same, unit, (long long)c->n_sky * n_fdot, n_f, out,
+                                  n_outside ? c->d_slide_out : nullptr, st));
     c->launches += same ? 1 : 2;
     if (!same) {
         c->slide_last = h;

@@ -268,9 +268,10 @@ struct SlideSeg {
     long long n_f;
     double f0, df, t;
 };
-// prep = false reuses A_fx, B_fx of an earlier call with the same segments and grid.
+// prep = false reuses A_fx, B_fx of an earlier call with the same segments and
+// grid; unit = every segment's df_s equals df exactly (B = 1).
 cudaError_t launch_stackslide(const SlideSeg* seg, int n_seg, const double* fdot, int n_fdot, double f0, double df,
-                              double t_ref, long long* A_fx, long long* B_fx, bool prep, long long n_rows, int n_f,
-                              float* out, unsigned long long* n_outside, cudaStream_t s);
+                              double t_ref, long long* A_fx, long long* B_fx, bool prep, bool unit, long long n_rows,
+                              int n_f, float* out, unsigned long long* n_outside, cudaStream_t s);
 
 }  // namespace fs
