@@ -136,3 +136,39 @@ def test_stack_slide_pins_catch_mutants(monkeypatch, kind):
         except AssertionError:
             failed += 1
     assert failed >= 1, kind
+
+
+# ------------------------------------------------------------ frequency coverage
+
+def _coverage_mutant(kind):
+    from oracle import coverage_oracle as CO
+    orig = CO.compute_fstat_coverage
+
+    def f(dets, T, k_lo, dterms, bank, j_lo, j_hi, sky_indices=None):
+        j_lo, j_hi = np.asarray(j_lo), np.asarray(j_hi)
+        if kind == "inclusive_end":       # [j_lo, j_hi] instead of [j_lo, j_hi)
+            return orig(dets, T, k_lo, dterms, bank, j_lo, j_hi + 1, sky_indices)
+        if kind == "ignored":             # coverage dropped
+            return orig(dets, T, k_lo, dterms, bank, np.zeros_like(j_lo), np.full_like(j_hi, bank.n_f), sky_indices)
+        if kind == "off_by_one_start":    # (j_lo, j_hi)
+            return orig(dets, T, k_lo, dterms, bank, j_lo + 1, j_hi, sky_indices)
+        raise ValueError(kind)
+    return f
+
+
+@pytest.mark.parametrize("kind", ["inclusive_end", "ignored", "off_by_one_start"])
+def test_coverage_pins_catch_mutants(monkeypatch, kind):
+    from oracle import coverage_oracle as CO
+    import tests.test_oracle_coverage as CP
+    pins = [CP.test_detector_split_gives_each_detector_alone,
+            CP.test_sft_covering_nothing_is_absent_and_uncovered_frequency_is_zero]
+    for pin in pins:
+        pin()
+    monkeypatch.setattr(CO, "compute_fstat_coverage", _coverage_mutant(kind))
+    failed = 0
+    for pin in pins:
+        try:
+            pin()
+        except AssertionError:
+            failed += 1
+    assert failed >= 1, kind
