@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--compare-forms", action="store_true", help="also time the other storage forms")
     ap.add_argument("--n-seg", type=int, default=8, help="time segments (semicoherent mode)")
+    ap.add_argument("--coverage", type=float, default=0.0,
+                    help="per-SFT frequency coverage: this fraction of the SFTs covers a random contiguous run of "
+                         "50-100 %% of the band, the rest all of it (0 = off); pairs count covered pairs only")
     ap.add_argument("--config", default="workunit", choices=["workunit", "batch", "proposal", "semicoherent"],
                     help="workunit: one workunit-sized bank (default); batch: 64 heterogeneous workunits")
     ap.add_argument("--n-wu", type=int, default=64, help="workunits in the batch mode")
@@ -82,6 +85,13 @@ def workload(rank: int, world: int, n_sky: int):
     from workload import config1, fibonacci_sky
     sky_all = fibonacci_sky(n_sky * world)
     return config1(sky=sky_all[rank * n_sky:(rank + 1) * n_sky])
+
+
+def algo_of(variant: int) -> str:
+    """Form of a plan's kernel variant id (include/fstat.h, fstat_get_plan)."""
+    if variant < 100:
+        return "direct"
+    return "sincpoly" if variant in (112, 113, 114, 115, 116) else "farpoly"
 
 
 def kernel_hash(algo: str) -> str:
@@ -466,6 +476,17 @@ def main():
 
     w = workload(rank, world, args.n_sky)
     n_pairs = w.n_pairs
+    cov = None
+    if args.coverage > 0:
+        # a seeded fraction of the SFTs covers a random contiguous run of
+        # 50-100 % of the frequencies; the others cover all of them
+        rng = np.random.default_rng(4242 + rank)
+        n_f = w.bank.n_f
+        ragged = rng.random(w.n_sft_total) < args.coverage
+        width = np.where(ragged, rng.integers(n_f // 2, n_f + 1, w.n_sft_total), n_f)
+        lo = (rng.random(w.n_sft_total) * (n_f - width + 1)).astype(np.int64)
+        cov = (lo.astype(np.int32), (lo + width).astype(np.int32))
+        n_pairs = w.bank.n_sky * w.bank.n_fdot * int(width.sum())
     stream = torch.cuda.Stream()
 
     def make(form, kahan=False, algo=None):
@@ -476,6 +497,8 @@ def main():
         g.inject(w.injections, w.bank.t_ref)
         if args.noise_floor:
             fs.fstat_set_noise_floor(g.ctx, args.noise_floor)
+        if cov is not None:
+            fs.fstat_set_coverage(g.ctx, *cov)
         return g
 
     def barrier():
@@ -554,6 +577,8 @@ def main():
         for i, d in enumerate(w.detectors):
             fs.fstat_set_sfts(g.ctx, i, d.lat, d.lon, d.az, w.T, w.k_lo, d.t_start,
                               pinned[i].numpy().view(np.complex64).reshape(d.n_sft, w.n_bins))
+        if cov is not None:
+            fs.fstat_set_coverage(g.ctx, *cov)
         g.set_bank(w.bank)
         g.compute(stream)
         g.toplist(w.topk)
@@ -579,8 +604,7 @@ def main():
             ms2, kd2, _, _ = timed_run(g2, args.steps, 1)
             name = f + ("+kahan" if kahan else "") + ("" if kahan or algo == "auto" else "/" + algo)
             forms[name] = {"value": n_pairs * args.steps / (ms2 / 1e3), "dirichlet_ms": kd2,
-                           "algo": ("direct" if g2.plan()["variant"] < 100 else
-                                    "sincpoly" if g2.plan()["variant"] >= 112 else "farpoly")}
+                           "algo": algo_of(g2.plan()["variant"])}
             g2.close()
 
     if rank != 0:
@@ -592,7 +616,7 @@ def main():
     peak = N_SM * FP32_LANES * 2 * clock_mhz * 1e6 / 1e12       # TFLOP/s, recipe unit counts, max clock
     achieved = FLOP_PER_PAIR * n_pairs / (k_dir / 1e3) / 1e12
     vid = plan.get("variant", 0)
-    algo_used = "direct" if vid < 100 else ("sincpoly" if vid >= 112 else "farpoly")
+    algo_used = algo_of(vid)
     kernel_name = KERNEL_NAMES[algo_used] if vid < 107 else "dirichlet_far_ring_kernel"
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": ncu_traffic(args.form, algo_used), "kernel": kernel_name,
@@ -610,6 +634,7 @@ def main():
                                    "8 injected signals; 10000 sky x 1800 f x 10 fdot, D=8, top-1000",
                        "form": args.form, "algo": algo_used, "pairs_per_step_per_gpu": n_pairs,
                        "noise_floor_half_window": args.noise_floor,
+                       "coverage": args.coverage or None,
                        "l2": "per-step working set ~5 GB (bases, 2F array) > 129 MB L2; L2 flushed before timing",
                        "plan": plan},
             "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": int(h2d),

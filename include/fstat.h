@@ -211,7 +211,8 @@ int fstat_get_bins(fstat_ctx *ctx, int32_t det_index, float *out, int32_t mem);
 
 /* Device-side error flags raised by the last compute (0 = none); synchronises.
  * Bit 0: a template window left the staged SFT range (clamped).
- * Bit 1: a sky point had D = AB - C^2 <= 0 (its 2F set to 0).
+ * Bit 1: a sky point (or, with coverage, a frequency) had a degenerate
+ *        D = AB - C^2 (its 2F set to 0).
  * Bit 2: a wait of the far-field ring pipeline gave up (that block's 2F invalid). */
 int fstat_get_error_flags(fstat_ctx *ctx, int32_t *flags);
 
@@ -228,6 +229,26 @@ int fstat_get_error_flags(fstat_ctx *ctx, int32_t *flags);
  *          C, Fa and Fb (w = 0 where Sbar = 0, left out of the mean).
  * W = 0 switches it off (the default).  Errors: EINVAL (W outside 0..64). */
 int fstat_set_noise_floor(fstat_ctx *ctx, int32_t half_window);
+
+/* Per-SFT frequency coverage: a varying number of SFTs per frequency (the
+ * data the paper's version-3 client pads its thread blocks for, Section
+ * "CUDA").  SFT i (in load order: all SFTs of detector 0, then detector 1,
+ * ...) contributes only to templates whose frequency index j (f = f0 + j df)
+ * lies in [j_lo[i], j_hi[i]); each template's A, B, C, D are summed over
+ * the SFTs that cover it:
+ *   Fa(j) = sum_{i covers j} a_i z_i(j),   A(j) = sum_{i covers j} a_i^2, ...
+ * A frequency no SFT covers gets 2F = 0 (no flag); a degenerate D elsewhere
+ * raises flag bit 1.  Ranges may reach outside [0, n_f) (clamped).
+ * An SFT that covers none of a thread's templates is skipped, so work falls
+ * with coverage.  From the next fstat_compute on; both pointers NULL switch
+ * coverage off.  Loading SFTs (fstat_set_sfts) switches it off too.
+ * Restrictions: n_f <= 8192 while coverage is on; the far-field form runs
+ * only in its TMA-ring staging (elsewhere the direct form is used); batched
+ * workunits have no coverage.  fstat_get_abcd stays the per-sky sum over
+ * all SFTs.
+ * Errors: EINVAL (one pointer NULL, n_sft != loaded SFTs, j_lo > j_hi),
+ * ESTATE (no SFTs loaded), ECUDA. */
+int fstat_set_coverage(fstat_ctx *ctx, const int32_t *j_lo, const int32_t *j_hi, int32_t n_sft);
 
 /* The noise floor S [n_sft][n_bins] (FP32; NULL to skip) and the weights
  * [n_sft] (FP64; NULL to skip) of the last compute, SFTs in detector order,
@@ -247,7 +268,9 @@ int fstat_test_ring_stall(fstat_ctx *ctx, int32_t after_sft);
 /* Tile configuration chosen for the current bank (after fstat_set_templates):
  * out[8] = (P, L, M, warps, sft_chunk, lane-groups per column row,
  *           staged pairs per SFT, kernel variant id; ids 100..111 are the
- *           far-field polynomial form, 112..115 the sinc-polynomial form). */
+ *           far-field polynomial form, 112..115 the sinc-polynomial form,
+ *           116 the sinc and 117 the far-field form with frequency coverage;
+ *           107 and up use the TMA-ring staging). */
 int fstat_get_plan(fstat_ctx *ctx, int32_t *out);
 
 /* Number of CUDA kernels this context has launched since it was created. */

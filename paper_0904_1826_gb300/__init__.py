@@ -78,6 +78,7 @@ SIGNATURES = {
     "fstat_get_plan": (ctypes.c_int, [_P, _P]),
     "fstat_test_ring_stall": (ctypes.c_int, [_P, _I32]),
     "fstat_set_noise_floor": (ctypes.c_int, [_P, _I32]),
+    "fstat_set_coverage": (ctypes.c_int, [_P, _P, _P, _I32]),
     "fstat_get_noise": (ctypes.c_int, [_P, _P, _P, _I32]),
     "fstat_get_launch_count": (ctypes.c_int, [_P, ctypes.POINTER(_I64)]),
     "fstat_take_kernel_time": (ctypes.c_int, [_P, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_I32)]),
@@ -257,6 +258,19 @@ def fstat_get_error_flags(ctx) -> int:
 
 def fstat_set_noise_floor(ctx, half_window: int) -> None:
     _check(ctx, _lib.fstat_set_noise_floor(ctx, int(half_window)))
+
+
+def fstat_set_coverage(ctx, j_lo=None, j_hi=None) -> None:
+    """Per-SFT frequency-index ranges [j_lo, j_hi) in SFT load order
+    (include/fstat.h); None, None switches coverage off."""
+    if j_lo is None and j_hi is None:
+        _check(ctx, _lib.fstat_set_coverage(ctx, None, None, 0))
+        return
+    lo = np.ascontiguousarray(j_lo, dtype=np.int32)
+    hi = np.ascontiguousarray(j_hi, dtype=np.int32)
+    if lo.shape != hi.shape or lo.ndim != 1:
+        raise ValueError("j_lo and j_hi must be equal-length 1-D arrays")
+    _check(ctx, _lib.fstat_set_coverage(ctx, _host_ptr(lo), _host_ptr(hi), int(lo.shape[0])))
 
 
 def fstat_get_noise(ctx, n_sft: int, n_bins: int):

@@ -46,11 +46,14 @@ struct FarRow {
     int M, L;
     int ring;   // compute warps of the TMA-ring staging (L = 2, uniform spindown grid), 0 = cp.async rounds
     bool sinc;  // sinc-polynomial form (whole window as one polynomial), else near pairs + far polynomial
+    bool cov;   // per-SFT frequency coverage compiled in (ring only; single launches)
 };
-const FarRow kFarVariants[] = {{7, 2, 0, false},  {5, 2, 0, false},  {9, 2, 0, false},  {7, 1, 0, false},
-                               {9, 1, 0, false},  {5, 1, 0, false},  {1, 1, 0, false},  {5, 2, 8, false},
-                               {7, 2, 8, false},  {9, 2, 8, false},  {5, 2, 10, false}, {7, 2, 10, false},
-                               {5, 2, 10, true},  {7, 2, 10, true},  {5, 2, 8, true},   {7, 2, 8, true}};
+const FarRow kFarVariants[] = {{7, 2, 0, false, false},  {5, 2, 0, false, false},  {9, 2, 0, false, false},
+                               {7, 1, 0, false, false},  {9, 1, 0, false, false},  {5, 1, 0, false, false},
+                               {1, 1, 0, false, false},  {5, 2, 8, false, false},  {7, 2, 8, false, false},
+                               {9, 2, 8, false, false},  {5, 2, 10, false, false}, {7, 2, 10, false, false},
+                               {5, 2, 10, true, false},  {7, 2, 10, true, false},  {5, 2, 8, true, false},
+                               {7, 2, 8, true, false},   {5, 2, 10, true, true},   {5, 2, 10, false, true}};
 constexpr int kNumFar = sizeof(kFarVariants) / sizeof(kFarVariants[0]);
 constexpr int kFarIdBase = 100;   // variant ids reported for the far-field form
 
@@ -93,6 +96,11 @@ struct fstat_ctx {
     float* d_floor = nullptr;       // noise floor S [n_sft][n_bins]
     double* d_sbar = nullptr;       // mean floor per SFT
     double* d_weight = nullptr;     // noise weight per SFT
+    // per-SFT frequency coverage (fstat_set_coverage)
+    bool have_cov = false;
+    int2* d_cov = nullptr;          // [n_sft] frequency-index range [x, y)
+    float4* d_comb_j = nullptr;     // [n_sky][n_f] combine weights per frequency
+    size_t cap_comb_j = 0;
     // stack-slide scratch (held by the first segment of a call)
     SlideSeg* d_slide_seg = nullptr;
     long long* d_slide_A = nullptr;
@@ -374,7 +382,9 @@ bool make_far_plan(fstat_ctx* c, int P, int L, bool found, Plan& best) {
         for (int M_ : Mr) {
             int fid = -1;
             for (int i = 0; i < kNumFar; ++i)
-                if (kFarVariants[i].ring == nwc && kFarVariants[i].M == M_ && kFarVariants[i].sinc == want_sinc) fid = i;
+                if (kFarVariants[i].ring == nwc && kFarVariants[i].M == M_ && kFarVariants[i].sinc == want_sinc &&
+                    kFarVariants[i].cov == c->have_cov)
+                    fid = i;
             if (fid < 0) continue;
             const int PM = P * M_;
             const int lg_cta = 32 * nwc / P;
@@ -431,6 +441,7 @@ bool make_far_plan(fstat_ctx* c, int P, int L, bool found, Plan& best) {
         }
         if (have_ring) return true;
     }
+    if (c->have_cov) return false;   // the rounds staging has no coverage path
     std::vector<int> Ms;
     // M = 5 measured fastest on GB300 (the wider tiles give up round size to
     // shared memory); the autotuner also tries 7 and 9
@@ -786,7 +797,7 @@ void fstat_destroy(fstat_ctx* c) {
                     c->d_fdot, c->d_meta, c->d_kh0, c->d_ph0, c->d_abcd, c->d_comb, c->d_twoF, c->d_err,
                     c->tw.hist, c->tw.state, c->tw.tie_count, c->tw.cand_idx, c->tw.cand_val, c->tw.n_cand,
                     c->tw.out_idx, c->tw.out_val, c->d_inj_work, c->d_sig, c->d_ptab, c->d_pcoef,
-                    c->d_bins_w, c->d_floor, c->d_sbar, c->d_weight, c->d_slide_seg, c->d_slide_A,
+                    c->d_bins_w, c->d_floor, c->d_sbar, c->d_weight, c->d_cov, c->d_comb_j, c->d_slide_seg, c->d_slide_A,
                     c->d_slide_B, c->d_slide_out};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -800,6 +811,34 @@ void fstat_destroy(fstat_ctx* c) {
 }
 
 const char* fstat_last_error(const fstat_ctx* c) { return c ? c->err.c_str() : ""; }
+
+int fstat_set_coverage(fstat_ctx* c, const int32_t* j_lo, const int32_t* j_hi, int32_t n_sft) {
+    if (!c) return FSTAT_EINVAL;
+    c->err.clear();
+    if (!j_lo && !j_hi) {
+        c->have_cov = false;
+        c->plan_valid = false;
+        c->computed = false;
+        return FSTAT_OK;
+    }
+    if (!j_lo || !j_hi) return fail(c, FSTAT_EINVAL, "j_lo and j_hi must both be given or both be null");
+    if (!c->have_sfts) return fail(c, FSTAT_ESTATE, "load SFTs first");
+    if (n_sft != c->n_sft) return fail(c, FSTAT_EINVAL, "n_sft %d != loaded SFTs %d", n_sft, c->n_sft);
+    std::vector<int2> h(n_sft);
+    for (int i = 0; i < n_sft; ++i) {
+        if (j_lo[i] > j_hi[i]) return fail(c, FSTAT_EINVAL, "SFT %d: j_lo > j_hi", i);
+        h[i] = make_int2(j_lo[i], j_hi[i]);
+    }
+    if (set_device(c) != FSTAT_OK) return FSTAT_ECUDA;
+    if (c->d_cov) cudaFree(c->d_cov);
+    c->d_cov = nullptr;
+    CUDA_TRY(c, cudaMalloc(&c->d_cov, (size_t)n_sft * sizeof(int2)));
+    CUDA_TRY(c, cudaMemcpy(c->d_cov, h.data(), (size_t)n_sft * sizeof(int2), cudaMemcpyHostToDevice));
+    c->have_cov = true;
+    c->plan_valid = false;
+    c->computed = false;
+    return FSTAT_OK;
+}
 
 int fstat_stackslide(fstat_ctx* const* seg, int32_t n_seg, double f0, double df, int32_t n_f, double t_ref,
                      float* out, int64_t* n_outside, void* cuda_stream) {
@@ -969,6 +1008,7 @@ int fstat_set_sfts(fstat_ctx* c, int32_t det_index, const fstat_detector* det, d
     c->sft_dirty = true;
     c->plan_valid = false;
     c->computed = false;
+    c->have_cov = false;   // coverage is per SFT index: a new SFT set clears it
     return FSTAT_OK;
 }
 
@@ -1041,6 +1081,10 @@ int prepare(fstat_ctx* c, cudaStream_t s) {
     if ((rc = grow(c, &c->d_comb, c->cap_comb, (size_t)c->n_sky)) != FSTAT_OK) return rc;
     if ((rc = grow(c, &c->d_twoF, c->cap_twoF, n_twoF)) != FSTAT_OK) return rc;
     if ((rc = ensure_topk(c)) != FSTAT_OK) return rc;
+    if (c->have_cov) {
+        if (c->n_f > kCovMaxF) return fail(c, FSTAT_EINVAL, "coverage supports at most %d frequencies", kCovMaxF);
+        if ((rc = grow(c, &c->d_comb_j, c->cap_comb_j, (size_t)c->n_sky * c->n_f)) != FSTAT_OK) return rc;
+    }
     return ensure_tables(c, s);
 }
 
@@ -1129,6 +1173,8 @@ DirichletParams dirichlet_params(const fstat_ctx* c) {
     dp.sft_chunk = pl.C;
     dp.err = c->d_err;
     dp.ring_stop = c->ring_stall;
+    dp.cov = c->have_cov ? c->d_cov : nullptr;
+    dp.comb_j = c->have_cov ? c->d_comb_j : nullptr;
     if (pl.far) {
         dp.ptab = c->d_ptab;
         dp.pcoef = c->d_pcoef;
@@ -1187,6 +1233,10 @@ int fstat_compute(fstat_ctx* c, void* cuda_stream) {
     const int slot = c->n_timed % kTimedRing;
     CUDA_TRY(c, cudaEventRecord(c->ev_a[slot], s));
     CUDA_TRY(c, launch_timing(timing_params(c, c->n_sky), s));
+    if (c->have_cov) {
+        CUDA_TRY(c, launch_coverage_comb(timing_params(c, c->n_sky), c->d_cov, c->n_f, c->d_comb_j, s));
+        c->launches += 1;
+    }
     CUDA_TRY(c, cudaEventRecord(c->ev_b[slot], s));
     cudaError_t e = launch_dir(c, dirichlet_params(c), c->plan.grid, s);
     if (e != cudaSuccess) return fail(c, FSTAT_ECUDA, "Dirichlet launch: %s", cudaGetErrorString(e));

@@ -328,13 +328,24 @@ __device__ __forceinline__ void dirichlet_block(const DirichletParams& p, const 
                 kh_row = s_kh0[(cslot * C + c) * p.n_fdot + row_i];
                 ph0 = s_ph0[(cslot * C + c) * p.n_fdot + row_i];
             }
+            // frequency coverage: skip the SFT if it covers none of the
+            // thread's templates, mask per template if it covers some
+            int clo = 0, chi = 0x7fffffff;
+            if (p.cov) {
+                const int2 cv = __ldg(p.cov + a0 + c);
+                clo = cv.x;
+                chi = cv.y;
+            }
+            const int j_last = j_t + (M - 1) * p.P;
+            if (j_last < clo || j_t >= chi) continue;
+            const bool part = j_t < clo || j_last >= chi;
             const long long kh = kh_row + (long long)j_t * m.dk;
             const int k0 = (int)(kh >> 32);
             const int lo_rel = s_lo[(lslot * C + c) * 2];
             const int b = (k0 - (int)p.k_lo) - (D - 1) - lo_rel;   // first pair of template 0
             const float4* tab = s_tab + (size_t)c * p.w_tab;
             const float2 a2 = make_float2(m.a, m.a), b2 = make_float2(m.b, m.b);
-            const bool fast = ((int)((kh + m.span) >> 32) == k0 + (M - 1) * L);
+            const bool fast = !part && ((int)((kh + m.span) >> 32) == k0 + (M - 1) * L);
             if (fast) {
                 int bb = b;
                 if (bb < 0 || bb + (M - 1) * L + 2 * (D - 1) >= p.w_pairs) {
@@ -364,6 +375,7 @@ __device__ __forceinline__ void dirichlet_block(const DirichletParams& p, const 
                 const long long pdk = (long long)p.P * m.dk;
 #pragma unroll
                 for (int q = 0; q < M; ++q) {
+                    if (part && (j_t + q * p.P < clo || j_t + q * p.P >= chi)) continue;
                     const long long khq = kh + (long long)q * pdk;
                     const int k0q = (int)(khq >> 32);
                     const float kap = clamp_kappa(frac_to_float((unsigned int)khq));
@@ -402,10 +414,11 @@ __device__ __forceinline__ void dirichlet_block(const DirichletParams& p, const 
     for (int q = 0; q < M; ++q) {
         const int j = j_t + q * p.P;
         if (j < j_end) {
+            const float4 cw = p.comb_j ? p.comb_j[(size_t)sky * p.n_f + j] : cm;
             const float2 A_ = KAHAN ? ta[q] : fa[q];
             const float2 B_ = KAHAN ? tb[q] : fb[q];
-            const float v = cm.x * fmaf(A_.x, A_.x, A_.y * A_.y) + cm.y * fmaf(B_.x, B_.x, B_.y * B_.y) +
-                            cm.z * fmaf(A_.x, B_.x, A_.y * B_.y);
+            const float v = cw.x * fmaf(A_.x, A_.x, A_.y * A_.y) + cw.y * fmaf(B_.x, B_.x, B_.y * B_.y) +
+                            cw.z * fmaf(A_.x, B_.x, A_.y * B_.y);
             out[j] = fmaxf(v, 0.0f);
         }
     }

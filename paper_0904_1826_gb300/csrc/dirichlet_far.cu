@@ -32,6 +32,8 @@
 //    compute warps run up to S SFTs apart and never meet at a block barrier.
 // Blocks are ordered sky-fastest inside a column: the blocks resident at one
 // time read the same column slice of the tables, which stays in L2.
+#include <type_traits>
+
 #include "dirichlet.cuh"
 
 namespace fs {
@@ -109,11 +111,14 @@ __device__ __forceinline__ float2 far_window_sum(const float4* __restrict__ pn, 
 // cf + plane4 that of the half kappa >= 1/2, both parity-split for L = 2.
 // P already carries sin(pi kappa)/2, so the template's term is the twiddle
 // times P, with no reciprocal, sine or clamp.
-template <int M, int L>
+template <int M, int L, bool COV>
 __device__ __forceinline__ void sinc_sft(const DirichletParams& p, const SkySftMeta& m, long long kh_row,
                                          unsigned int ph0, int lo_rel, const float4* __restrict__ cf, int plane4,
-                                         int half, int j_t, float2 (&fa)[M], float2 (&fb)[M]) {
+                                         int half, int j_t, int clo, int chi, float2 (&fa)[M], float2 (&fb)[M]) {
     constexpr int D = 8;
+    const bool part = COV && (j_t < clo || j_t + (M - 1) * p.P >= chi);   // coverage holds some templates only
+    // template q counts for this SFT (always, without coverage)
+    auto covered = [&](int q) { return !COV || !part || (j_t + q * p.P >= clo && j_t + q * p.P < chi); };
     const long long kh = kh_row + (long long)j_t * m.dk;
     const int k0 = (int)(kh >> 32);
     const int b = (k0 - (int)p.k_lo) - (D - 1) - lo_rel;
@@ -132,8 +137,11 @@ __device__ __forceinline__ void sinc_sft(const DirichletParams& p, const SkySftM
         const bool up = u >= 0.f;
         return horner(cf + (up ? plane4 : 0) + 3 * pos, u + (up ? -0.25f : 0.25f));
     };
-    auto add = [&](float tw_re, float tw_im, float2 P, float2& fa_q, float2& fb_q) {
-        const float2 z = make_float2(fmaf(tw_re, P.x, -tw_im * P.y), fmaf(tw_re, P.y, tw_im * P.x));
+    // use = false (a template outside the SFT's coverage) adds zero: a select,
+    // not a branch, so partially covered threads stay on the common path
+    auto add = [&](float tw_re, float tw_im, float2 P, float2& fa_q, float2& fb_q, bool use) {
+        float2 z = make_float2(fmaf(tw_re, P.x, -tw_im * P.y), fmaf(tw_re, P.y, tw_im * P.x));
+        if (COV) z = use ? z : make_float2(0.f, 0.f);
         fa_q = __ffma2_rn(a2, z, fa_q);
         fb_q = __ffma2_rn(b2, z, fb_q);
     };
@@ -150,37 +158,48 @@ __device__ __forceinline__ void sinc_sft(const DirichletParams& p, const SkySftM
         __sincosf((float)(int)ph * kPhaseToRad, &sn, &cs);
         float tw_re = cs, tw_im = -sn;
         const float u0 = frac_to_float((unsigned int)kh) - 0.5f;
-        if (fabsf(m.eps) * (float)(M - 1) <= kSincSlack) {
-            // kappa drifts by at most kSincSlack over the M templates: one half
-            // bin, chosen at the middle template, serves all of them (at most
-            // kSincSlack / 2 outside it, where the interpolant still holds)
-            const bool up = fmaf(0.5f * (float)(M - 1), m.eps, u0) >= 0.f;
-            const float4* cq = cf + (up ? plane4 : 0) + 3 * pos0;
-            const float v0 = u0 + (up ? -0.25f : 0.25f);
+        // partially covered threads (coverage edges) take a copy of the loops
+        // that zeroes the uncovered templates; everyone else runs them as is
+        auto loops = [&](auto masked) {
+            constexpr bool MK = decltype(masked)::value;
+            float tr = tw_re, ti = tw_im;
+            if (fabsf(m.eps) * (float)(M - 1) <= kSincSlack) {
+                // kappa drifts by at most kSincSlack over the M templates: one half
+                // bin, chosen at the middle template, serves all of them (at most
+                // kSincSlack / 2 outside it, where the interpolant still holds)
+                const bool up = fmaf(0.5f * (float)(M - 1), m.eps, u0) >= 0.f;
+                const float4* cq = cf + (up ? plane4 : 0) + 3 * pos0;
+                const float v0 = u0 + (up ? -0.25f : 0.25f);
 #pragma unroll
-            for (int q = 0; q < M; ++q) {
-                add(tw_re, tw_im, horner(cq + 3 * q, fmaf((float)q, m.eps, v0)), fa[q], fb[q]);
-                if (q + 1 < M) {
-                    const float t = fmaf(tw_re, m.rot_re, -tw_im * m.rot_im);
-                    tw_im = fmaf(tw_re, m.rot_im, tw_im * m.rot_re);
-                    tw_re = t;
+                for (int q = 0; q < M; ++q) {
+                    add(tr, ti, horner(cq + 3 * q, fmaf((float)q, m.eps, v0)), fa[q], fb[q], !MK || covered(q));
+                    if (q + 1 < M) {
+                        const float t = fmaf(tr, m.rot_re, -ti * m.rot_im);
+                        ti = fmaf(tr, m.rot_im, ti * m.rot_re);
+                        tr = t;
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < M; ++q) {
+                    add(tr, ti, poly(pos0 + q, fmaf((float)q, m.eps, u0)), fa[q], fb[q], !MK || covered(q));
+                    if (q + 1 < M) {
+                        const float t = fmaf(tr, m.rot_re, -ti * m.rot_im);
+                        ti = fmaf(tr, m.rot_im, ti * m.rot_re);
+                        tr = t;
+                    }
                 }
             }
-        } else {
-#pragma unroll
-            for (int q = 0; q < M; ++q) {
-                add(tw_re, tw_im, poly(pos0 + q, fmaf((float)q, m.eps, u0)), fa[q], fb[q]);
-                if (q + 1 < M) {
-                    const float t = fmaf(tw_re, m.rot_re, -tw_im * m.rot_im);
-                    tw_im = fmaf(tw_re, m.rot_im, tw_im * m.rot_re);
-                    tw_re = t;
-                }
-            }
-        }
+        };
+        if (COV && part)
+            loops(std::true_type{});
+        else
+            loops(std::false_type{});
     } else {
         const long long pdk = (long long)p.P * m.dk;
 #pragma unroll
         for (int q = 0; q < M; ++q) {
+            if (!covered(q)) continue;
             const long long khq = kh + (long long)q * pdk;
             const int k0q = (int)(khq >> 32);
             const unsigned int phq = ph0 + (unsigned int)(j_t + q * p.P) * m.dphi + ((unsigned int)k0q << 31);
@@ -191,7 +210,7 @@ __device__ __forceinline__ void sinc_sft(const DirichletParams& p, const SkySftM
                 atomicOr(p.err, 1);
                 bq = max(0, min(bq, p.w_pairs - 1 - 2 * (D - 1)));
             }
-            add(c2, -s2, poly(tab_pos<L>(bq + 7, half), frac_to_float((unsigned int)khq) - 0.5f), fa[q], fb[q]);
+            add(c2, -s2, poly(tab_pos<L>(bq + 7, half), frac_to_float((unsigned int)khq) - 0.5f), fa[q], fb[q], true);
         }
     }
 }
@@ -241,13 +260,16 @@ __global__ void __launch_bounds__(256) sinc_tables_kernel(const typename RawT<FO
 // and phase bases of the thread's spindown row, lo_rel the bin of the staged
 // rows' entry 0 relative to k_lo, tab / cf the staged pair and coefficient
 // rows (parity-split for L = 2).
-template <int M, int L>
+template <int M, int L, bool COV>
 __device__ __forceinline__ void far_sft(const DirichletParams& p, const SkySftMeta& m, long long kh_row,
                                         unsigned int ph0, int lo_rel, const float4* __restrict__ tab,
-                                        const float4* __restrict__ cf, int half, int j_t, float2 (&fa)[M],
-                                        float2 (&fb)[M]) {
+                                        const float4* __restrict__ cf, int half, int j_t, int clo, int chi,
+                                        float2 (&fa)[M], float2 (&fb)[M]) {
     constexpr int D = 8;
     constexpr int STRIDE = (L == 2) ? 1 : 2;
+    const bool part = COV && (j_t < clo || j_t + (M - 1) * p.P >= chi);   // coverage holds some templates only
+    // template q counts for this SFT (always, without coverage)
+    auto covered = [&](int q) { return !COV || !part || (j_t + q * p.P >= clo && j_t + q * p.P < chi); };
     const long long kh = kh_row + (long long)j_t * m.dk;
     const int k0 = (int)(kh >> 32);
     const int b = (k0 - (int)p.k_lo) - (D - 1) - lo_rel;   // first pair of template 0
@@ -270,7 +292,7 @@ __device__ __forceinline__ void far_sft(const DirichletParams& p, const SkySftMe
         for (int q = 0; q < M; ++q) {
             const float kap = clamp_kappa(fmaf((float)q, m.eps, kap0));
             const float2 Q = far_window_sum<STRIDE>(pn + q, cp + 3 * q, kap);
-            accumulate(tw_re, tw_im, sinpi_unit(kap), Q, a2, b2, fa[q], fb[q]);
+            if (covered(q)) accumulate(tw_re, tw_im, sinpi_unit(kap), Q, a2, b2, fa[q], fb[q]);
             if (q + 1 < M) {
                 const float t = fmaf(tw_re, m.rot_re, -tw_im * m.rot_im);
                 tw_im = fmaf(tw_re, m.rot_im, tw_im * m.rot_re);
@@ -281,6 +303,7 @@ __device__ __forceinline__ void far_sft(const DirichletParams& p, const SkySftMe
         const long long pdk = (long long)p.P * m.dk;
 #pragma unroll
         for (int q = 0; q < M; ++q) {
+            if (!covered(q)) continue;
             const long long khq = kh + (long long)q * pdk;
             const int k0q = (int)(khq >> 32);
             const float kap = clamp_kappa(frac_to_float((unsigned int)khq));
@@ -309,9 +332,10 @@ __device__ __forceinline__ void far_store(const DirichletParams& p, int sky, int
     for (int q = 0; q < M; ++q) {
         const int j = j_t + q * p.P;
         if (j < j_end) {
+            const float4 cw = p.comb_j ? p.comb_j[(size_t)sky * p.n_f + j] : cm;
             const float2 A_ = fa[q], B_ = fb[q];
-            const float v = cm.x * fmaf(A_.x, A_.x, A_.y * A_.y) + cm.y * fmaf(B_.x, B_.x, B_.y * B_.y) +
-                            cm.z * fmaf(A_.x, B_.x, A_.y * B_.y);
+            const float v = cw.x * fmaf(A_.x, A_.x, A_.y * A_.y) + cw.y * fmaf(B_.x, B_.x, B_.y * B_.y) +
+                            cw.z * fmaf(A_.x, B_.x, A_.y * B_.y);
             out[j] = fmaxf(v, 0.0f);
         }
     }
@@ -445,8 +469,8 @@ __device__ __forceinline__ void far_block(const DirichletParams& p, long long bi
                 kh_row = s_kh0[(cslot * C + c) * p.n_fdot + row_i];
                 ph0 = s_ph0[(cslot * C + c) * p.n_fdot + row_i];
             }
-            far_sft<M, L>(p, m, kh_row, ph0, lo_of(m), s_pair + ((size_t)slot * C + c) * p.w_tab,
-                          s_coef + ((size_t)slot * C + c) * 3 * p.w_tab, half, j_t, fa, fb);
+            far_sft<M, L, false>(p, m, kh_row, ph0, lo_of(m), s_pair + ((size_t)slot * C + c) * p.w_tab,
+                          s_coef + ((size_t)slot * C + c) * 3 * p.w_tab, half, j_t, 0, 0x7fffffff, fa, fb);
         }
     }
     if (active) far_store<M>(p, sky, drow, j_t, j_col0 + width, fa, fb);
@@ -515,7 +539,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
 
 // L = 2, uniform spindown grid.  Warps 0..NW-1 compute, warp NW produces.
 // Error flag bit 2: a pipeline wait gave up (results of the block invalid).
-template <int M, bool SINC>
+template <int M, bool SINC, bool COV>
 __device__ __forceinline__ void far_ring_block(const DirichletParams& p, long long bid, unsigned char* smem) {
     constexpr int D = 8, L = 2;
     const int S = p.sft_chunk;
@@ -579,6 +603,8 @@ __device__ __forceinline__ void far_ring_block(const DirichletParams& p, long lo
         const int n_issue = p.ring_stop >= 0 ? min(p.ring_stop, p.n_sft) : p.n_sft;
         for (int a0 = 0; a0 < n_issue && !stop; a0 += 32) {
             int x_lane = 0;
+            int2 cv_lane = make_int2(0, 0x7fffffff);
+            if (COV && a0 + lane < p.n_sft) cv_lane = p.cov[a0 + lane];
             if (a0 + lane < p.n_sft) {
                 const SkySftMeta* gm = p.meta + meta0 + a0 + lane;
                 x_lane = (int)(((gm->khmin + (long long)j_col0 * gm->dk) >> 32) - p.k_lo) - (D - 1) + p.xoff;
@@ -586,6 +612,8 @@ __device__ __forceinline__ void far_ring_block(const DirichletParams& p, long lo
             const int n_here = min(32, n_issue - a0);
             for (int j = 0; j < n_here; ++j) {
                 int x0 = __shfl_sync(0xffffffffu, x_lane, j);
+                const int clo = __shfl_sync(0xffffffffu, cv_lane.x, j);
+                const int chi = __shfl_sync(0xffffffffu, cv_lane.y, j);
                 if (lane == 0) {
                     a = a0 + j;
                     if (a >= S && !mbar_wait<128>(empty_bar(pslot), pparity)) {
@@ -600,7 +628,7 @@ __device__ __forceinline__ void far_ring_block(const DirichletParams& p, long lo
                             x0 = max(0, min(x0, p.n_pos - p.w_pairs));
                         }
                         unsigned char* st = smem + (size_t)pslot * lay.stage;
-                        *reinterpret_cast<int*>(st + lay.lo) = x0 - p.xoff;
+                        *reinterpret_cast<int4*>(st + lay.lo) = make_int4(x0 - p.xoff, 0, clo, chi);
                         const uint32_t ss = sb + (uint32_t)((size_t)pslot * lay.stage);
                         const uint32_t fb = full_bar(pslot);
                         mbar_expect_tx(fb, bytes);
@@ -653,17 +681,25 @@ __device__ __forceinline__ void far_ring_block(const DirichletParams& p, long lo
                 break;
             }
             if (warp_live) {
-                const SkySftMeta m = *reinterpret_cast<const SkySftMeta*>(st + lay.meta);
-                const SkySftBase bs = *reinterpret_cast<const SkySftBase*>(st + lay.base);
-                const int lo_rel = *reinterpret_cast<const int*>(st + lay.lo);
-                if (SINC)
-                    sinc_sft<M, L>(p, m, bs.kh0 + (long long)drow * bs.dkh, bs.ph0 + (unsigned int)drow * bs.dph,
-                                   lo_rel, reinterpret_cast<const float4*>(st + lay.coef), (int)(lay.plane >> 4), half,
-                                   j_t, fa, fb);
-                else
-                    far_sft<M, L>(p, m, bs.kh0 + (long long)drow * bs.dkh, bs.ph0 + (unsigned int)drow * bs.dph,
-                                  lo_rel, reinterpret_cast<const float4*>(st + lay.pairs),
-                                  reinterpret_cast<const float4*>(st + lay.coef), half, j_t, fa, fb);
+                // window base; with coverage, the SFT's frequency-index range
+                const int4 lo4 = COV ? *reinterpret_cast<const int4*>(st + lay.lo)
+                                     : make_int4(*reinterpret_cast<const int*>(st + lay.lo), 0, 0, 0x7fffffff);
+                // skip an SFT whose coverage holds none of the thread's templates
+                if (!COV || (j_t + (M - 1) * p.P >= lo4.z && j_t < lo4.w)) {
+                    const SkySftMeta m = *reinterpret_cast<const SkySftMeta*>(st + lay.meta);
+                    const SkySftBase bs = *reinterpret_cast<const SkySftBase*>(st + lay.base);
+                    if (SINC)
+                        sinc_sft<M, L, COV>(p, m, bs.kh0 + (long long)drow * bs.dkh,
+                                            bs.ph0 + (unsigned int)drow * bs.dph, lo4.x,
+                                            reinterpret_cast<const float4*>(st + lay.coef), (int)(lay.plane >> 4),
+                                            half, j_t, lo4.z, lo4.w, fa, fb);
+                    else
+                        far_sft<M, L, COV>(p, m, bs.kh0 + (long long)drow * bs.dkh,
+                                           bs.ph0 + (unsigned int)drow * bs.dph, lo4.x,
+                                           reinterpret_cast<const float4*>(st + lay.pairs),
+                                           reinterpret_cast<const float4*>(st + lay.coef), half, j_t, lo4.z, lo4.w, fa,
+                                           fb);
+                }
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(empty_bar(slot));
@@ -692,10 +728,10 @@ __device__ __forceinline__ void far_ring_block(const DirichletParams& p, long lo
 }
 
 // NWC compute warps plus the producer; two resident blocks per SM.
-template <int M, int NWC, bool SINC>
+template <int M, int NWC, bool SINC, bool COV>
 __global__ void __launch_bounds__(32 * (NWC + 1), 2) dirichlet_far_ring_kernel(const DirichletParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
-    far_ring_block<M, SINC>(p, (long long)blockIdx.x, smem);
+    far_ring_block<M, SINC, COV>(p, (long long)blockIdx.x, smem);
 }
 
 // Persistent ring form over many template banks (workunits): every block
@@ -730,7 +766,7 @@ __global__ void __launch_bounds__(32 * (NWC + 1), 2)
         if (it >= total) break;
         const int w = s_wu;
         const DirichletParams p = banks[w];
-        far_ring_block<M, SINC>(p, it - item_prefix[w], smem);
+        far_ring_block<M, SINC, false>(p, it - item_prefix[w], smem);
         __syncthreads();
         if (threadIdx.x == 0) {
             __threadfence();
@@ -760,6 +796,10 @@ __global__ void __launch_bounds__(32 * (NWC + 1), 2)
     X(13, 7, 10, true)      \
     X(14, 5, 8, true)       \
     X(15, 7, 8, true)
+// the same kernels with per-SFT frequency coverage (single launches only)
+#define FS_RING_COV_VARIANTS(X) \
+    X(16, 5, 10, true)          \
+    X(17, 5, 10, false)
 
 cudaError_t launch_dirichlet_far(int v, const DirichletParams& p, int threads, size_t smem, long long grid,
                                  cudaStream_t s) {
@@ -774,15 +814,20 @@ cudaError_t launch_dirichlet_far(int v, const DirichletParams& p, int threads, s
     }
         FS_FAR_VARIANTS(FS_FCASE)
 #undef FS_FCASE
-#define FS_RCASE(ID, M_, W_, S_)                                                                          \
+#define FS_RCASE(ID, M_, W_, S_, C_)                                                                      \
     case ID: {                                                                                            \
-        auto fn = dirichlet_far_ring_kernel<M_, W_, S_>;                                                  \
+        auto fn = dirichlet_far_ring_kernel<M_, W_, S_, C_>;                                              \
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
         if (e != cudaSuccess) return e;                                                                   \
         fn<<<(unsigned)grid, threads, smem, s>>>(p);                                                      \
         return cudaGetLastError();                                                                        \
     }
-        FS_RING_VARIANTS(FS_RCASE)
+#define FS_RCASE_PLAIN(ID, M_, W_, S_) FS_RCASE(ID, M_, W_, S_, false)
+#define FS_RCASE_COV(ID, M_, W_, S_) FS_RCASE(ID, M_, W_, S_, true)
+        FS_RING_VARIANTS(FS_RCASE_PLAIN)
+        FS_RING_COV_VARIANTS(FS_RCASE_COV)
+#undef FS_RCASE_COV
+#undef FS_RCASE_PLAIN
 #undef FS_RCASE
         default:
             return cudaErrorInvalidValue;

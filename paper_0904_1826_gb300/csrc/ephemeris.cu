@@ -222,6 +222,86 @@ __global__ void __launch_bounds__(kTimingBlock) timing_kernel(const TimingParams
     }
 }
 
+// Per-frequency A, B, C of one sky point over the SFTs whose coverage
+// [x, y) holds the frequency index: a^2, b^2, ab of each SFT (with its noise
+// weight) in 2^-36 fixed point go into difference arrays at x and y (integer
+// atomics: exact and order-free), a prefix over j gives A, B, C per j, and
+// from them the combine weights.  A frequency no SFT covers gets zero weights
+// (2F = 0) without a flag; any other degenerate D raises flag bit 1.
+constexpr double kCovScale = 68719476736.0;   // 2^36
+
+__global__ void __launch_bounds__(kTimingBlock) coverage_comb_kernel(const TimingParams p, const int2* __restrict__ cov,
+                                                                     int n_f, float4* __restrict__ comb_j) {
+    extern __shared__ unsigned long long cdiff[];   // [3][n_f + 1]
+    __shared__ unsigned long long tot[3][kTimingBlock];
+    const int sky = blockIdx.x;
+    const int n1 = n_f + 1;
+    for (int t = threadIdx.x; t < 3 * n1; t += kTimingBlock) cdiff[t] = 0ull;
+    __syncthreads();
+    const SkyFrame fr = sky_frame(p.sky[2 * sky], p.sky[2 * sky + 1]);
+    for (int i = threadIdx.x; i < p.n_sft; i += kTimingBlock) {
+        const int2 c = cov[i];
+        const int lo = max(0, min(c.x, n_f)), hi = max(0, min(c.y, n_f));
+        if (lo >= hi) continue;
+        double dtau, tdot, a, b;
+        timing_antenna(p.st[i], fr, p.t_ref, dtau, tdot, a, b);
+        if (p.weight) {
+            const double sw = sqrt(p.weight[i]);
+            a *= sw;
+            b *= sw;
+        }
+        const unsigned long long q[3] = {(unsigned long long)llrint(a * a * kCovScale),
+                                         (unsigned long long)llrint(b * b * kCovScale),
+                                         (unsigned long long)llrint(a * b * kCovScale)};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            atomicAdd(&cdiff[k * n1 + lo], q[k]);
+            atomicAdd(&cdiff[k * n1 + hi], 0ull - q[k]);
+        }
+    }
+    __syncthreads();
+    // inclusive prefix over j: each thread scans a contiguous run, then the
+    // runs' totals are scanned by thread 0
+    const int run = (n1 + kTimingBlock - 1) / kTimingBlock;
+    const int j0 = threadIdx.x * run, j1 = min(n1, j0 + run);
+    unsigned long long sum[3] = {0ull, 0ull, 0ull};
+    for (int j = j0; j < j1; ++j)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) sum[k] += cdiff[k * n1 + j];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) tot[k][threadIdx.x] = sum[k];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long acc[3] = {0ull, 0ull, 0ull};
+        for (int t = 0; t < kTimingBlock; ++t)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const unsigned long long v = tot[k][t];
+                tot[k][t] = acc[k];
+                acc[k] += v;
+            }
+    }
+    __syncthreads();
+    unsigned long long run_sum[3] = {tot[0][threadIdx.x], tot[1][threadIdx.x], tot[2][threadIdx.x]};
+    bool degenerate = false;
+    for (int j = j0; j < j1 && j < n_f; ++j) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) run_sum[k] += cdiff[k * n1 + j];
+        const long long ia = (long long)run_sum[0], ib = (long long)run_sum[1], ic = (long long)run_sum[2];
+        float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (ia != 0 || ib != 0) {
+            const double A = (double)ia / kCovScale, B = (double)ib / kCovScale, C = (double)ic / kCovScale;
+            const double D = A * B - C * C;
+            if (D > 1e-300 && D > 1e-13 * A * B)
+                w = make_float4((float)(2.0 * B / D), (float)(2.0 * A / D), (float)(-4.0 * C / D), 1.f);
+            else
+                degenerate = true;
+        }
+        comb_j[(size_t)sky * n_f + j] = w;
+    }
+    if (degenerate) atomicOr(p.err, 2);
+}
+
 __global__ void sft_timing_one_kernel(const SftState* __restrict__ st, int n_sft, double alpha,
                                       double delta, double t_ref, double* __restrict__ out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -406,5 +486,13 @@ cudaError_t launch_quantize(const float2* src, long long row, int n_sft, int n_b
 }
 
 size_t inject_work_doubles(int n_sig, int n_sft) { return (size_t)n_sig * (kInjHead + 4 * (size_t)n_sft); }
+
+cudaError_t launch_coverage_comb(const TimingParams& tp, const int2* cov, int n_f, float4* comb_j, cudaStream_t s) {
+    const size_t smem = 3 * (size_t)(n_f + 1) * sizeof(unsigned long long);
+    cudaError_t e = cudaFuncSetAttribute(coverage_comb_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    coverage_comb_kernel<<<tp.n_sky, kTimingBlock, smem, s>>>(tp, cov, n_f, comb_j);
+    return cudaGetLastError();
+}
 
 }  // namespace fs

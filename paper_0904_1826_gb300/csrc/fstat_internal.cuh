@@ -92,6 +92,8 @@ struct DirichletParams {
     int n_pos;                 // positions per SFT row
     int xoff;                  // position of bin k_lo
     int ring_stop;             // testing aid: the ring's copy warp stops after this many SFTs (< 0: never)
+    const int2* cov;           // [n_sft] frequency-index range [x, y) each SFT contributes to, or null (all)
+    const float4* comb_j;      // [n_sky][n_f] per-frequency combine weights with coverage, or null
 };
 
 // Far-field polynomial form (D = 8): the window's 12 bins at offsets -7..-2
@@ -273,5 +275,10 @@ struct SlideSeg {
 cudaError_t launch_stackslide(const SlideSeg* seg, int n_seg, const double* fdot, int n_fdot, double f0, double df,
                               double t_ref, long long* A_fx, long long* B_fx, bool prep, bool unit, long long n_rows,
                               int n_f, float* out, unsigned long long* n_outside, cudaStream_t s);
+
+// Per-(sky, frequency) combine weights over the SFTs covering each frequency
+// index (one block per sky point; n_f <= kCovMaxF).
+constexpr int kCovMaxF = 8192;
+cudaError_t launch_coverage_comb(const TimingParams& tp, const int2* cov, int n_f, float4* comb_j, cudaStream_t s);
 
 }  // namespace fs
