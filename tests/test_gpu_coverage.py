@@ -129,3 +129,38 @@ def test_coverage_errors(lib, case):
         assert g.error_flags() == 0
     finally:
         g.close()
+
+
+def test_coverage_with_noise_floor_and_weights(lib):
+    from oracle import noise_oracle as N
+    import tests.test_gpu_noise as TN
+    w, scaled, dets = TN._case(seed=33)
+    lo, hi = _ragged(w.n_sft_total, w.bank.n_f, 12)
+    ref = CO.compute_fstat_coverage(N.weighted_detectors(dets, TN.W), w.T, w.k_lo, w.dterms, w.bank, lo, hi).ravel()
+    g = lib.FStat(0, dterms=w.dterms, topk=10)
+    try:
+        g.load_workload(w, bins_override=scaled)
+        lib.fstat_set_noise_floor(g.ctx, TN.W)
+        lib.fstat_set_coverage(g.ctx, lo, hi)
+        g.compute()
+        got = g.twoF().astype(np.float64)
+        assert g.error_flags() == 0
+    finally:
+        g.close()
+    assert np.all(np.abs(got - ref) <= REL * ref + ABS)
+
+
+def test_coverage_rejects_bands_wider_than_its_limit(lib, case):
+    w, bins, _, _, _ = case
+    wide = dataclasses.replace(w.bank, n_f=8193, df=w.bank.df / 64)
+    g = lib.FStat(0, topk=10)
+    try:
+        g.load_workload(dataclasses.replace(w, bank=wide), bins_override=bins)
+        lib.fstat_set_coverage(g.ctx, np.zeros(w.n_sft_total, np.int32), np.full(w.n_sft_total, 10, np.int32))
+        with pytest.raises(lib.FstatError) as e:
+            g.compute()
+        assert e.value.code == lib.FSTAT_EINVAL
+        lib.fstat_set_coverage(g.ctx, None, None)   # without coverage the same bank computes
+        g.compute()
+    finally:
+        g.close()

@@ -44,7 +44,7 @@ def test_floor_and_weights_match_oracle(lib):
     np.testing.assert_allclose(wt, ref_w, rtol=1e-12)
 
 
-@pytest.mark.parametrize("algo", ["farpoly", "direct"])
+@pytest.mark.parametrize("algo", ["auto", "farpoly", "direct"])
 def test_weighted_2F_matches_oracle(lib, algo):
     w, scaled, dets = _case(seed=32)
     ref = O.compute_fstat_freq_band(N.weighted_detectors(dets, W), w.T, w.k_lo, w.dterms, w.bank).ravel()
