@@ -377,8 +377,12 @@ bool make_far_plan(fstat_ctx* c, int P, int L, bool found, Plan& best) {
         // M = 5 with 8 stages measured fastest on GB300 (1105 ms on the workunit; M = 7: 1139 ms)
         std::vector<int> Mr = {5};
         if (c->opts.tile_m > 0) Mr = {c->opts.tile_m};
-        const int nwc = c->opts.tile_warps ? c->opts.tile_warps - 1 : 10;   // the last warp produces
+        int nwc = c->opts.tile_warps ? c->opts.tile_warps - 1 : 10;   // the last warp produces
+        // every lane-group needs all P of its threads: P must divide the compute
+        // warps (P = 4 takes 8 compute warps unless the caller fixed them)
+        if (nwc % P != 0 && !c->opts.tile_warps && 8 % P == 0) nwc = 8;
         double best_r = 1e300;
+        if (nwc % P != 0) Mr.clear();
         for (int M_ : Mr) {
             int fid = -1;
             for (int i = 0; i < kNumFar; ++i)

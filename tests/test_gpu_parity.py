@@ -340,3 +340,18 @@ def test_ring_form_edges(lib, n_sft, n_f):
     assert out["plan"]["variant"] >= 107
     assert out["flags"] & 1 == 0
     _assert_parity(out["twoF"], ref, f"ring n_sft={n_sft} n_f={n_f}")
+
+
+@pytest.mark.parametrize("algo", ["sincpoly", "farpoly"])
+def test_ring_with_four_threads_per_lane_group_on_a_wide_bank(lib, algo):
+    """df = 1/(2T) gives P = 4 threads per lane-group; with enough lane-groups
+    per block every one of them must have all four threads (warps divisible
+    by P), else templates would go uncomputed."""
+    w = config_mid(df_bins=0.5, n_f=600, n_fdot=10, n_sky=2, n_bins=360)
+    bins = _oracle_bins(w)
+    ref = O.compute_fstat_freq_band(_dets(w, bins), w.T, w.k_lo, w.dterms, w.bank).ravel()
+    out = _gpu(lib, w, bins, algo=algo)
+    assert (out["plan"]["P"], out["plan"]["L"]) == (4, 2)
+    assert out["plan"]["variant"] >= 107 and (out["plan"]["warps"] - 1) % 4 == 0   # ring, 8 compute warps
+    assert out["flags"] == 0
+    _assert_parity(out["twoF"], ref, "P=4 wide bank")
