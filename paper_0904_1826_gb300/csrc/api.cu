@@ -448,8 +448,10 @@ bool make_far_plan(fstat_ctx* c, int P, int L, bool found, Plan& best) {
     if (c->have_cov) return false;   // the rounds staging has no coverage path
     std::vector<int> Ms;
     // M = 5 measured fastest on GB300 (the wider tiles give up round size to
-    // shared memory); the autotuner also tries 7 and 9
-    if (found) Ms = {5};
+    // shared memory); the autotuner also tries 7 and 9.  M = 1 competes in the
+    // cost model: on narrow bands with P = 8 (L = 1) an M = 5 lane-group spans
+    // 40 frequencies and most of a block's lanes would idle.
+    if (found) Ms = {5, 1};
     else Ms = {1};
     if (c->opts.tile_m > 0) Ms = {c->opts.tile_m};
     double best_cost = 1e300;
