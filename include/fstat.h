@@ -175,13 +175,15 @@ int fstat_compute(fstat_ctx *ctx, void *cuda_stream);
 
 /* Copy 2F of templates [offset, offset + count) to `out` (host or device per
  * `mem`), after synchronising the context's stream.  FP32.
- * Errors: ESTATE (nothing computed), EINVAL (range), ERANGE / ETIMEOUT if the
- * computation flagged an error. */
+ * Errors: ESTATE (nothing computed), EINVAL (range); ETIMEOUT (flag bit 2)
+ * or ERANGE (flag bit 0) if the computation raised that device flag, with
+ * `out` written all the same. */
 int fstat_get_2f(fstat_ctx *ctx, float *out, int64_t offset, int64_t count, int32_t mem);
 
 /* Copy the first k (<= topk) toplist entries, ordered by 2F descending then
  * template index ascending, to host arrays idx[k] and twoF[k].  Synchronises.
- * Errors: ESTATE, EINVAL (k out of range), ERANGE. */
+ * Errors: ESTATE, EINVAL (k out of range); ETIMEOUT / ERANGE as for
+ * fstat_get_2f, with the entries written all the same. */
 int fstat_get_toplist(fstat_ctx *ctx, int32_t k, int64_t *idx, float *twoF);
 
 /* Per-sky antenna-pattern sums of the last compute: out[n_sky][4] =

@@ -696,6 +696,17 @@ int sync_ctx(fstat_ctx* c) {
     return FSTAT_OK;
 }
 
+// After a synchronised read-back: the error code for the device flags of the
+// last compute (bit 2: a bounded wait gave up; bit 0: a window left the
+// staged range).  The outputs were written either way.
+int flag_status(fstat_ctx* c) {
+    int h = 0;
+    CUDA_TRY(c, cudaMemcpy(&h, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h & 4) return fail(c, FSTAT_ETIMEOUT, "a bounded device wait gave up: 2F of some blocks is invalid");
+    if (h & 1) return fail(c, FSTAT_ERANGE, "a template window left the staged SFT range (clamped)");
+    return FSTAT_OK;
+}
+
 // The bins the path reads: the whitened copy when the noise floor is on.
 const float2* work_bins(const fstat_ctx* c) { return c->nf_half > 0 ? c->d_bins_w : c->d_bins; }
 
@@ -1265,7 +1276,8 @@ int fstat_get_2f(fstat_ctx* c, float* out, int64_t offset, int64_t count, int32_
     CUDA_TRY(c, cudaMemcpyAsync(out, c->d_twoF + offset, (size_t)count * sizeof(float),
                                 mem == FSTAT_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                                 c->stream));
-    return sync_ctx(c);
+    const int rc = sync_ctx(c);
+    return rc != FSTAT_OK ? rc : flag_status(c);
 }
 
 int fstat_get_toplist(fstat_ctx* c, int32_t k, int64_t* idx, float* twoF) {
@@ -1280,7 +1292,8 @@ int fstat_get_toplist(fstat_ctx* c, int32_t k, int64_t* idx, float* twoF) {
         CUDA_TRY(c, cudaMemcpyAsync(idx, c->tw.out_idx, (size_t)k * sizeof(long long), cudaMemcpyDeviceToHost, c->stream));
         CUDA_TRY(c, cudaMemcpyAsync(twoF, c->tw.out_val, (size_t)k * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
     }
-    return sync_ctx(c);
+    const int rc = sync_ctx(c);
+    return rc != FSTAT_OK ? rc : flag_status(c);
 }
 
 int fstat_get_abcd(fstat_ctx* c, double* out) {

@@ -321,6 +321,9 @@ def test_ring_wait_timeout_is_reported_and_context_survives(lib):
         lib.fstat_test_ring_stall(g.ctx, 3)
         g.compute()
         assert g.error_flags() & 4
+        with pytest.raises(lib.FstatError) as e:   # reading the results reports it too
+            g.twoF()
+        assert e.value.code == lib.FSTAT_ETIMEOUT
         lib.fstat_test_ring_stall(g.ctx, -1)
         g.compute()
         assert g.error_flags() == 0
