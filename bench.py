@@ -624,8 +624,6 @@ def main():
                 "peak_note": "152 SM x 128 FP32 lanes x 2 flop x 2070 MHz (max SM clock)"}
     if clocks and clocks.get("sm_mhz"):
         roofline["frac_at_sampled_clock"] = achieved / (N_SM * FP32_LANES * 2 * clocks["sm_mhz"] * 1e6 / 1e12)
-    # the clock the power-capped cuBLAS loop of the peak measurement settled at
-    roofline["frac_at_1440_mhz"] = achieved / (N_SM * FP32_LANES * 2 * 1440.0 * 1e6 / 1e12)
     line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "step_ms": {"best": steps_ms[0], "median": steps_ms[len(steps_ms) // 2]} if steps_ms else None,
