@@ -91,7 +91,7 @@ def algo_of(variant: int) -> str:
     """Form of a plan's kernel variant id (include/fstat.h, fstat_get_plan)."""
     if variant < 100:
         return "direct"
-    return "sincpoly" if variant in (112, 113, 114, 115, 116) else "farpoly"
+    return "sincpoly" if variant in (112, 113, 114, 115, 116, 118, 119) else "farpoly"
 
 
 def kernel_hash(algo: str) -> str:

@@ -271,8 +271,9 @@ int fstat_test_ring_stall(fstat_ctx *ctx, int32_t after_sft);
  * out[8] = (P, L, M, warps, sft_chunk, lane-groups per column row,
  *           staged pairs per SFT, kernel variant id; ids 100..111 are the
  *           far-field polynomial form, 112..115 the sinc-polynomial form,
- *           116 the sinc and 117 the far-field form with frequency coverage;
- *           107 and up use the TMA-ring staging). */
+ *           116 the sinc and 117 the far-field form with frequency coverage,
+ *           118 and 119 the sinc form for L = 1 banks (P = 8); 107 and up use
+ *           the TMA-ring staging). */
 int fstat_get_plan(fstat_ctx *ctx, int32_t *out);
 
 /* Number of CUDA kernels this context has launched since it was created. */

@@ -53,7 +53,8 @@ const FarRow kFarVariants[] = {{7, 2, 0, false, false},  {5, 2, 0, false, false}
                                {1, 1, 0, false, false},  {5, 2, 8, false, false},  {7, 2, 8, false, false},
                                {9, 2, 8, false, false},  {5, 2, 10, false, false}, {7, 2, 10, false, false},
                                {5, 2, 10, true, false},  {7, 2, 10, true, false},  {5, 2, 8, true, false},
-                               {7, 2, 8, true, false},   {5, 2, 10, true, true},   {5, 2, 10, false, true}};
+                               {7, 2, 8, true, false},   {5, 2, 10, true, true},   {5, 2, 10, false, true},
+                               {5, 1, 8, true, false},   {1, 1, 8, true, false}};
 constexpr int kNumFar = sizeof(kFarVariants) / sizeof(kFarVariants[0]);
 constexpr int kFarIdBase = 100;   // variant ids reported for the far-field form
 
@@ -122,6 +123,7 @@ struct fstat_ctx {
     FarGamma gam{};                 // far-field interpolation weights
     SincGamma sgam{};               // sinc-polynomial interpolation weights
     bool tab_sinc = false;          // kind of the built tables
+    bool tab_split = true;          // sinc tables split by position parity (L = 2) or plain (L = 1)
     float4* d_ptab = nullptr;       // far-field pair table [n_sft][n_pos]
     float4* d_pcoef = nullptr;      // far-field coefficients [n_sft][4][n_pos]
     size_t cap_ptab = 0, cap_pcoef = 0;
@@ -373,9 +375,13 @@ bool make_far_plan(fstat_ctx* c, int P, int L, bool found, Plan& best) {
     // AUTO takes the sinc-polynomial form where the ring applies (1027 ms per
     // workunit launch on GB300 against 1105 ms for near pairs + far polynomial)
     const bool want_sinc = c->opts.algo == FSTAT_ALGO_SINCPOLY || c->opts.algo == FSTAT_ALGO_AUTO;
-    if (found && L == 2 && c->fdot_uniform && (c->opts.tile_warps == 0 || c->opts.tile_warps >= 9)) {
-        // M = 5 with 8 stages measured fastest on GB300 (1105 ms on the workunit; M = 7: 1139 ms)
+    // L = 1 (P = 8) runs the ring in the sinc form only, with plain tables
+    const bool ring_l = L == 2 || (L == 1 && want_sinc && !c->have_cov);
+    if (found && ring_l && c->fdot_uniform && (c->opts.tile_warps == 0 || c->opts.tile_warps >= 9)) {
+        // M = 5 with 8 stages measured fastest on GB300 (1105 ms on the workunit; M = 7: 1139 ms).
+        // For L = 1, M = 1 competes: narrow banks leave an M = 5 lane-group's lanes idle.
         std::vector<int> Mr = {5};
+        if (L == 1) Mr = {5, 1};
         if (c->opts.tile_m > 0) Mr = {c->opts.tile_m};
         int nwc = c->opts.tile_warps ? c->opts.tile_warps - 1 : 10;   // the last warp produces
         // every lane-group needs all P of its threads: P must divide the compute
@@ -386,8 +392,8 @@ bool make_far_plan(fstat_ctx* c, int P, int L, bool found, Plan& best) {
         for (int M_ : Mr) {
             int fid = -1;
             for (int i = 0; i < kNumFar; ++i)
-                if (kFarVariants[i].ring == nwc && kFarVariants[i].M == M_ && kFarVariants[i].sinc == want_sinc &&
-                    kFarVariants[i].cov == c->have_cov)
+                if (kFarVariants[i].ring == nwc && kFarVariants[i].M == M_ && kFarVariants[i].L == L &&
+                    kFarVariants[i].sinc == want_sinc && kFarVariants[i].cov == c->have_cov)
                     fid = i;
             if (fid < 0) continue;
             const int PM = P * M_;
@@ -396,10 +402,10 @@ bool make_far_plan(fstat_ctx* c, int P, int L, bool found, Plan& best) {
             for (int lg_row = 1; lg_row <= lg_max; ++lg_row) {
                 const int col_w = lg_row * PM;
                 const int n_col = (c->n_f + col_w - 1) / col_w;
-                const int w_pairs = std::max(pairs_needed(c, col_w, 8), (M_ - 1) * 2 + 2 * 8 + 2);
+                const int w_pairs = std::max(pairs_needed(c, col_w, 8), (M_ - 1) * L + 2 * 8 + 2);
                 int hf = (w_pairs + 1) / 2;
                 hf += ((4 - hf % 8) + 8) % 8;
-                const int w_tab = 2 * hf;
+                const int w_tab = L == 2 ? 2 * hf : w_pairs;
                 int S = c->opts.sft_chunk > 0 ? c->opts.sft_chunk : 8;
                 while (S > 3 && ring_smem(S, w_tab, want_sinc).total > 110 * 1024) --S;
                 const size_t smem = ring_smem(S, w_tab, want_sinc).total;
@@ -423,7 +429,7 @@ bool make_far_plan(fstat_ctx* c, int P, int L, bool found, Plan& best) {
                     best_r = cost;
                     best = Plan{};
                     best.P = P;
-                    best.L = 2;
+                    best.L = L;
                     best.M = M_;
                     best.W = nwc + 1;
                     best.C = S;
@@ -1111,13 +1117,14 @@ int ensure_tables(fstat_ctx* c, cudaStream_t s) {
     int rc;
     if (c->plan.far) far_extent(c, c->plan.w_pairs, &c->far_xoff, &c->n_pos);
     if (c->plan.far &&
-        (c->tab_dirty || c->tab_npos != c->n_pos || c->tab_xoff != c->far_xoff || c->tab_sinc != c->plan.sinc)) {
+        (c->tab_dirty || c->tab_npos != c->n_pos || c->tab_xoff != c->far_xoff || c->tab_sinc != c->plan.sinc ||
+         (c->plan.sinc && c->tab_split != (c->plan.L == 2)))) {
         const size_t n_tab = (size_t)c->n_sft * c->n_pos;
         const void* bins = c->opts.bins_form == FSTAT_BINS_C64 ? (const void*)work_bins(c) : (const void*)c->d_bins16;
         if (c->plan.sinc) {
             if ((rc = grow(c, &c->d_pcoef, c->cap_pcoef, 6 * n_tab)) != FSTAT_OK) return rc;
             CUDA_TRY(c, launch_sinc_tables(bins, c->opts.bins_form, c->row, c->n_sft, c->n_bins, c->sgam, c->d_pcoef,
-                                           c->n_pos, c->far_xoff, s));
+                                           c->n_pos, c->far_xoff, c->plan.L == 2, s));
         } else {
             if ((rc = grow(c, &c->d_ptab, c->cap_ptab, n_tab)) != FSTAT_OK) return rc;
             if ((rc = grow(c, &c->d_pcoef, c->cap_pcoef, 3 * n_tab)) != FSTAT_OK) return rc;
@@ -1129,6 +1136,7 @@ int ensure_tables(fstat_ctx* c, cudaStream_t s) {
         c->tab_npos = c->n_pos;
         c->tab_xoff = c->far_xoff;
         c->tab_sinc = c->plan.sinc;
+        c->tab_split = c->plan.L == 2;
     }
     return FSTAT_OK;
 }
@@ -1207,7 +1215,8 @@ bool tables_match(const fstat_ctx* c, const Plan& pl) {
     if (!pl.far) return true;
     int xoff = 0, n_pos = 0;
     far_extent(c, pl.w_pairs, &xoff, &n_pos);
-    return !c->tab_dirty && c->tab_sinc == pl.sinc && c->tab_npos == n_pos && c->tab_xoff == xoff &&
+    return !c->tab_dirty && c->tab_sinc == pl.sinc && (!pl.sinc || c->tab_split == (pl.L == 2)) &&
+           c->tab_npos == n_pos && c->tab_xoff == xoff &&
            c->n_pos == n_pos && c->far_xoff == xoff;
 }
 
@@ -1587,7 +1596,7 @@ int fstat_batch_add(fstat_ctx* c, const fstat_workunit* wu, int32_t* wu_id) {
     // the persistent kernels exist for the direct and the ring forms: a workunit
     // the far-field form would stage in rounds runs the direct form, alone or batched
     Plan pl;
-    if (make_plan(w, pl) == FSTAT_OK && pl.far && !pl.ring) w->opts.algo = FSTAT_ALGO_DIRECT;
+    if (make_plan(w, pl) == FSTAT_OK && pl.far && (!pl.ring || pl.L != 2)) w->opts.algo = FSTAT_ALGO_DIRECT;
     w->plan_valid = false;
     w->err.clear();
     c->wus.push_back(w);
@@ -1725,7 +1734,7 @@ int fstat_batch_compute(fstat_ctx* c, void* cuda_stream) {
         w->stream = s;
         int rc = prepare(w, s);
         if (rc != FSTAT_OK) return fail(c, rc, "workunit: %s", w->err.c_str());
-        if (w->plan.far && !w->plan.ring) {   // the persistent kernels exist for the direct and ring forms
+        if (w->plan.far && (!w->plan.ring || w->plan.L != 2)) {   // persistent kernels: direct and L = 2 ring forms
             w->opts.algo = FSTAT_ALGO_DIRECT;
             w->plan_valid = false;
             c->graph_valid = false;

@@ -217,11 +217,12 @@ __device__ __forceinline__ void sinc_sft(const DirichletParams& p, const SkySftM
 
 // Sinc tables: per (SFT, position x) and half bin h, the six complex
 // coefficients c_{h,n} = sum_k X_{x - xoff + k} gamma[h][k + 7][n] (bins outside
-// the band count as zero), stored at [SFT][h][parity-split position].
+// the band count as zero), stored at [SFT][h][position], positions split by
+// parity for the L = 2 layouts.
 template <int FORM>
 __global__ void __launch_bounds__(256) sinc_tables_kernel(const typename RawT<FORM>::T* __restrict__ bins,
                                                           long long row, int n_sft, int n_bins, const SincGamma gam,
-                                                          float4* __restrict__ pcoef, int n_pos, int xoff) {
+                                                          float4* __restrict__ pcoef, int n_pos, int xoff, bool split) {
     using RT = RawT<FORM>;
     const long long total = (long long)n_sft * n_pos;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
@@ -229,7 +230,8 @@ __global__ void __launch_bounds__(256) sinc_tables_kernel(const typename RawT<FO
         const int s = (int)(t / n_pos);
         const int x = (int)(t - (long long)s * n_pos);
         const int r = x - xoff;
-        const size_t slot = (size_t)(x & 1) * (n_pos >> 1) + (x >> 1);   // parity-split position
+        // parity-split position (L = 2) or plain (L = 1)
+        const size_t slot = split ? (size_t)(x & 1) * (n_pos >> 1) + (x >> 1) : (size_t)x;
         const typename RT::T* rp = bins + (size_t)s * row;
         float2 v[kSincTerms];
 #pragma unroll
@@ -537,11 +539,14 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
     return false;
 }
 
-// L = 2, uniform spindown grid.  Warps 0..NW-1 compute, warp NW produces.
+// Uniform spindown grid; L = 2 (tables split by position parity, two runs
+// per table and SFT) or L = 1 (sinc form only: plain tables, one run).
+// Warps 0..NW-1 compute, warp NW produces.
 // Error flag bit 2: a pipeline wait gave up (results of the block invalid).
-template <int M, bool SINC, bool COV>
+template <int M, bool SINC, bool COV, int L>
 __device__ __forceinline__ void far_ring_block(const DirichletParams& p, long long bid, unsigned char* smem) {
-    constexpr int D = 8, L = 2;
+    static_assert(L == 2 || (L == 1 && SINC), "the L = 1 ring is built for the sinc tables");
+    constexpr int D = 8;
     const int S = p.sft_chunk;
     const RingSmem lay = ring_smem(S, p.w_tab, SINC);
     const int NW = (int)(blockDim.x >> 5) - 1;
@@ -634,8 +639,15 @@ __device__ __forceinline__ void far_ring_block(const DirichletParams& p, long lo
                         mbar_expect_tx(fb, bytes);
                         bulk_g2s(ss + (uint32_t)lay.meta, p.meta + meta0 + a, 48, fb);
                         bulk_g2s(ss + (uint32_t)lay.base, p.base + meta0 + a, 32, fb);
+                        if (L == 1) {   // plain tables: one run of w_pairs positions per plane
 #pragma unroll
-                        for (int h = 0; h < 2; ++h) {
+                            for (int hb = 0; hb < 2; ++hb)
+                                bulk_g2s(ss + (uint32_t)(hb * lay.plane),
+                                         p.pcoef + 3 * (((size_t)a * 2 + hb) * p.n_pos + x0),
+                                         (uint32_t)p.w_pairs * 48u, fb);
+                        }
+#pragma unroll
+                        for (int h = 0; h < (L == 2 ? 2 : 0); ++h) {
                             const int cnt = h ? n1 : n0;
                             const size_t go = (size_t)a * p.n_pos + (size_t)((x0 + h) & 1) * nh + ((x0 + h) >> 1);
                             if (SINC) {
@@ -728,10 +740,10 @@ __device__ __forceinline__ void far_ring_block(const DirichletParams& p, long lo
 }
 
 // NWC compute warps plus the producer; two resident blocks per SM.
-template <int M, int NWC, bool SINC, bool COV>
+template <int M, int NWC, bool SINC, bool COV, int L>
 __global__ void __launch_bounds__(32 * (NWC + 1), 2) dirichlet_far_ring_kernel(const DirichletParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
-    far_ring_block<M, SINC, COV>(p, (long long)blockIdx.x, smem);
+    far_ring_block<M, SINC, COV, L>(p, (long long)blockIdx.x, smem);
 }
 
 // Persistent ring form over many template banks (workunits): every block
@@ -766,7 +778,7 @@ __global__ void __launch_bounds__(32 * (NWC + 1), 2)
         if (it >= total) break;
         const int w = s_wu;
         const DirichletParams p = banks[w];
-        far_ring_block<M, SINC, false>(p, it - item_prefix[w], smem);
+        far_ring_block<M, SINC, false, 2>(p, it - item_prefix[w], smem);
         __syncthreads();
         if (threadIdx.x == 0) {
             __threadfence();
@@ -800,6 +812,10 @@ __global__ void __launch_bounds__(32 * (NWC + 1), 2)
 #define FS_RING_COV_VARIANTS(X) \
     X(16, 5, 10, true)          \
     X(17, 5, 10, false)
+// sinc form for L = 1 banks (P = 8 threads per lane-group; single launches only)
+#define FS_RING_L1_VARIANTS(X) \
+    X(18, 5, 8, true)          \
+    X(19, 1, 8, true)
 
 cudaError_t launch_dirichlet_far(int v, const DirichletParams& p, int threads, size_t smem, long long grid,
                                  cudaStream_t s) {
@@ -814,18 +830,21 @@ cudaError_t launch_dirichlet_far(int v, const DirichletParams& p, int threads, s
     }
         FS_FAR_VARIANTS(FS_FCASE)
 #undef FS_FCASE
-#define FS_RCASE(ID, M_, W_, S_, C_)                                                                      \
+#define FS_RCASE(ID, M_, W_, S_, C_, L_)                                                                  \
     case ID: {                                                                                            \
-        auto fn = dirichlet_far_ring_kernel<M_, W_, S_, C_>;                                              \
+        auto fn = dirichlet_far_ring_kernel<M_, W_, S_, C_, L_>;                                          \
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
         if (e != cudaSuccess) return e;                                                                   \
         fn<<<(unsigned)grid, threads, smem, s>>>(p);                                                      \
         return cudaGetLastError();                                                                        \
     }
-#define FS_RCASE_PLAIN(ID, M_, W_, S_) FS_RCASE(ID, M_, W_, S_, false)
-#define FS_RCASE_COV(ID, M_, W_, S_) FS_RCASE(ID, M_, W_, S_, true)
+#define FS_RCASE_PLAIN(ID, M_, W_, S_) FS_RCASE(ID, M_, W_, S_, false, 2)
+#define FS_RCASE_COV(ID, M_, W_, S_) FS_RCASE(ID, M_, W_, S_, true, 2)
+#define FS_RCASE_L1(ID, M_, W_, S_) FS_RCASE(ID, M_, W_, S_, false, 1)
         FS_RING_VARIANTS(FS_RCASE_PLAIN)
         FS_RING_COV_VARIANTS(FS_RCASE_COV)
+        FS_RING_L1_VARIANTS(FS_RCASE_L1)
+#undef FS_RCASE_L1
 #undef FS_RCASE_COV
 #undef FS_RCASE_PLAIN
 #undef FS_RCASE
@@ -869,18 +888,19 @@ cudaError_t dirichlet_far_batch_occupancy(int v, int threads, size_t smem, int* 
 }
 
 cudaError_t launch_sinc_tables(const void* bins, int form, long long row, int n_sft, int n_bins,
-                               const SincGamma& gam, float4* pcoef, int n_pos, int xoff, cudaStream_t s) {
+                               const SincGamma& gam, float4* pcoef, int n_pos, int xoff, bool split,
+                               cudaStream_t s) {
     const long long total = (long long)n_sft * n_pos;
     const int grid = (int)std::min<long long>((total + 255) / 256, 152LL * 16);
     if (form == FSTAT_BINS_C64)
         sinc_tables_kernel<FSTAT_BINS_C64><<<grid, 256, 0, s>>>(static_cast<const float2*>(bins), row, n_sft, n_bins,
-                                                                 gam, pcoef, n_pos, xoff);
+                                                                 gam, pcoef, n_pos, xoff, split);
     else if (form == FSTAT_BINS_F16)
         sinc_tables_kernel<FSTAT_BINS_F16><<<grid, 256, 0, s>>>(static_cast<const __half2*>(bins), row, n_sft,
-                                                                 n_bins, gam, pcoef, n_pos, xoff);
+                                                                 n_bins, gam, pcoef, n_pos, xoff, split);
     else
         sinc_tables_kernel<FSTAT_BINS_BF16><<<grid, 256, 0, s>>>(static_cast<const __nv_bfloat162*>(bins), row, n_sft,
-                                                                  n_bins, gam, pcoef, n_pos, xoff);
+                                                                  n_bins, gam, pcoef, n_pos, xoff, split);
     return cudaGetLastError();
 }
 

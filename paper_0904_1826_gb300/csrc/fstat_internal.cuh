@@ -255,8 +255,10 @@ struct TopkWork {
 };
 cudaError_t launch_far_tables(const void* bins, int form, long long row, int n_sft, int n_bins, const FarGamma& gam,
                               float4* ptab, float4* pcoef, int n_pos, int xoff, cudaStream_t s);
+// split: positions split by parity (the L = 2 layout) or plain (L = 1).
 cudaError_t launch_sinc_tables(const void* bins, int form, long long row, int n_sft, int n_bins,
-                               const SincGamma& gam, float4* pcoef, int n_pos, int xoff, cudaStream_t s);
+                               const SincGamma& gam, float4* pcoef, int n_pos, int xoff, bool split,
+                               cudaStream_t s);
 cudaError_t launch_dirichlet_far(int v, const DirichletParams& p, int threads, size_t smem, long long grid,
                                  cudaStream_t s);
 cudaError_t launch_dirichlet_far_batch(int v, const DirichletBatch& b, int threads, size_t smem, int grid,

@@ -358,3 +358,18 @@ def test_ring_with_four_threads_per_lane_group_on_a_wide_bank(lib, algo):
     assert out["plan"]["variant"] >= 107 and (out["plan"]["warps"] - 1) % 4 == 0   # ring, 8 compute warps
     assert out["flags"] == 0
     _assert_parity(out["twoF"], ref, "P=4 wide bank")
+
+
+def test_sinc_ring_for_l1_banks(lib):
+    """df = 1/(8T): P = 8, L = 1; the sinc form runs in the TMA ring on plain
+    (not parity-split) tables, with M = 1 or 5 per the planner, across
+    several blocks per column and a ragged tail."""
+    w = config_mid(df_bins=0.125, n_f=700, n_fdot=3, n_sky=2, n_bins=160)
+    bins = _oracle_bins(w)
+    ref = O.compute_fstat_freq_band(_dets(w, bins), w.T, w.k_lo, w.dterms, w.bank).ravel()
+    for tile in (dict(), dict(tile_m=5), dict(tile_m=1)):
+        out = _gpu(lib, w, bins, algo="sincpoly", **tile)
+        assert (out["plan"]["P"], out["plan"]["L"]) == (8, 1)
+        assert out["plan"]["variant"] in (118, 119), out["plan"]
+        assert out["flags"] == 0
+        _assert_parity(out["twoF"], ref, f"L=1 ring {tile}")
