@@ -102,9 +102,9 @@ def kernel_hash(algo: str) -> str:
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(form: str, algo: str):
-    """DRAM bytes per launch of the Dirichlet kernel from the committed ncu
-    summary, if it was taken on the current kernel source (else None)."""
+def ncu_entry(form: str, algo: str):
+    """The committed ncu summary of the Dirichlet kernel, if it was taken on
+    the current kernel source (else None)."""
     p = os.path.join(ROOT, "profiles", "dirichlet_counters.json")
     try:
         with open(p) as fh:
@@ -114,7 +114,13 @@ def ncu_traffic(form: str, algo: str):
     e = d.get(f"{algo}/{form}")
     if not e or e.get("kernel_hash") != kernel_hash(algo):
         return None
-    return e.get("dram_bytes_per_full_launch")
+    return e
+
+
+def ncu_traffic(form: str, algo: str):
+    """DRAM bytes per launch of the Dirichlet kernel (ncu, current source) or None."""
+    e = ncu_entry(form, algo)
+    return e.get("dram_bytes_per_full_launch") if e else None
 
 
 class ClockSampler:
@@ -624,6 +630,15 @@ def main():
                 "peak_note": "152 SM x 128 FP32 lanes x 2 flop x 2070 MHz (max SM clock)"}
     if clocks and clocks.get("sm_mhz"):
         roofline["frac_at_sampled_clock"] = achieved / (N_SM * FP32_LANES * 2 * clocks["sm_mhz"] * 1e6 / 1e12)
+    # the table forms are bound by shared-memory loads: that bound too, from the
+    # ncu wavefront count per pair (128 B each) against 128 B per SM and clock
+    ent = ncu_entry(args.form, algo_used)
+    if ent and ent.get("smem_wavefronts_per_pair"):
+        smem_b = ent["smem_wavefronts_per_pair"] * 128.0 * n_pairs
+        smem_peak = N_SM * 128.0 * clock_mhz * 1e6 / 1e12       # TB/s
+        roofline["shared_memory"] = {"achieved": smem_b / (k_dir / 1e3) / 1e12, "peak": smem_peak, "unit": "TB/s",
+                                     "frac": smem_b / (k_dir / 1e3) / 1e12 / smem_peak,
+                                     "bytes_per_pair": ent["smem_wavefronts_per_pair"] * 128.0}
     line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "step_ms": {"best": steps_ms[0], "median": steps_ms[len(steps_ms) // 2]} if steps_ms else None,
