@@ -45,7 +45,7 @@ constexpr int kJ = 4;
 // per-(segment, fdot) integer offset floor(A + 1/2), clamped to +-2^30 (past
 // that every lookup is outside the band anyway; n_f < 2^30).
 template <bool UNIT>
-__global__ void __launch_bounds__(kSlideBlock, 4) stackslide_kernel(const SlideSeg* __restrict__ seg, int n_seg,
+__global__ void __launch_bounds__(kSlideBlock, 6) stackslide_kernel(const SlideSeg* __restrict__ seg, int n_seg,
                                                                     const long long* __restrict__ A_fx,
                                                                     const long long* __restrict__ B_fx, int n_fdot,
                                                                     int n_f, float* __restrict__ out,
