@@ -373,3 +373,23 @@ def test_sinc_ring_for_l1_banks(lib):
         assert out["plan"]["variant"] in (118, 119), out["plan"]
         assert out["flags"] == 0
         _assert_parity(out["twoF"], ref, f"L=1 ring {tile}")
+
+
+def test_size_limits_are_errors_not_allocations(lib):
+    """Banks past the documented limits are refused before any device
+    allocation: more than 2^40 templates, more than 64 spindowns."""
+    w = config_mid(n_sky=2, n_f=20, n_fdot=2)
+    g = lib.FStat(0, topk=10)
+    try:
+        g.load_workload(w)
+        sky = np.zeros((1 << 21, 2))
+        with pytest.raises(lib.FstatError) as e:      # 2^21 x 2^20 x 1 = 2^41 templates
+            lib.fstat_set_templates(g.ctx, sky, w.bank.f0, w.bank.df, 1 << 20, np.zeros(1), w.bank.t_ref)
+        assert e.value.code == lib.FSTAT_EINVAL
+        with pytest.raises(lib.FstatError) as e:      # 65 spindowns
+            lib.fstat_set_templates(g.ctx, w.bank.sky, w.bank.f0, w.bank.df, 20, np.zeros(65), w.bank.t_ref)
+        assert e.value.code == lib.FSTAT_EINVAL
+        g.compute()                                    # the earlier bank still computes
+        assert g.error_flags() == 0
+    finally:
+        g.close()
