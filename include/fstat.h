@@ -95,8 +95,9 @@ typedef struct {
  *   coefficients are precomputed per SFT, window position and half (two
  *   48-byte records per stored bin and SFT; interpolation error below 2.1e-6
  *   of each term; no reciprocal, sine or clamp per template).  It runs in the
- *   TMA-ring staging (uniform spindown grid, P df T = 2, 5 or 7 templates per
- *   thread); elsewhere it falls back to FARPOLY.
+ *   TMA-ring staging on a uniform spindown grid: P df T = 2 (5 or 7 templates
+ *   per thread) or P df T = 1 with P = 8 (1 or 5); elsewhere it falls back
+ *   to FARPOLY.
  * Batched workunits use the TMA-ring form where it applies, else DIRECT.
  * AUTO: SINCPOLY where the TMA ring applies, else FARPOLY where it applies,
  *   else DIRECT. */
