@@ -8,6 +8,13 @@ basis kernel, the Dirichlet kernel with fused 2F, and the toplist selection.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--form c64|f16|bf16]
   python bench.py --impl reference ...   (the FP64 CPU oracle on a bounded sample)
+  python bench.py --config batch | semicoherent | proposal   (other workloads)
+  python bench.py --coverage F | --noise-floor W | --algo ...   (variants)
+
+The JSON line's `roofline` is the Dirichlet kernel's ALU bound (100 flop per
+pair of the direct sum), with the DRAM traffic and, for the table forms, the
+shared-memory bound (`roofline.shared_memory`) taken from the committed ncu
+summary while it matches the kernel source.
 
 Multi-GPU (torchrun, one process per GPU): sky points are sharded, each rank
 runs a full workunit-sized step on its shard (weak scaling) and the local
