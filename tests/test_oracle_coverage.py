@@ -88,3 +88,20 @@ def test_noise_mean_stays_four_where_half_the_sfts_remain():
     low, high = np.concatenate(low), np.concatenate(high)
     for x in (low, high):
         assert abs(x.mean() - 4.0) < 4 * math.sqrt(8.0 / x.shape[0])
+
+
+def test_full_coverage_with_noise_weights_is_the_weighted_oracle():
+    # per-SFT noise weights (attribute `weights`) enter A, B, C and Fa, Fb the
+    # same way in both oracles
+    from oracle import noise_oracle as N
+    dets = _dets(seed=41)
+    rng = np.random.default_rng(4)
+    dets = [DetectorData(d.lat, d.lon, d.az, d.t_start,
+                         (d.bins * np.sqrt(rng.uniform(1, 5, len(d.t_start)))[:, None]).astype(np.complex64))
+            for d in dets]
+    wd = N.weighted_detectors(dets, 8)
+    bank = _bank()
+    n = sum(len(d.t_start) for d in wd)
+    got = CO.compute_fstat_coverage(wd, T, K_LO, 8, bank, np.zeros(n), np.full(n, bank.n_f))
+    want = O.compute_fstat_freq_band(wd, T, K_LO, 8, bank)
+    np.testing.assert_allclose(got, want, rtol=1e-11, atol=1e-12)
