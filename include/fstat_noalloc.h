@@ -30,9 +30,16 @@ extern "C" {
 #define FSTAT_NOALLOC_MAX_K 16384
 
 /* The k largest values of v[0 .. n-1] (device FP32, n >= 1, values >= 0 and
- * not NaN as 2F is), ordered by value descending and, for equal values, by
- * index ascending -- the order fstat_get_toplist returns.  idx_out [k]
- * (int64) and val_out [k] (FP32) are device arrays owned by the caller.
+ * not NaN as 2F is; -0.0 ranks as +0.0 and is returned as +0.0), ordered by
+ * value descending and, for equal values, by index ascending -- the order
+ * fstat_get_toplist returns.  idx_out [k] (int64) and val_out [k] (FP32) are
+ * device arrays owned by the caller.
+ *
+ * Alignment: v may start at any element (4-byte aligned address, e.g. a view
+ * at an offset into a larger array); val_out must be 4-byte and idx_out
+ * 8-byte aligned.  A pointer that breaks this is refused with EINVAL before
+ * anything is launched.
+ *
  * Everything runs asynchronously on cuda_stream (NULL = the legacy default
  * stream) on `device`, which becomes the calling thread's current device.
  *
@@ -51,8 +58,9 @@ extern "C" {
  * stream capture begins.
  *
  * msg / msg_len (optional, may be NULL / 0): receives a one-line description
- * of an error.  Errors: ERANGE (k above FSTAT_NOALLOC_MAX_K), EINVAL (null
- * pointers, n < 1, k < 1 or k > n, bad device), ECUDA (a CUDA call failed). */
+ * of an error.  Errors: ERANGE (k above FSTAT_NOALLOC_MAX_K), EINVAL (null or
+ * misaligned pointers, n < 1, k < 1 or k > n, bad device), ECUDA (a CUDA call
+ * failed). */
 int fstat_toplist_noalloc(int device, const float *v, int64_t n, int32_t k, int64_t *idx_out, float *val_out,
                           void *cuda_stream, char *msg, int32_t msg_len);
 

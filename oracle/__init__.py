@@ -13,7 +13,10 @@ Pinned functions (see tests/test_oracle_pins.py):
   * quantisation                                   -- exactly representable cases;
   * the MLP forward/backward                       -- central finite differences;
   * noise floor, whitening, noise weights           -- closed-form medians and weights,
-    stationary invariance, chi^2_4 mean on non-stationary noise.
+    stationary invariance, chi^2_4 mean on non-stationary noise;
+  * c_oracle (the same F-statistic as plain C loops, for whole workunits)
+    -- equality with the numpy oracle, the noise-free closed form and its
+    D -> infinity limit, planted mistakes (tests/test_oracle_c.py).
 """
 from . import fstat_oracle  # noqa: F401
 from . import mlp_oracle  # noqa: F401

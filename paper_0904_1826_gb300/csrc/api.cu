@@ -1527,7 +1527,7 @@ int fstat_autotune(fstat_ctx* c, void* cuda_stream, int32_t* out) {
             // a slice of the bank: the first sky points, about four waves of blocks
             const long long per_sky = (long long)c->plan.n_col * c->plan.chunks_per_col;
             int occ = 2;
-            const long long want = 4LL * occ * 152;
+            const long long want = 4LL * occ * current_sm_count();
             const int n_sky_sub = (int)std::min<long long>(c->n_sky, std::max<long long>(1, (want + per_sky - 1) / per_sky));
             if (launch_timing(timing_params(c, n_sky_sub), s) != cudaSuccess) continue;
             DirichletParams dp = dirichlet_params(c);
@@ -1678,8 +1678,7 @@ int enqueue_batch(fstat_ctx* c, const std::vector<int>& order, const std::vector
     }
     CUDA_TRY(c, cudaMemcpyAsync(c->d_rem, c->d_rem_init, sizeof(int) * n, cudaMemcpyDeviceToDevice, s));
     CUDA_TRY(c, cudaMemsetAsync(c->d_queue, 0, sizeof(unsigned long long) * groups.size(), s));
-    int dev_sms = 152;
-    cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, c->device);
+    const int dev_sms = current_sm_count();
     for (size_t g = 0; g < groups.size(); ++g) {
         const BatchGroup& G = groups[g];
         DirichletBatch b{};

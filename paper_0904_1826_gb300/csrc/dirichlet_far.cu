@@ -891,7 +891,7 @@ cudaError_t launch_sinc_tables(const void* bins, int form, long long row, int n_
                                const SincGamma& gam, float4* pcoef, int n_pos, int xoff, bool split,
                                cudaStream_t s) {
     const long long total = (long long)n_sft * n_pos;
-    const int grid = (int)std::min<long long>((total + 255) / 256, 152LL * 16);
+    const int grid = (int)std::min<long long>((total + 255) / 256, (long long)current_sm_count() * 16);
     if (form == FSTAT_BINS_C64)
         sinc_tables_kernel<FSTAT_BINS_C64><<<grid, 256, 0, s>>>(static_cast<const float2*>(bins), row, n_sft, n_bins,
                                                                  gam, pcoef, n_pos, xoff, split);
@@ -907,7 +907,7 @@ cudaError_t launch_sinc_tables(const void* bins, int form, long long row, int n_
 cudaError_t launch_far_tables(const void* bins, int form, long long row, int n_sft, int n_bins, const FarGamma& gam,
                               float4* ptab, float4* pcoef, int n_pos, int xoff, cudaStream_t s) {
     const long long total = (long long)n_sft * n_pos;
-    const int grid = (int)std::min<long long>((total + 255) / 256, 152LL * 16);
+    const int grid = (int)std::min<long long>((total + 255) / 256, (long long)current_sm_count() * 16);
     if (form == FSTAT_BINS_C64)
         far_tables_kernel<FSTAT_BINS_C64><<<grid, 256, 0, s>>>(static_cast<const float2*>(bins), row, n_sft, n_bins,
                                                                 gam, ptab, pcoef, n_pos, xoff);

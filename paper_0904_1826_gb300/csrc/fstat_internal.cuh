@@ -221,6 +221,19 @@ struct TimingParams {
     int* err;
 };
 
+// Streaming multiprocessors of the calling thread's current device, queried
+// once per device (grid sizes are multiples of it).
+inline int current_sm_count() {
+    static int cache[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 1;
+    if (dev < 64 && cache[dev] > 0) return cache[dev];
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 1;
+    if (dev < 64) cache[dev] = n;
+    return n;
+}
+
 // ---- launchers (defined in the .cu files) --------------------------------
 cudaError_t launch_sft_state(const double* t_start, const int* det_of_sft, const fstat_detector* dets,
                              int n_sft, double T, SftState* out, cudaStream_t s);

@@ -7,6 +7,7 @@
 // result is deterministic.  A single block then sorts the K candidates.
 #include "fstat_internal.cuh"
 
+#include <algorithm>
 #include <cstdio>
 #include <mutex>
 
@@ -26,6 +27,13 @@ __device__ __forceinline__ void warp_hist_add(unsigned int* h, unsigned int bin,
     if ((int)(threadIdx.x & 31) == leader) atomicAdd(&h[bin], (unsigned int)__popc(peers));
 }
 
+// Ranking key of a value: its FP32 bit pattern, with -0.0 taken as +0.0 (for
+// the non-negative values ranked here the patterns order like the values).
+__device__ __forceinline__ unsigned int key_bits(float x) {
+    const unsigned int b = __float_as_uint(x);
+    return b == 0x80000000u ? 0u : b;
+}
+
 template <int LEVEL>
 __device__ __forceinline__ void classify(unsigned int b, unsigned int prefix, unsigned int& bin, bool& ok) {
     if (LEVEL == 0) {
@@ -40,16 +48,18 @@ __device__ __forceinline__ void classify(unsigned int b, unsigned int prefix, un
     }
 }
 
+// v + head is 16-byte aligned (head < 4): the head, the float4 body and the
+// tail of fewer than four values are histogrammed separately.
 template <int LEVEL>
-__global__ void __launch_bounds__(kBlk) hist_kernel(const float* __restrict__ v, long long n,
+__global__ void __launch_bounds__(kBlk) hist_kernel(const float* __restrict__ v, long long n, int head,
                                                     const unsigned int* __restrict__ state,
                                                     unsigned int* __restrict__ hist) {
     __shared__ unsigned int h[kBins];
     for (int i = threadIdx.x; i < kBins; i += kBlk) h[i] = 0;
     __syncthreads();
     const unsigned int prefix = LEVEL == 0 ? 0u : state[0];
-    const long long n4 = n >> 2;
-    const float4* v4 = reinterpret_cast<const float4*>(v);
+    const long long n4 = (n - head) >> 2;
+    const float4* v4 = reinterpret_cast<const float4*>(v + head);
     const long long stride = (long long)gridDim.x * kBlk;
     // every thread of a warp runs the same number of iterations (ballot below)
     for (long long base = (long long)blockIdx.x * kBlk; base < n4; base += stride) {
@@ -62,17 +72,21 @@ __global__ void __launch_bounds__(kBlk) hist_kernel(const float* __restrict__ v,
         for (int c = 0; c < 4; ++c) {
             unsigned int bin;
             bool ok;
-            classify<LEVEL>(__float_as_uint(xs[c]), prefix, bin, ok);
+            classify<LEVEL>(key_bits(xs[c]), prefix, bin, ok);
             warp_hist_add(h, bin, ok && in);
         }
     }
-    // tail (n not a multiple of 4)
+    // head (before the 16-byte boundary) and tail (after the last float4)
     if (blockIdx.x == 0 && threadIdx.x < 32) {
-        const long long i = n4 * 4 + threadIdx.x;
-        const bool in = i < n;
+        const long long t = threadIdx.x;
+        const long long n_tail = n - head - 4 * n4;
+        long long i = -1;
+        if (t < head) i = t;
+        else if (t - head < n_tail) i = head + 4 * n4 + (t - head);
+        const bool in = i >= 0;
         unsigned int bin = 0;
         bool ok = false;
-        if (in) classify<LEVEL>(__float_as_uint(v[i]), prefix, bin, ok);
+        if (in) classify<LEVEL>(key_bits(v[i]), prefix, bin, ok);
         warp_hist_add(h, bin, ok && in);
     }
     __syncthreads();
@@ -122,7 +136,7 @@ __global__ void __launch_bounds__(kBlk) collect_kernel(const float* __restrict__
     unsigned int my_ties = 0;
     for (long long i = lo + threadIdx.x; i < hi; i += kBlk) {
         const float x = v[i];
-        const unsigned int b = __float_as_uint(x);
+        const unsigned int b = key_bits(x);
         if (b > tau) {
             const unsigned int s = atomicAdd(n_cand, 1u);
             cand_idx[s] = i;
@@ -159,7 +173,7 @@ __global__ void __launch_bounds__(kBlk) tie_kernel(const float* __restrict__ v, 
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     for (long long base = lo; base < hi && prefix < need; base += kBlk) {
         const long long i = base + threadIdx.x;
-        const bool t = (i < hi) && (__float_as_uint(v[i]) == tau);
+        const bool t = (i < hi) && (key_bits(v[i]) == tau);
         const unsigned int bal = __ballot_sync(0xffffffffu, t);
         if (l == 0) wsum[w] = __popc(bal);
         __syncthreads();
@@ -232,12 +246,14 @@ cudaError_t launch_topk(const float* v, long long n, int k, TopkWork& w, cudaStr
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(w.n_cand, 0, sizeof(unsigned int), s);
     if (e != cudaSuccess) return e;
-    const int hgrid = 152 * 8;
-    hist_kernel<0><<<hgrid, kBlk, 0, s>>>(v, n, w.state, w.hist);
+    const int hgrid = current_sm_count() * 8;
+    // values before the first 16-byte boundary (v itself is 4-byte aligned)
+    const int head = (int)std::min<long long>(n, (long long)(((16u - ((uintptr_t)v & 15u)) & 15u) / 4u));
+    hist_kernel<0><<<hgrid, kBlk, 0, s>>>(v, n, head, w.state, w.hist);
     select_kernel<0><<<1, 32, 0, s>>>(w.hist, w.state, (unsigned int)k);
-    hist_kernel<1><<<hgrid, kBlk, 0, s>>>(v, n, w.state, w.hist);
+    hist_kernel<1><<<hgrid, kBlk, 0, s>>>(v, n, head, w.state, w.hist);
     select_kernel<1><<<1, 32, 0, s>>>(w.hist, w.state, (unsigned int)k);
-    hist_kernel<2><<<hgrid, kBlk, 0, s>>>(v, n, w.state, w.hist);
+    hist_kernel<2><<<hgrid, kBlk, 0, s>>>(v, n, head, w.state, w.hist);
     select_kernel<2><<<1, 32, 0, s>>>(w.hist, w.state, (unsigned int)k);
     const long long per_block = (n + w.n_blocks - 1) / w.n_blocks;
     collect_kernel<<<w.n_blocks, kBlk, 0, s>>>(v, n, per_block, w.state, w.cand_idx, w.cand_val, w.n_cand,
@@ -291,6 +307,9 @@ extern "C" int fstat_toplist_noalloc(int device, const float* v, int64_t n, int3
     using namespace fs;
     if (msg && msg_len > 0) msg[0] = 0;
     if (!v || !idx_out || !val_out) return na_fail(msg, msg_len, FSTAT_EINVAL, "null array pointer");
+    if (((uintptr_t)v & 3u) || ((uintptr_t)val_out & 3u) || ((uintptr_t)idx_out & 7u))
+        return na_fail(msg, msg_len, FSTAT_EINVAL,
+                       "misaligned array: v and val_out need 4-byte, idx_out 8-byte alignment");
     if (k > FSTAT_NOALLOC_MAX_K)
         return na_fail(msg, msg_len, FSTAT_ERANGE, "k = %lld is above the static scratch limit of %lld", k,
                        FSTAT_NOALLOC_MAX_K);
