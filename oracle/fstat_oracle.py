@@ -23,7 +23,7 @@ coefficients a, b, and combined with A = sum a^2, B = sum b^2, C = sum ab,
 D = AB - C^2 into 2F.  Every formula is written out directly in FP64 with
 numpy, vectorised over templates only; nothing is blocked or reordered.
 
-Readings where the paper is silent (each listed in the design notes):
+Readings where the paper is silent, taken here:
   * synthetic Sun-centred ephemeris (circular orbit in the ecliptic plane,
     spherical rotating Earth), no Einstein or Shapiro delays;
   * x-arm azimuth from local North clockwise, y-arm at +90 degrees;

@@ -3,9 +3,11 @@
 Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline legs of
 ``bench.py`` may import this module; it shares no code with the CUDA MLP.
 
-Network (the learned-proposal reading of the design notes): 8192 inputs ->
-256 ReLU -> 256 ReLU -> 1 logit s; p = sigmoid(s); loss = mean binary
-cross-entropy with a positive-class weight w+:
+Network (the learned proposal is not in the paper; this is its reading: a
+patch of 16 x 16 sky points x 32 frequencies of the coarse 2F map, ReLU
+hidden layers, a sigmoid output trained with binary cross-entropy): 8192
+inputs -> 256 ReLU -> 256 ReLU -> 1 logit s; p = sigmoid(s); loss = mean
+binary cross-entropy with a positive-class weight w+:
     L = mean_i  w_i (softplus(s_i) - y_i s_i),  w_i = w+ if y_i = 1 else 1.
 Parameters: W1 [8192, 256], b1 [256], W2 [256, 256], b2 [256], w3 [256], b3.
 Adam: m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2; p -= lr m_hat / (sqrt(v_hat) + eps).

@@ -25,7 +25,10 @@ in this order)
 
 A_fx = rint(A 2^32) and B_fx = rint(B 2^32) (half to even), and the index is
 i = floor((A_fx + j B_fx + 2^31) / 2^32) in exact integer arithmetic.  The sum
-itself is FP64 here.
+itself is FP64 here.  Wherever x = (f0 + j df + fdot (t_s - t_ref) - f0_s) / df_s
+is not within 1e-6 of a half-integer, this index is the plain nearest bin
+floor(x + 1/2) of the exact x (pinned on workunit-shaped and finer grids in
+tests/test_oracle_semicoherent.py).
 """
 from __future__ import annotations
 

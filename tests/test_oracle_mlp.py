@@ -87,3 +87,98 @@ def test_store_hook_reaches_layer_two_and_its_gradient():
     g2 = MO.backward(p, X, y, 2.0)
     for k in MO.NAMES:
         np.testing.assert_array_equal(g1[k], g2[k])
+
+
+# ---------------------------------------------------------------- Adam closed forms
+
+def _adam_closed_form_error(step, eps=1e-8, beta1=0.9, beta2=0.999):
+    """Largest deviation of an Adam implementation `step(params, grads,
+    state, lr, beta1, beta2, eps)` from Adam's closed forms, over:
+      * step 1 from zero moments: p1 - p0 = -lr g1 / (|g1| + eps);
+      * step 2: m_hat = (beta1 g1 + g2) / (1 + beta1),
+                v_hat = (beta2 g1^2 + g2^2) / (1 + beta2),
+        p2 - p1 = -lr m_hat / (sqrt(v_hat) + eps);
+      * a constant gradient for 5 steps: every step moves -lr g / (|g| + eps)
+        (bias correction makes m_hat = g, v_hat = g^2 at every t).
+    Gradients span magnitudes from 1e-6 to 1 so that eps matters for some."""
+    rng = np.random.default_rng(21)
+    shapes = {"W1": (5, 4), "b1": (4,), "W2": (4, 4), "b2": (4,), "w3": (4,), "b3": ()}
+    lr = 1e-3
+
+    def grads():
+        return {k: rng.standard_normal(s) * 10.0 ** rng.uniform(-6, 0, s) for k, s in shapes.items()}
+
+    p0 = {k: rng.standard_normal(s) for k, s in shapes.items()}
+    g1, g2 = grads(), grads()
+    st = {}
+    p = {k: v.copy() for k, v in p0.items()}
+    p = step(p, g1, st, lr, beta1, beta2, eps)
+    err = 0.0
+    for k in shapes:
+        want = -lr * g1[k] / (np.abs(g1[k]) + eps)
+        err = max(err, float(np.max(np.abs((p[k] - p0[k]) - want))) / lr)
+    p1 = {k: v.copy() for k, v in p.items()}
+    p = step(p, g2, st, lr, beta1, beta2, eps)
+    for k in shapes:
+        mh = (beta1 * g1[k] + g2[k]) / (1 + beta1)
+        vh = (beta2 * g1[k] ** 2 + g2[k] ** 2) / (1 + beta2)
+        want = -lr * mh / (np.sqrt(vh) + eps)
+        err = max(err, float(np.max(np.abs((p[k] - p1[k]) - want))) / lr)
+    st = {}
+    p = {k: v.copy() for k, v in p0.items()}
+    for _ in range(5):
+        prev = {k: v.copy() for k, v in p.items()}
+        p = step(p, g1, st, lr, beta1, beta2, eps)
+        for k in shapes:
+            want = -lr * g1[k] / (np.abs(g1[k]) + eps)
+            err = max(err, float(np.max(np.abs((p[k] - prev[k]) - want))) / lr)
+    return err
+
+
+def _adam_no_bias_correction(params, grads, state, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    state["t"] = state.get("t", 0) + 1
+    for k in MO.NAMES:
+        m = state.setdefault("m_" + k, np.zeros_like(params[k]))
+        v = state.setdefault("v_" + k, np.zeros_like(params[k]))
+        m[...] = beta1 * m + (1 - beta1) * grads[k]
+        v[...] = beta2 * v + (1 - beta2) * grads[k] ** 2
+        params[k] = params[k] - lr * m / (np.sqrt(v) + eps)
+    return params
+
+
+def _adam_swapped_betas(params, grads, state, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    return MO.adam_step(params, grads, state, lr, beta2, beta1, eps)
+
+
+def _adam_eps_inside_sqrt(params, grads, state, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    state["t"] = state.get("t", 0) + 1
+    t = state["t"]
+    for k in MO.NAMES:
+        m = state.setdefault("m_" + k, np.zeros_like(params[k]))
+        v = state.setdefault("v_" + k, np.zeros_like(params[k]))
+        m[...] = beta1 * m + (1 - beta1) * grads[k]
+        v[...] = beta2 * v + (1 - beta2) * grads[k] ** 2
+        params[k] = params[k] - lr * (m / (1 - beta1 ** t)) / np.sqrt(v / (1 - beta2 ** t) + eps)
+    return params
+
+
+def _adam_first_moment_only_bias(params, grads, state, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    state["t"] = state.get("t", 0) + 1
+    t = state["t"]
+    for k in MO.NAMES:
+        m = state.setdefault("m_" + k, np.zeros_like(params[k]))
+        v = state.setdefault("v_" + k, np.zeros_like(params[k]))
+        m[...] = beta1 * m + (1 - beta1) * grads[k]
+        v[...] = beta2 * v + (1 - beta2) * grads[k] ** 2
+        params[k] = params[k] - lr * (m / (1 - beta1 ** t)) / (np.sqrt(v) + eps)
+    return params
+
+
+def test_adam_matches_closed_forms():
+    assert _adam_closed_form_error(MO.adam_step) < 1e-12
+
+
+def test_adam_closed_forms_catch_planted_mistakes():
+    for bad in (_adam_no_bias_correction, _adam_swapped_betas, _adam_eps_inside_sqrt,
+                _adam_first_moment_only_bias):
+        assert _adam_closed_form_error(bad) > 1e-2, bad.__name__

@@ -111,3 +111,77 @@ def test_signal_with_spindown_peaks_at_its_template_only_when_slid():
     # ... and the sum over segments at the true template without the slide is far lower
     no_slide = sum(tw[0, 1, pad + 4] for tw in segs)
     assert out[0, 1, 4] > 1.5 * no_slide
+
+
+# ---------------------------------------------------------------- fixed point vs the plain nearest bin
+
+def _nearest_exact(f0, df, fdot, t_ref, f0_s, df_s, t_s, n_f):
+    """The plain definition, nearest coarse bin floor(x + 1/2) of
+    x = (f0 + j df + fdot (t_s - t_ref) - f0_s) / df_s, in exact rational
+    arithmetic on the FP64 inputs; also the distance of frac(x) from 1/2."""
+    from fractions import Fraction as F
+    a = (F(f0) - F(f0_s) + F(fdot) * (F(t_s) - F(t_ref))) / F(df_s)
+    b = F(df) / F(df_s)
+    den = a.denominator * b.denominator
+    an, bn = a.numerator * b.denominator, b.numerator * a.denominator
+    idx = np.empty(n_f, dtype=np.int64)
+    tie = np.empty(n_f, dtype=np.float64)
+    for j in range(n_f):
+        num = an + j * bn
+        q = (2 * num + den) // (2 * den)           # floor(x + 1/2)
+        idx[j] = q
+        r = F(num, den) - q + F(1, 2)               # in [0, 1): 0 means an exact tie
+        tie[j] = float(min(r, 1 - r))
+    return idx, tie
+
+
+def _grids():
+    """Workunit-shaped stack-slide grids (1/T steps, 8 segments over ~3.1e6 s,
+    spindowns to -1e-9 Hz/s, bands padded by 8 bins) and finer and shifted
+    semicoherent grids with random offsets."""
+    rng = np.random.default_rng(17)
+    T = 1800.0
+    out = []
+    t_ref = 8.0e8
+    for s in range(8):
+        t_s = t_ref + (s + 0.5) * 3.1e6 / 8
+        out.append((100.0, 1 / T, t_ref, 100.0 - 8 / T, 1 / T, t_s, 1800))
+    for k in (1, 2, 3, 4, 8):
+        f0 = 100.0 + rng.integers(0, 1000) / T + rng.uniform(0, 1) / (k * T)
+        t_s = t_ref + rng.uniform(-5e6, 5e6)
+        f0_s = f0 - rng.integers(10, 30) / T + rng.uniform(-0.5, 0.5) / T
+        out.append((f0, 1 / (k * T), t_ref, f0_s, 1 / T, t_s, 600))
+    return out
+
+
+def test_fixed_point_index_is_the_plain_nearest_bin():
+    """Wherever frac(x) is not within 1e-6 of 1/2, the 32.32 fixed-point
+    index equals the nearest bin of the plain definition, and the plain FP64
+    evaluation round((f - f0_s) / df_s) agrees with both."""
+    fdots = np.concatenate([-1e-9 * np.arange(10) / 9, [3e-10, -2.7e-9]])
+    n_cmp = n_near = 0
+    for f0, df, t_ref, f0_s, df_s, t_s, n_f in _grids():
+        A_fx, B_fx = S.slide_constants(f0, df, fdots, t_ref, f0_s, df_s, t_s)
+        j = np.arange(n_f)
+        for m, fd in enumerate(fdots):
+            got = S.slide_index(A_fx[m], B_fx, j)
+            want, tie = _nearest_exact(f0, df, float(fd), t_ref, f0_s, df_s, t_s, n_f)
+            plain = np.floor((f0 + j * df + fd * (t_s - t_ref) - f0_s) / df_s + 0.5).astype(np.int64)
+            ok = tie > 1e-6
+            np.testing.assert_array_equal(got[ok], want[ok])
+            np.testing.assert_array_equal(plain[ok], want[ok])
+            n_cmp += int(ok.sum())
+            n_near += int((~ok).sum())
+    assert n_cmp > 100_000
+    assert n_near <= 1e-4 * n_cmp
+
+
+def test_nearest_bin_pin_catches_truncation_and_inverse_ratio():
+    f0, df, t_ref, f0_s, df_s, t_s, n_f = _grids()[9]
+    want, tie = _nearest_exact(f0, df, -4e-10, t_ref, f0_s, df_s, t_s, n_f)
+    A_fx, B_fx = S.slide_constants(f0, df, [-4e-10], t_ref, f0_s, df_s, t_s)
+    j = np.arange(n_f)
+    trunc = (np.int64(A_fx[0]) + j * np.int64(B_fx)) >> np.int64(32)
+    assert np.any(trunc[tie > 1e-6] != want[tie > 1e-6])
+    A2, B2 = S.slide_constants(f0, df_s, [-4e-10], t_ref, f0_s, df, t_s)
+    assert np.any(S.slide_index(A2[0], B2, j)[tie > 1e-6] != want[tie > 1e-6])
