@@ -12,9 +12,15 @@ basis kernel, the Dirichlet kernel with fused 2F, and the toplist selection.
   python bench.py --coverage F | --noise-floor W | --algo ...   (variants)
 
 The JSON line's `roofline` is the Dirichlet kernel's ALU bound (100 flop per
-pair of the direct sum), with the DRAM traffic and, for the table forms, the
-shared-memory bound (`roofline.shared_memory`) taken from the committed ncu
-summary while it matches the kernel source.
+pair of the direct sum, peak from the queried SM count), with the DRAM traffic
+and, for the table forms, the shared-memory bound (`roofline.shared_memory`)
+taken from the committed ncu summary while it matches the kernel source.
+`plain_fp32` times the plain FP32 form (direct Dirichlet sum) on the same
+workunit; `twoF_error` gives max and p99 |GPU 2F - oracle 2F| of both forms
+on the CPU baseline's sample (16 sky points x 1800 f x 10 fdot x 2400 SFTs,
+signals added by the FP64 oracle), which the plain-C FP64 oracle times on
+every host core (`cpu_baseline`, also one core); `--impl reference` times the
+same oracle on the same sample per step.
 
 Multi-GPU (torchrun, one process per GPU): sky points are sharded, each rank
 runs a full workunit-sized step on its shard (weak scaling) and the local
@@ -39,7 +45,6 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 FLOP_PER_PAIR = 100.0          # direct-sum FP32 work of one template.SFT pair: 16 bins x (4 + 1) + 20 per-pair constants
-N_SM = 152
 FP32_LANES = 128
 METRIC = "template·SFT pairs/s (2F) on 1 GB300, chosen vs plain FP32 form at stated 2F error"
 KERNEL_SOURCES = {"direct": ["fstat_internal.cuh", "dirichlet.cuh", "dirichlet_c64.cu", "dirichlet_f16.cu",
@@ -181,42 +186,147 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
-def cpu_baseline(w, n_fdot_sample=None):
-    """The FP64 oracle as it stands, single process, on one sky point of the
-    workload (all frequencies, all spindowns, all SFTs of both detectors)."""
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the machine type)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
+
+
+N_SAMPLE_SKY = 16
+
+
+def baseline_sample(w):
+    """The bounded sample of the workunit that the CPU oracle times and that
+    the GPU's 2F error is measured on: the 8 sky points of the lattice
+    nearest to the 8 signals, then the first sky points, up to 16; every
+    frequency, spindown and SFT of each (16 x 1800 x 10 x 2400 = 6.9e8 pairs).
+    Signals are added to the SFTs by the FP64 oracle."""
+    from oracle import fstat_oracle as O
+    from workload import DetectorData, TemplateBank
+    sky = w.bank.sky
+    n = np.stack([np.cos(sky[:, 1]) * np.cos(sky[:, 0]), np.cos(sky[:, 1]) * np.sin(sky[:, 0]), np.sin(sky[:, 1])], 1)
+    pick = []
+    for inj in w.injections:
+        v = np.array([math.cos(inj.delta) * math.cos(inj.alpha), math.cos(inj.delta) * math.sin(inj.alpha),
+                      math.sin(inj.delta)])
+        i = int(np.argmax(n @ v))
+        if i not in pick:
+            pick.append(i)
+    i = 0
+    while len(pick) < N_SAMPLE_SKY:
+        if i not in pick:
+            pick.append(i)
+        i += 1
+    pick = sorted(pick)
+    bins = O.inject(w.detectors, w.T, w.k_lo, w.injections, w.bank.t_ref)
+    dets = [DetectorData(d.lat, d.lon, d.az, d.t_start, b) for d, b in zip(w.detectors, bins)]
+    sub = TemplateBank(sky[pick], w.bank.f0, w.bank.df, w.bank.n_f, w.bank.fdot, w.bank.t_ref)
+    return pick, dets, bins, sub
+
+
+def cpu_oracle_run(w, dets, sub, threads: int, n_sky: int | None = None):
+    """The plain-C FP64 oracle as it stands over the sample's first n_sky sky
+    points (all by default) on `threads` host threads: (pairs/s, pairs,
+    seconds, 2F [n_sky][n_fdot][n_f])."""
+    from oracle import c_oracle as CO
+    sel = range(sub.n_sky if n_sky is None else n_sky)
+    t0 = time.perf_counter()
+    out = CO.compute_fstat_freq_band(dets, w.T, w.k_lo, w.dterms, sub, sky_indices=sel, threads=threads)
+    dt = time.perf_counter() - t0
+    pairs = len(sel) * sub.n_f * sub.n_fdot * w.n_sft_total
+    return pairs / dt, pairs, dt, out
+
+
+def cpu_baseline(w, gpu_error=None):
+    """The oracle on the host cores: all cores on the 16-sky sample, one core
+    on one sky point of it (the plain-C oracle), and the numpy oracle on one
+    sky point x 2 spindowns; the numbers the 2F error is measured against come
+    from the all-core run.  gpu_error(pick, bins, sub, ref) -> dict, if given,
+    measures the GPU's 2F on the same sample against the oracle's."""
     from oracle import fstat_oracle as O
     from workload import TemplateBank
-    bank = w.bank
-    fd = bank.fdot if n_fdot_sample is None else bank.fdot[:n_fdot_sample]
-    sub = TemplateBank(bank.sky[:1], bank.f0, bank.df, bank.n_f, fd, bank.t_ref)
+    nproc = os.cpu_count() or 1
+    pick, dets, bins, sub = baseline_sample(w)
+    v_all, p_all, t_all, ref = cpu_oracle_run(w, dets, sub, nproc)
+    v_one, p_one, t_one, _ = cpu_oracle_run(w, dets, sub, 1, n_sky=1)
+    one = TemplateBank(sub.sky[:1], sub.f0, sub.df, sub.n_f, sub.fdot[:2], sub.t_ref)
     t0 = time.perf_counter()
-    O.compute_fstat_freq_band(w.detectors, w.T, w.k_lo, w.dterms, sub)
-    dt = time.perf_counter() - t0
-    pairs = sub.n_f * sub.n_fdot * w.n_sft_total
-    return pairs / dt, pairs, dt
+    O.compute_fstat_freq_band(dets, w.T, w.k_lo, w.dterms, one)
+    t_np = time.perf_counter() - t0
+    p_np = one.n_f * one.n_fdot * w.n_sft_total
+    out = {"value": v_all, "unit": "pairs/s", "cores": min(nproc, sub.n_sky), "kind": "oracle",
+           "sample": f"{sub.n_sky} sky (lattice points nearest the 8 signals, then the first) x {sub.n_f} f x "
+                     f"{sub.n_fdot} fdot x {w.n_sft_total} SFT = {p_all:.3g} pairs, plain-C FP64 oracle on "
+                     f"{min(nproc, sub.n_sky)} threads, {t_all:.1f} s",
+           "nproc": nproc, "cpu_model": cpu_model(),
+           "single_core": {"value": v_one, "unit": "pairs/s", "sample": f"1 sky x {sub.n_f} f x {sub.n_fdot} fdot "
+                                                                        f"x {w.n_sft_total} SFT, {t_one:.1f} s"},
+           "numpy_single_core": {"value": p_np / t_np, "unit": "pairs/s",
+                                 "sample": f"1 sky x {one.n_f} f x {one.n_fdot} fdot x {w.n_sft_total} SFT, "
+                                           f"{t_np:.1f} s"}}
+    if gpu_error is not None:
+        out["gpu_2F_error"] = gpu_error(pick, bins, sub, ref)
+    return out
+
+
+def twoF_error_stats(got, ref) -> dict:
+    """max and p99 of |GPU 2F - oracle 2F| and the largest ratio to the
+    tolerance 1e-4 2F + 1e-3, over every template of the sample."""
+    got = np.asarray(got, np.float64).ravel()
+    ref = np.asarray(ref, np.float64).ravel()
+    err = np.abs(got - ref)
+    return {"max_abs": float(err.max()), "p99_abs": float(np.percentile(err, 99)),
+            "max_over_tol": float(np.max(err / (1e-4 * ref + 1e-3))), "templates": int(ref.size),
+            "max_2F": float(ref.max())}
+
+
+def shared_config(args) -> dict:
+    """The workload description both arms print."""
+    return {"workload": "plain workunit: 2 det x 1200 gapped SFT (T=1800 s), 1 Hz band at 100 Hz, "
+                        "8 injected signals; 10000 sky x 1800 f x 10 fdot, D=8, top-1000",
+            "form": args.form, "pairs_per_step_per_gpu": 432000000000,
+            "l2": "per-step working set ~5 GB (bases, 2F array) > 129 MB L2; L2 flushed before timing"}
 
 
 def run_reference(args):
+    """The FP64 oracle on the host cores: each step is the plain-C oracle on
+    the 16-sky sample of the workunit (6.9e8 pairs), every core."""
     rank, _, world = dist_env()
     if rank != 0:
         return
     w = workload(0, 1, args.n_sky)
-    # each step: the oracle on 1 sky x 1800 f x 1 fdot x 2400 SFTs (4.3e6 pairs)
+    nproc = os.cpu_count() or 1
+    _, dets, _, sub = baseline_sample(w)
     for _ in range(args.warmup):
-        cpu_baseline(w, n_fdot_sample=1)
+        cpu_oracle_run(w, dets, sub, nproc)
     tot_pairs, tot_t = 0, 0.0
     for _ in range(args.steps):
-        _, p, t = cpu_baseline(w, n_fdot_sample=1)
+        _, p, t, _ = cpu_oracle_run(w, dets, sub, nproc)
         tot_pairs += p
         tot_t += t
     v = tot_pairs / tot_t
+    sample = (f"{sub.n_sky} sky (lattice points nearest the 8 signals, then the first) x {sub.n_f} f x "
+              f"{sub.n_fdot} fdot x {w.n_sft_total} SFT per step, plain-C FP64 oracle")
     line = {"metric": METRIC, "value": v, "unit": "pairs/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": "plain workunit: 2 det x 1200 SFT, 10000 sky x 1800 f x 10 fdot, D=8",
-                       "sample": "1 sky x 1800 f x 1 fdot x 2400 SFT per step"},
-            "cpu_baseline": {"value": v, "unit": "pairs/s", "cores": 1, "kind": "oracle",
-                             "sample": "1 sky x 1800 f x 1 fdot x 2400 SFT per step"},
+            "config": shared_config(args),
+            "cpu_baseline": {"value": v, "unit": "pairs/s", "cores": min(nproc, sub.n_sky), "kind": "oracle",
+                             "sample": sample, "nproc": nproc, "cpu_model": cpu_model()},
             "e2e": {"value": v, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -309,7 +419,8 @@ def run_semicoherent(args):
     except (OSError, ValueError, KeyError):
         pass
     achieved = FLOP_PER_PAIR * seg_pairs / (k_dir / 1e3) / 1e12
-    peak = N_SM * FP32_LANES * 2 * 2070.0 * 1e6 / 1e12
+    n_sm = int(torch.cuda.get_device_properties(local_rank).multi_processor_count)
+    peak = n_sm * FP32_LANES * 2 * 2070.0 * 1e6 / 1e12
     line = {"metric": METRIC, "value": seg_pairs * args.steps / (ms / 1e3), "unit": "pairs/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -620,13 +731,24 @@ def main():
                            "algo": algo_of(g2.plan()["variant"])}
             g2.close()
 
+    # the plain FP32 form (direct Dirichlet sum, FP32 bins) on the same workunit
+    plain = None
+    if rank == 0 and world == 1 and algo_of(plan.get("variant", 0)) != "direct":
+        g2 = make("c64", False, "direct")
+        ms2, kd2, _, _ = timed_run(g2, 2, 1)
+        plain = {"value": n_pairs * 2 / (ms2 / 1e3), "unit": "pairs/s", "ms_per_step": ms2 / 2,
+                 "dirichlet_ms": kd2, "algo": "direct", "steps": 2, "warmup": 1}
+        g2.close()
+
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
         return
 
-    clock_mhz = 2070.0
-    peak = N_SM * FP32_LANES * 2 * clock_mhz * 1e6 / 1e12       # TFLOP/s, recipe unit counts, max clock
+    props = torch.cuda.get_device_properties(local_rank)
+    n_sm = int(props.multi_processor_count)
+    clock_mhz = float(clocks["sm_max_mhz"]) if clocks and clocks.get("sm_max_mhz") else 2070.0
+    peak = n_sm * FP32_LANES * 2 * clock_mhz * 1e6 / 1e12       # TFLOP/s, recipe unit counts, max clock
     achieved = FLOP_PER_PAIR * n_pairs / (k_dir / 1e3) / 1e12
     vid = plan.get("variant", 0)
     algo_used = algo_of(vid)
@@ -634,43 +756,70 @@ def main():
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": ncu_traffic(args.form, algo_used), "kernel": kernel_name,
                 "dirichlet_ms": k_dir, "step_ms_device": k_step,
-                "peak_note": "152 SM x 128 FP32 lanes x 2 flop x 2070 MHz (max SM clock)"}
+                "peak_note": f"{n_sm} SM (queried) x {FP32_LANES} FP32 lanes x 2 flop x {clock_mhz:.0f} MHz "
+                             "(maximum SM clock)"}
     if clocks and clocks.get("sm_mhz"):
-        roofline["frac_at_sampled_clock"] = achieved / (N_SM * FP32_LANES * 2 * clocks["sm_mhz"] * 1e6 / 1e12)
+        roofline["frac_at_sampled_clock"] = achieved / (n_sm * FP32_LANES * 2 * clocks["sm_mhz"] * 1e6 / 1e12)
     # the table forms are bound by shared-memory loads: that bound too, from the
     # ncu wavefront count per pair (128 B each) against 128 B per SM and clock
     ent = ncu_entry(args.form, algo_used)
     if ent and ent.get("smem_wavefronts_per_pair"):
         smem_b = ent["smem_wavefronts_per_pair"] * 128.0 * n_pairs
-        smem_peak = N_SM * 128.0 * clock_mhz * 1e6 / 1e12       # TB/s
+        smem_peak = n_sm * 128.0 * clock_mhz * 1e6 / 1e12       # TB/s
         roofline["shared_memory"] = {"achieved": smem_b / (k_dir / 1e3) / 1e12, "peak": smem_peak, "unit": "TB/s",
                                      "frac": smem_b / (k_dir / 1e3) / 1e12 / smem_peak,
                                      "bytes_per_pair": ent["smem_wavefronts_per_pair"] * 128.0}
+    config = shared_config(args)
+    config["pairs_per_step_per_gpu"] = n_pairs
+    if args.noise_floor:
+        config["noise_floor_half_window"] = args.noise_floor
+    if args.coverage:
+        config["coverage"] = args.coverage
     line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "step_ms": {"best": steps_ms[0], "median": steps_ms[len(steps_ms) // 2]} if steps_ms else None,
             "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": {"c64": "f32", "f16": "f16-storage/f32", "bf16": "bf16-storage/f32"}[args.form],
             "data": "synthetic",
-            "config": {"workload": "plain workunit: 2 det x 1200 gapped SFT (T=1800 s), 1 Hz band at 100 Hz, "
-                                   "8 injected signals; 10000 sky x 1800 f x 10 fdot, D=8, top-1000",
-                       "form": args.form, "algo": algo_used, "pairs_per_step_per_gpu": n_pairs,
-                       "noise_floor_half_window": args.noise_floor,
-                       "coverage": args.coverage or None,
-                       "l2": "per-step working set ~5 GB (bases, 2F array) > 129 MB L2; L2 flushed before timing",
-                       "plan": plan},
+            "config": config,
+            "kernel": {"algo": algo_used, "plan": plan},
             "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms_max},
             "roofline": roofline,
             "gpu_launches": launches,
             "clocks": clocks,
             "top": {"2F": float(val[0]), "idx": int(idx[0])}}
+    if plain:
+        plain["chosen_over_plain"] = value / plain["value"]
+        line["plain_fp32"] = plain
     if forms:
         line["other_forms"] = forms
+
+    def gpu_error(pick, bins, sub, ref):
+        """The GPU's 2F on the CPU baseline's sample (the same bins, signals
+        added by the oracle), chosen form and plain FP32 form, against the
+        oracle's all-core run."""
+        import dataclasses
+        wl = dataclasses.replace(w, bank=sub)
+        out = {}
+        for name, form, algo in (("chosen", args.form, args.algo), ("plain_fp32", "c64", "direct")):
+            g3 = fs.FStat(local_rank, dterms=w.dterms, topk=10, bins_form=form, algo=algo, tile_m=args.tile_m,
+                          tile_warps=args.tile_warps, sft_chunk=args.sft_chunk)
+            try:
+                g3.load_workload(wl, bins_override=bins)
+                g3.compute(stream)
+                got = g3.twoF()
+                st = twoF_error_stats(got, ref)
+                st["variant"] = g3.plan()["variant"]
+                out[name] = st
+            finally:
+                g3.close()
+        return out
+
     if world == 1 and not args.no_cpu_baseline:
-        v, p, t = cpu_baseline(w)
-        line["cpu_baseline"] = {"value": v, "unit": "pairs/s", "cores": 1, "kind": "oracle",
-                                "sample": f"1 sky x 1800 f x 10 fdot x 2400 SFT ({p:.3g} pairs, {t:.1f} s)"}
+        line["cpu_baseline"] = cpu_baseline(w, gpu_error if not (args.coverage or args.noise_floor) else None)
+        if "gpu_2F_error" in line["cpu_baseline"]:
+            line["twoF_error"] = line["cpu_baseline"]["gpu_2F_error"]
     g.close()
     print(json.dumps(line))
     if world > 1:

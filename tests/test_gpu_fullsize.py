@@ -116,3 +116,91 @@ def test_full_workunit_sampled_with_coverage(lib, full):
         jobs.append((one, lo - j, hi - j))
     ref = np.array(_pool_map(_coverage_job, jobs, w, dets))
     assert np.all(np.abs(got - ref) <= REL * ref + ABS), np.max(np.abs(got - ref) - REL * ref)
+
+
+# ---------------------------------------------------------------- the whole toplist against the cached oracle
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _read_golden():
+    """tests/golden/config1_top.txt (header facts, top 1200) and
+    config1_sky_max.txt, written by tests/golden/make_config1_toplist.py with
+    the FP64 oracle over every template of the workunit."""
+    head, rows = {}, []
+    with open(os.path.join(GOLDEN, "config1_top.txt")) as fh:
+        for line in fh:
+            if line.startswith("#"):
+                parts = line[1:].split()
+                if parts and parts[0] in ("n_templates", "mean_2F"):
+                    head[parts[0]] = float(parts[1])
+                elif parts and parts[0] == "count_above":
+                    head["count_above"] = [(float(a), int(b)) for a, b in (p.split(":") for p in parts[1:])]
+                continue
+            r, i, v = line.split()
+            rows.append((int(i), float(v)))
+    sky_max = np.loadtxt(os.path.join(GOLDEN, "config1_sky_max.txt"), comments="#")
+    idx = np.array([r[0] for r in rows], dtype=np.int64)
+    val = np.array([r[1] for r in rows], dtype=np.float64)
+    return head, idx, val, sky_max
+
+
+def test_full_workunit_toplist_against_cached_oracle(lib, full):
+    """The top-1000 of the whole workunit (1.8e8 templates) in the bench's
+    launch configuration, against the FP64 oracle's ranking of every template
+    (C10: rank by rank up to near-ties within the 2F tolerance, membership
+    exact outside the tolerance band of the K-th value), against a host sort
+    of the GPU's own 2F array, plus every sky point's maximum and global
+    facts of the whole 2F array."""
+    w, bins, dets = full
+    head, g_idx, g_val, sky_max = _read_golden()
+    K = w.topk
+    g = lib.FStat(0, topk=K)
+    try:
+        g.load_workload(w, bins_override=bins)
+        g.compute()
+        assert g.error_flags() == 0
+        assert g.plan()["variant"] == 112
+        idx, val = g.toplist(K)
+        allv = g.twoF()
+    finally:
+        g.close()
+    n = allv.size
+    assert n == int(head["n_templates"])
+    # (1) exact on the GPU's own values: (2F desc, index asc)
+    vk_gpu = np.partition(allv, n - K)[n - K]
+    cand = np.nonzero(allv >= vk_gpu)[0]
+    own = cand[np.lexsort((cand, -allv[cand].astype(np.float64)))][:K]
+    np.testing.assert_array_equal(idx, own)
+    np.testing.assert_array_equal(val, allv[own])
+    # (2) the oracle's values at every kept oracle rank, element by element
+    got = allv[g_idx].astype(np.float64)
+    assert np.all(np.abs(got - g_val) <= REL * g_val + ABS), np.max(np.abs(got - g_val) - REL * g_val)
+    # (3) C10 against the oracle's ranking
+    ref_of = dict(zip(g_idx.tolist(), g_val.tolist()))
+    missing = [int(i) for i in idx if int(i) not in ref_of]
+    if missing:    # GPU entries ranked below the kept oracle list: the oracle computes them one by one
+        from oracle import c_oracle as CO
+        vals = CO.compute_fstat_templates(dets, w.T, w.k_lo, w.dterms, w.bank, np.array(missing))
+        ref_of.update(zip(missing, vals.tolist()))
+    o_of_gpu = np.array([ref_of[int(i)] for i in idx])
+    vk = g_val[K - 1]
+    tol_k = REL * vk + ABS
+    sure = set(g_idx[:K][g_val[:K] > vk + 2 * tol_k].tolist())
+    assert sure <= set(idx.tolist())
+    assert np.all(o_of_gpu >= vk - 2 * tol_k)
+    tol_r = REL * g_val[:K] + ABS
+    assert np.all(np.abs(o_of_gpu - g_val[:K]) <= 2 * tol_r), np.max(np.abs(o_of_gpu - g_val[:K]) / tol_r)
+    swaps = int(np.sum(idx != g_idx[:K]))
+    print(f"workunit top-{K}: {swaps} positions hold a near-tie swap, {len(missing)} GPU entries below the "
+          f"oracle's first {g_idx.size}, {len(sure)} of {K} outside the K-th value's band")
+    # (4) every sky point's maximum
+    smax = allv.reshape(w.bank.n_sky, -1).max(axis=1).astype(np.float64)
+    assert np.all(np.abs(smax - sky_max) <= REL * sky_max + ABS), np.max(np.abs(smax - sky_max) - REL * sky_max)
+    # (5) global facts: the mean, and the counts above thresholds up to values within tolerance of them
+    mean = float(allv.astype(np.float64).mean())
+    assert abs(mean - head["mean_2F"]) <= REL * head["mean_2F"] + ABS
+    for thr, cnt in head["count_above"]:
+        c = int(np.sum(allv > thr))
+        near = int(np.sum(np.abs(allv - thr) <= REL * thr + ABS))
+        assert abs(c - cnt) <= near, (thr, c, cnt, near)
