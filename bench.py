@@ -50,9 +50,12 @@ METRIC = "template·SFT pairs/s (2F) on 1 GB300, chosen vs plain FP32 form at st
 KERNEL_SOURCES = {"direct": ["fstat_internal.cuh", "dirichlet.cuh", "dirichlet_c64.cu", "dirichlet_f16.cu",
                              "dirichlet_bf16.cu"],
                   "farpoly": ["fstat_internal.cuh", "dirichlet.cuh", "dirichlet_far.cu"],
-                  "sincpoly": ["fstat_internal.cuh", "dirichlet.cuh", "dirichlet_far.cu"]}
+                  "sincpoly": ["fstat_internal.cuh", "dirichlet.cuh", "dirichlet_far.cu"],
+                  "sincrows": ["fstat_internal.cuh", "dirichlet.cuh", "dirichlet_far.cu"],
+                  "sincpairs": ["fstat_internal.cuh", "dirichlet.cuh", "dirichlet_far.cu"]}
 KERNEL_NAMES = {"direct": "dirichlet_kernel", "farpoly": "dirichlet_far_kernel",
-                "sincpoly": "dirichlet_far_ring_kernel"}
+                "sincpoly": "dirichlet_far_ring_kernel", "sincrows": "dirichlet_rows_kernel",
+                "sincpairs": "dirichlet_ring2_kernel"}
 
 
 def parse():
@@ -78,7 +81,7 @@ def parse():
     ap.add_argument("--n-refine", type=int, default=8, help="patches refined per workunit (proposal mode)")
     ap.add_argument("--train-steps", type=int, default=6000, help="Adam steps (proposal mode)")
     ap.add_argument("--proposal-sft", type=int, default=800, help="SFTs per detector (proposal mode)")
-    ap.add_argument("--algo", default="auto", choices=["auto", "direct", "farpoly", "sincpoly"],
+    ap.add_argument("--algo", default="auto", choices=["auto", "direct", "farpoly", "sincpoly", "sincrows", "sincpairs"],
                     help="evaluation of the D-term kernel sum")
     ap.add_argument("--noise-floor", type=int, default=0,
                     help="running-median half window of the noise-floor normalisation (0 = off)")
@@ -103,6 +106,10 @@ def algo_of(variant: int) -> str:
     """Form of a plan's kernel variant id (include/fstat.h, fstat_get_plan)."""
     if variant < 100:
         return "direct"
+    if variant >= 127:
+        return "sincpairs"
+    if variant >= 120:
+        return "sincrows"
     return "sincpoly" if variant in (112, 113, 114, 115, 116, 118, 119) else "farpoly"
 
 
@@ -613,10 +620,10 @@ def main():
         n_pairs = w.bank.n_sky * w.bank.n_fdot * int(width.sum())
     stream = torch.cuda.Stream()
 
-    def make(form, kahan=False, algo=None):
-        g = fs.FStat(local_rank, dterms=w.dterms, topk=w.topk, bins_form=form, kahan=kahan, tile_m=args.tile_m,
-                     tile_warps=args.tile_warps, sft_chunk=args.sft_chunk,
-                     algo=args.algo if algo is None else algo)
+    def make(form, kahan=False, algo=None, tiles=True):
+        g = fs.FStat(local_rank, dterms=w.dterms, topk=w.topk, bins_form=form, kahan=kahan,
+                     tile_m=args.tile_m if tiles else 0, tile_warps=args.tile_warps if tiles else 0,
+                     sft_chunk=args.sft_chunk if tiles else 0, algo=args.algo if algo is None else algo)
         g.load_workload(w)
         g.inject(w.injections, w.bank.t_ref)
         if args.noise_floor:
@@ -734,7 +741,7 @@ def main():
     # the plain FP32 form (direct Dirichlet sum, FP32 bins) on the same workunit
     plain = None
     if rank == 0 and world == 1 and algo_of(plan.get("variant", 0)) != "direct":
-        g2 = make("c64", False, "direct")
+        g2 = make("c64", False, "direct", tiles=False)   # the planner's own tiles for the plain form
         ms2, kd2, _, _ = timed_run(g2, 2, 1)
         plain = {"value": n_pairs * 2 / (ms2 / 1e3), "unit": "pairs/s", "ms_per_step": ms2 / 2,
                  "dirichlet_ms": kd2, "algo": "direct", "steps": 2, "warmup": 1}
@@ -752,7 +759,7 @@ def main():
     achieved = FLOP_PER_PAIR * n_pairs / (k_dir / 1e3) / 1e12
     vid = plan.get("variant", 0)
     algo_used = algo_of(vid)
-    kernel_name = KERNEL_NAMES[algo_used] if vid < 107 else "dirichlet_far_ring_kernel"
+    kernel_name = KERNEL_NAMES[algo_used] if (vid < 107 or vid >= 120) else "dirichlet_far_ring_kernel"
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": ncu_traffic(args.form, algo_used), "kernel": kernel_name,
                 "dirichlet_ms": k_dir, "step_ms_device": k_step,
@@ -802,9 +809,10 @@ def main():
         import dataclasses
         wl = dataclasses.replace(w, bank=sub)
         out = {}
-        for name, form, algo in (("chosen", args.form, args.algo), ("plain_fp32", "c64", "direct")):
-            g3 = fs.FStat(local_rank, dterms=w.dterms, topk=10, bins_form=form, algo=algo, tile_m=args.tile_m,
-                          tile_warps=args.tile_warps, sft_chunk=args.sft_chunk)
+        for name, form, algo, tiles in (("chosen", args.form, args.algo, True), ("plain_fp32", "c64", "direct", False)):
+            g3 = fs.FStat(local_rank, dterms=w.dterms, topk=10, bins_form=form, algo=algo,
+                          tile_m=args.tile_m if tiles else 0, tile_warps=args.tile_warps if tiles else 0,
+                          sft_chunk=args.sft_chunk if tiles else 0)
             try:
                 g3.load_workload(wl, bins_override=bins)
                 g3.compute(stream)

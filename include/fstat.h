@@ -98,14 +98,29 @@ typedef struct {
  *   TMA-ring staging on a uniform spindown grid: P df T = 2 (5 or 7 templates
  *   per thread) or P df T = 1 with P = 8 (1 or 5); elsewhere it falls back
  *   to FARPOLY.
- * Batched workunits use the TMA-ring form where it applies, else DIRECT.
+ * SINCROWS (D = 8, no Kahan, uniform spindown grid of at least 4 spindowns,
+ *   no frequency coverage): the same sinc-polynomial records evaluated with
+ *   one frequency and up to 10 spindown rows per thread; a row whose window
+ *   and half bin equal the previous row's reuses the record held in
+ *   registers, so records are read once per run of rows instead of once per
+ *   template (plain tables, TMA-ring staging); elsewhere as SINCPOLY.
+ * SINCPAIRS (D = 8, no Kahan, P df T = 2, uniform spindown grid of at least
+ *   2 spindowns, no frequency coverage): the SINCPOLY ring with each thread
+ *   holding its templates in two adjacent spindown rows, one record serving
+ *   both rows where their windows and half bins agree; elsewhere as SINCPOLY.
+ * SINCROWS and SINCPAIRS give the same results within the stated tolerance
+ *   and are slower than SINCPOLY on the workunit-sized bank; they are kept as
+ *   options.  Batched workunits use the TMA-ring form where it applies, else
+ *   DIRECT.
  * AUTO: SINCPOLY where the TMA ring applies, else FARPOLY where it applies,
  *   else DIRECT. */
 typedef enum {
     FSTAT_ALGO_AUTO = 0,
     FSTAT_ALGO_DIRECT = 1,
     FSTAT_ALGO_FARPOLY = 2,
-    FSTAT_ALGO_SINCPOLY = 3
+    FSTAT_ALGO_SINCPOLY = 3,
+    FSTAT_ALGO_SINCROWS = 4,
+    FSTAT_ALGO_SINCPAIRS = 5
 } fstat_algo;
 
 typedef struct {

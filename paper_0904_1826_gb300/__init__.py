@@ -146,7 +146,7 @@ def fstat_version() -> str:
     return _lib.fstat_version().decode()
 
 
-ALGOS = {"auto": 0, "direct": 1, "farpoly": 2, "sincpoly": 3}
+ALGOS = {"auto": 0, "direct": 1, "farpoly": 2, "sincpoly": 3, "sincrows": 4, "sincpairs": 5}
 
 
 def fstat_create(device: int = 0, dterms: int = 8, bins_form="c64", topk: int = 1000, kahan: bool = False,

@@ -47,14 +47,22 @@ struct FarRow {
     int ring;   // compute warps of the TMA-ring staging (L = 2, uniform spindown grid), 0 = cp.async rounds
     bool sinc;  // sinc-polynomial form (whole window as one polynomial), else near pairs + far polynomial
     bool cov;   // per-SFT frequency coverage compiled in (ring only; single launches)
+    int rows;   // rows form: spindown rows per lane (one frequency per lane), 0 = templates along frequency
+    int minb;   // two-row tiles (sinc, L = 2): resident blocks per SM the kernel is built for, 0 = one row
 };
-const FarRow kFarVariants[] = {{7, 2, 0, false, false},  {5, 2, 0, false, false},  {9, 2, 0, false, false},
-                               {7, 1, 0, false, false},  {9, 1, 0, false, false},  {5, 1, 0, false, false},
-                               {1, 1, 0, false, false},  {5, 2, 8, false, false},  {7, 2, 8, false, false},
-                               {9, 2, 8, false, false},  {5, 2, 10, false, false}, {7, 2, 10, false, false},
-                               {5, 2, 10, true, false},  {7, 2, 10, true, false},  {5, 2, 8, true, false},
-                               {7, 2, 8, true, false},   {5, 2, 10, true, true},   {5, 2, 10, false, true},
-                               {5, 1, 8, true, false},   {1, 1, 8, true, false}};
+const FarRow kFarVariants[] = {{7, 2, 0, false, false, 0},  {5, 2, 0, false, false, 0},  {9, 2, 0, false, false, 0},
+                               {7, 1, 0, false, false, 0},  {9, 1, 0, false, false, 0},  {5, 1, 0, false, false, 0},
+                               {1, 1, 0, false, false, 0},  {5, 2, 8, false, false, 0},  {7, 2, 8, false, false, 0},
+                               {9, 2, 8, false, false, 0},  {5, 2, 10, false, false, 0}, {7, 2, 10, false, false, 0},
+                               {5, 2, 10, true, false, 0},  {7, 2, 10, true, false, 0},  {5, 2, 8, true, false, 0},
+                               {7, 2, 8, true, false, 0},   {5, 2, 10, true, true, 0},   {5, 2, 10, false, true, 0},
+                               {5, 1, 8, true, false, 0},   {1, 1, 8, true, false, 0},
+                               // rows form, in the order of FS_ROWS_VARIANTS: (R, NWC)
+                               {1, 1, 3, true, false, 10},  {1, 1, 4, true, false, 10},  {1, 1, 8, true, false, 10},
+                               {1, 1, 4, true, false, 5},   {1, 1, 8, true, false, 5},   {1, 1, 4, true, false, 8},
+                               {1, 1, 4, true, false, 4},
+                               // two-row tiles, in the order of FS_RING2_VARIANTS: (M, NWC, blocks per SM)
+                               {5, 2, 8, true, false, 0, 2},  {3, 2, 10, true, false, 0, 2}};
 constexpr int kNumFar = sizeof(kFarVariants) / sizeof(kFarVariants[0]);
 constexpr int kFarIdBase = 100;   // variant ids reported for the far-field form
 
@@ -66,6 +74,8 @@ struct Plan {
     bool far = false;   // far-field polynomial form (variant indexes kFarVariants)
     bool ring = false;  // far-field form with TMA-ring staging; C = stages, W includes the producer warp
     bool sinc = false;  // sinc-polynomial form (TMA ring only)
+    bool rows = false;  // rows form of the sinc polynomial: M = 1 frequency per lane, R rows (kFarVariants)
+    bool two = false;   // two-row tiles of the sinc ring form (L = 2)
     size_t smem = 0;
     long long grid = 0;
 };
@@ -368,13 +378,142 @@ void far_extent(const fstat_ctx* c, int w_pairs, int* xoff, int* n_pos) {
 // per block and SFT: ~40 instructions of set-up per thread plus ~58 per
 // template (polynomial, two near pairs, twiddle, accumulation, 6 table
 // loads), ~8 per staged table entry and plane, ~2000 per round (barrier).
+// Plan of the rows form (AUTO or SINCROWS, uniform spindown grid, no
+// coverage, at least 4 spindowns): the (R, NWC) variant with the least
+// modelled work.  Per lane and SFT ~45 instructions of set-up and ~26 per
+// row, idle lanes of the last column and idle rows of the last row chunk
+// included; ~0.05 per staged position and byte; blocks of the last wave.
+bool make_rows_plan(fstat_ctx* c, Plan& best) {
+    if (!c->fdot_uniform || c->have_cov || c->n_fdot < 4) return false;
+    if (c->opts.algo != FSTAT_ALGO_SINCROWS) return false;
+    if (c->opts.tile_m > 1) return false;   // templates along frequency requested
+    double best_cost = 1e300;
+    bool have = false;
+    for (int i = 0; i < kNumFar; ++i) {
+        const FarRow& v = kFarVariants[i];
+        if (!v.rows) continue;
+        if (c->opts.tile_warps > 0 && c->opts.tile_warps != v.ring + 1) continue;
+        const int F = 32 * v.ring;
+        const int n_col = (c->n_f + F - 1) / F;
+        const int n_rc = (c->n_fdot + v.rows - 1) / v.rows;
+        const int w_pairs = pairs_needed(c, F, 8);
+        int S = c->opts.sft_chunk > 0 ? c->opts.sft_chunk : 8;
+        while (S > 3 && ring_smem(S, w_pairs, true).total > 110 * 1024) --S;
+        const size_t smem = ring_smem(S, w_pairs, true).total;
+        if (smem > 220 * 1024) continue;
+        const double lanes = (double)n_col * F * n_rc;
+        const double per_lane = (45.0 + 26.0 * v.rows) * (1.0 + 0.2 / S);
+        const double cost = (double)c->n_sky * (lanes * per_lane + (double)n_col * n_rc * w_pairs * 96.0 * 0.05);
+        if (cost < best_cost * 0.999) {
+            best_cost = cost;
+            best = Plan{};
+            best.P = 1;
+            best.L = 1;
+            best.M = 1;
+            best.W = v.ring + 1;
+            best.C = S;
+            best.lg_row = F;
+            best.lg_cta = F;
+            best.n_col = n_col;
+            best.chunks_per_col = n_rc;
+            best.w_pairs = w_pairs;
+            best.w_tab = w_pairs;
+            best.variant = i;
+            best.far = true;
+            best.ring = true;
+            best.sinc = true;
+            best.rows = true;
+            best.smem = smem;
+            best.grid = (long long)c->n_sky * n_col * n_rc;
+            have = true;
+        }
+    }
+    return have;
+}
+
+// Plan of the two-row tiles (SINCPAIRS; sinc form, L = 2, uniform
+// spindown grid, no coverage, at least 2 spindowns).  Per thread and SFT
+// ~70 instructions of set-up and ~30 per template pair of rows; stages sized
+// for the variant's resident blocks per SM.
+bool make_ring2_plan(fstat_ctx* c, int P, int L, bool found, Plan& best) {
+    if (!found || L != 2 || !c->fdot_uniform || c->have_cov || c->n_fdot < 2) return false;
+    if (c->opts.algo != FSTAT_ALGO_SINCPAIRS) return false;
+    double best_cost = 1e300;
+    bool have = false;
+    for (int i = 0; i < kNumFar; ++i) {
+        const FarRow& v = kFarVariants[i];
+        if (!v.minb) continue;
+        if (c->opts.tile_m > 0 && c->opts.tile_m != v.M) continue;
+        if (c->opts.tile_warps > 0 && c->opts.tile_warps != v.ring + 1) continue;
+        if (v.ring % P != 0) continue;
+        const int PM = P * v.M;
+        const int lg_cta = 32 * v.ring / P;
+        const int n_pairs = (c->n_fdot + 1) / 2;
+        const int lg_max = std::min((c->n_f + PM - 1) / PM, lg_cta);
+        const size_t cap = (227 * 1024) / v.minb - 2048;
+        for (int lg_row = 1; lg_row <= lg_max; ++lg_row) {
+            const int col_w = lg_row * PM;
+            const int n_col = (c->n_f + col_w - 1) / col_w;
+            const int w_pairs = std::max(pairs_needed(c, col_w, 8), (v.M - 1) * L + 2 * 8 + 2);
+            int hf = (w_pairs + 1) / 2;
+            hf += ((4 - hf % 8) + 8) % 8;
+            const int w_tab = 2 * hf;
+            int S = c->opts.sft_chunk > 0 ? c->opts.sft_chunk : 8;
+            while (S > 2 && ring_smem(S, w_tab, true).total > cap) --S;
+            const size_t smem = ring_smem(S, w_tab, true).total;
+            if (smem > cap) continue;
+            double cost = 0.0;
+            int chunks_max = 0;
+            for (int col = 0; col < n_col; ++col) {
+                const int width = std::min(col_w, c->n_f - col * col_w);
+                const int Gc = (width + PM - 1) / PM;
+                const long long LG = (long long)n_pairs * Gc;
+                const int chunks = (int)((LG + lg_cta - 1) / lg_cta);
+                chunks_max = std::max(chunks_max, chunks);
+                for (int k = 0; k < chunks; ++k) {
+                    const long long lgs = std::min<long long>(lg_cta, LG - (long long)k * lg_cta);
+                    const long long warps = (lgs + 31) / 32 * P;
+                    cost += (double)warps * 32.0 * (70.0 + 30.0 * 2 * v.M) * (1.0 + 0.2 / S) + 0.05 * w_pairs * 96.0;
+                }
+            }
+            if (cost < best_cost * 0.999) {
+                best_cost = cost;
+                best = Plan{};
+                best.P = P;
+                best.L = L;
+                best.M = v.M;
+                best.W = v.ring + 1;
+                best.C = S;
+                best.lg_row = lg_row;
+                best.lg_cta = lg_cta;
+                best.n_col = n_col;
+                best.chunks_per_col = chunks_max;
+                best.w_pairs = w_pairs;
+                best.w_tab = w_tab;
+                best.variant = i;
+                best.far = true;
+                best.ring = true;
+                best.sinc = true;
+                best.two = true;
+                best.smem = smem;
+                best.grid = (long long)c->n_sky * n_col * chunks_max;
+                have = true;
+            }
+        }
+    }
+    return have;
+}
+
 bool make_far_plan(fstat_ctx* c, int P, int L, bool found, Plan& best) {
+    if (c->opts.algo == FSTAT_ALGO_SINCROWS && make_rows_plan(c, best)) return true;
+    if (make_ring2_plan(c, P, L, found, best)) return true;
     bool have_ring = false;
     // TMA-ring form first: L = 2, compact spindown bases
     // default: 10 compute warps + 1 copy warp (measured fastest on GB300); tile_warps 9 / 11 choose 8 / 10
     // AUTO takes the sinc-polynomial form where the ring applies (1027 ms per
     // workunit launch on GB300 against 1105 ms for near pairs + far polynomial)
-    const bool want_sinc = c->opts.algo == FSTAT_ALGO_SINCPOLY || c->opts.algo == FSTAT_ALGO_AUTO;
+    const bool want_sinc = c->opts.algo == FSTAT_ALGO_SINCPOLY || c->opts.algo == FSTAT_ALGO_AUTO ||
+                           c->opts.algo == FSTAT_ALGO_SINCROWS || c->opts.algo == FSTAT_ALGO_SINCPAIRS;
     // L = 1 (P = 8) runs the ring in the sinc form only, with plain tables
     const bool ring_l = L == 2 || (L == 1 && want_sinc && !c->have_cov);
     if (found && ring_l && c->fdot_uniform && (c->opts.tile_warps == 0 || c->opts.tile_warps >= 9)) {
@@ -393,7 +532,8 @@ bool make_far_plan(fstat_ctx* c, int P, int L, bool found, Plan& best) {
             int fid = -1;
             for (int i = 0; i < kNumFar; ++i)
                 if (kFarVariants[i].ring == nwc && kFarVariants[i].M == M_ && kFarVariants[i].L == L &&
-                    kFarVariants[i].sinc == want_sinc && kFarVariants[i].cov == c->have_cov)
+                    kFarVariants[i].sinc == want_sinc && kFarVariants[i].cov == c->have_cov && !kFarVariants[i].rows &&
+                    !kFarVariants[i].minb)
                     fid = i;
             if (fid < 0) continue;
             const int PM = P * M_;
@@ -467,7 +607,9 @@ bool make_far_plan(fstat_ctx* c, int P, int L, bool found, Plan& best) {
         if (M_ > 1 && !found) continue;
         int fid = -1;
         for (int i = 0; i < kNumFar; ++i)
-            if (kFarVariants[i].ring == 0 && !kFarVariants[i].sinc && kFarVariants[i].M == M_ && kFarVariants[i].L == Lq) fid = i;
+            if (kFarVariants[i].ring == 0 && !kFarVariants[i].sinc && !kFarVariants[i].rows && kFarVariants[i].M == M_ &&
+                kFarVariants[i].L == Lq)
+                fid = i;
         if (fid < 0) continue;
         const int Pv = found ? P : 1;
         const int PM = Pv * M_;
@@ -777,8 +919,10 @@ int fstat_create(fstat_ctx** out, int device, const fstat_opts* opts) {
     if (o.bins_form < 0 || o.bins_form > 2) return FSTAT_EINVAL;
     if (o.tile_m < 0 || o.tile_warps < 0 || o.tile_warps > 11 || o.sft_chunk < 0 || o.sft_chunk > 64)
         return FSTAT_EINVAL;
-    if (o.algo < FSTAT_ALGO_AUTO || o.algo > FSTAT_ALGO_SINCPOLY) return FSTAT_EINVAL;
-    if ((o.algo == FSTAT_ALGO_FARPOLY || o.algo == FSTAT_ALGO_SINCPOLY) && (o.dterms != 8 || o.kahan))
+    if (o.algo < FSTAT_ALGO_AUTO || o.algo > FSTAT_ALGO_SINCPAIRS) return FSTAT_EINVAL;
+    if ((o.algo == FSTAT_ALGO_FARPOLY || o.algo == FSTAT_ALGO_SINCPOLY || o.algo == FSTAT_ALGO_SINCROWS ||
+         o.algo == FSTAT_ALGO_SINCPAIRS) &&
+        (o.dterms != 8 || o.kahan))
         return FSTAT_EINVAL;
     int n_dev = 0;
     if (cudaGetDeviceCount(&n_dev) != cudaSuccess || device < 0 || device >= n_dev) return FSTAT_ECUDA;
@@ -1502,8 +1646,10 @@ int fstat_autotune(fstat_ctx* c, void* cuda_stream, int32_t* out) {
         c->opts = saved;
         return rc;
     }
-    std::vector<int> Ms;
-    if (c->plan.M == 1) Ms = {1};
+    std::vector<int> Ms;   // 0: the planner's own choice of form (the rows form where it applies)
+    if (c->plan.rows) Ms = {0, 5, 7};
+    else if (c->plan.two) Ms = {5, 3};
+    else if (c->plan.M == 1) Ms = {1};
     else if (c->opts.kahan) Ms = {5};
     else if (c->plan.L == 2 || c->plan.far) Ms = {5, 7, 9};
     else Ms = {7, 9};
@@ -1596,7 +1742,11 @@ int fstat_batch_add(fstat_ctx* c, const fstat_workunit* wu, int32_t* wu_id) {
     // the persistent kernels exist for the direct and the ring forms: a workunit
     // the far-field form would stage in rounds runs the direct form, alone or batched
     Plan pl;
-    if (make_plan(w, pl) == FSTAT_OK && pl.far && (!pl.ring || pl.L != 2)) w->opts.algo = FSTAT_ALGO_DIRECT;
+    if (make_plan(w, pl) == FSTAT_OK && (pl.rows || pl.two)) {   // no persistent form of these: the one-row ring
+        w->opts.algo = FSTAT_ALGO_SINCPOLY;
+        if (make_plan(w, pl) != FSTAT_OK) pl = Plan{};
+    }
+    if (pl.far && (!pl.ring || pl.L != 2)) w->opts.algo = FSTAT_ALGO_DIRECT;
     w->plan_valid = false;
     w->err.clear();
     c->wus.push_back(w);
@@ -1733,7 +1883,7 @@ int fstat_batch_compute(fstat_ctx* c, void* cuda_stream) {
         w->stream = s;
         int rc = prepare(w, s);
         if (rc != FSTAT_OK) return fail(c, rc, "workunit: %s", w->err.c_str());
-        if (w->plan.far && (!w->plan.ring || w->plan.L != 2)) {   // persistent kernels: direct and L = 2 ring forms
+        if (w->plan.far && (!w->plan.ring || w->plan.L != 2 || w->plan.rows || w->plan.two)) {   // persistent: direct, one-row L = 2 ring
             w->opts.algo = FSTAT_ALGO_DIRECT;
             w->plan_valid = false;
             c->graph_valid = false;

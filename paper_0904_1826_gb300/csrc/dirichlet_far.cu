@@ -539,6 +539,101 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
     return false;
 }
 
+// The ring's producer warp: fetches the window bases of 32 SFTs at a time
+// (one per lane, so the loads overlap); lane 0 then waits for each SFT's
+// stage to be free, writes its window base and coverage, and copies its
+// constants and table rows into the stage with bulk copies under the stage's
+// full barrier.  Returns (lane 0) the number of stages issued.
+template <bool SINC, bool COV, int L>
+__device__ __forceinline__ int ring_produce(const DirichletParams& p, const RingSmem& lay, int S, unsigned char* smem,
+                                            uint32_t sb, volatile int* ctrl, size_t meta0, int j_col0, int lane) {
+    constexpr int D = 8;
+    auto full_bar = [&](int s) { return sb + (uint32_t)(lay.bars + 16 * (size_t)s); };
+    auto empty_bar = [&](int s) { return sb + (uint32_t)(lay.bars + 16 * (size_t)s + 8); };
+    // the warp fetches the window bases of 32 SFTs at a time (one per lane,
+    // so the loads overlap); lane 0 then waits, stages and copies each SFT
+    const int nh = p.n_pos >> 1;
+    const int half = p.w_tab >> 1;
+    const int n0 = (p.w_pairs + 1) >> 1, n1 = p.w_pairs >> 1;
+    // per position 16 + 48 bytes (far field) or 2 x 48 bytes (sinc)
+    const uint32_t bytes = 48u + 32u + (uint32_t)(n0 + n1) * (SINC ? 96u : 64u);
+    int a = 0;
+    bool stop = false;
+    int pslot = 0;            // slot of SFT a
+    uint32_t pparity = 0;     // parity of the empty phase the next reuse of pslot waits for
+    const int n_issue = p.ring_stop >= 0 ? min(p.ring_stop, p.n_sft) : p.n_sft;
+    for (int a0 = 0; a0 < n_issue && !stop; a0 += 32) {
+        int x_lane = 0;
+        int2 cv_lane = make_int2(0, 0x7fffffff);
+        if (COV && a0 + lane < p.n_sft) cv_lane = p.cov[a0 + lane];
+        if (a0 + lane < p.n_sft) {
+            const SkySftMeta* gm = p.meta + meta0 + a0 + lane;
+            x_lane = (int)(((gm->khmin + (long long)j_col0 * gm->dk) >> 32) - p.k_lo) - (D - 1) + p.xoff;
+        }
+        const int n_here = min(32, n_issue - a0);
+        for (int j = 0; j < n_here; ++j) {
+            int x0 = __shfl_sync(0xffffffffu, x_lane, j);
+            const int clo = __shfl_sync(0xffffffffu, cv_lane.x, j);
+            const int chi = __shfl_sync(0xffffffffu, cv_lane.y, j);
+            if (lane == 0) {
+                a = a0 + j;
+                if (a >= S && !mbar_wait<128>(empty_bar(pslot), pparity)) {
+                    ctrl[1] = 1;
+                    atomicOr(p.err, 4);
+                    stop = true;
+                } else if (ctrl[1]) {
+                    stop = true;
+                } else {
+                    if (x0 < 0 || x0 + p.w_pairs > p.n_pos) {   // outside the padded tables: clamp, flag
+                        atomicOr(p.err, 1);
+                        x0 = max(0, min(x0, p.n_pos - p.w_pairs));
+                    }
+                    unsigned char* st = smem + (size_t)pslot * lay.stage;
+                    *reinterpret_cast<int4*>(st + lay.lo) = make_int4(x0 - p.xoff, 0, clo, chi);
+                    const uint32_t ss = sb + (uint32_t)((size_t)pslot * lay.stage);
+                    const uint32_t fb = full_bar(pslot);
+                    mbar_expect_tx(fb, bytes);
+                    bulk_g2s(ss + (uint32_t)lay.meta, p.meta + meta0 + a, 48, fb);
+                    bulk_g2s(ss + (uint32_t)lay.base, p.base + meta0 + a, 32, fb);
+                    if (L == 1) {   // plain tables: one run of w_pairs positions per plane
+#pragma unroll
+                        for (int hb = 0; hb < 2; ++hb)
+                            bulk_g2s(ss + (uint32_t)(hb * lay.plane),
+                                     p.pcoef + 3 * (((size_t)a * 2 + hb) * p.n_pos + x0),
+                                     (uint32_t)p.w_pairs * 48u, fb);
+                    }
+#pragma unroll
+                    for (int h = 0; h < (L == 2 ? 2 : 0); ++h) {
+                        const int cnt = h ? n1 : n0;
+                        const size_t go = (size_t)a * p.n_pos + (size_t)((x0 + h) & 1) * nh + ((x0 + h) >> 1);
+                        if (SINC) {
+                            const size_t gx = go - (size_t)a * p.n_pos;   // position within the SFT's row
+#pragma unroll
+                            for (int hb = 0; hb < 2; ++hb)
+                                bulk_g2s(ss + (uint32_t)(hb * lay.plane + (size_t)h * half * 48),
+                                         p.pcoef + 3 * (((size_t)a * 2 + hb) * p.n_pos + gx),
+                                         (uint32_t)cnt * 48u, fb);
+                        } else {
+                            bulk_g2s(ss + (uint32_t)(lay.pairs + (size_t)h * half * 16), p.ptab + go,
+                                     (uint32_t)cnt * 16u, fb);
+                            bulk_g2s(ss + (uint32_t)(lay.coef + (size_t)h * half * 48), p.pcoef + 3 * go,
+                                     (uint32_t)cnt * 48u, fb);
+                        }
+                    }
+                    ++a;
+                    if (++pslot == S) {   // the next use of slot 0 waits for the phase after this one
+                        pslot = 0;
+                        if (a > S) pparity ^= 1u;
+                    }
+                }
+            }
+            stop = __shfl_sync(0xffffffffu, stop, 0);
+            if (stop) break;
+        }
+    }
+    return a;
+}
+
 // Uniform spindown grid; L = 2 (tables split by position parity, two runs
 // per table and SFT) or L = 1 (sinc form only: plain tables, one run).
 // Warps 0..NW-1 compute, warp NW produces.
@@ -594,88 +689,8 @@ __device__ __forceinline__ void far_ring_block(const DirichletParams& p, long lo
 
     const size_t meta0 = (size_t)sky * p.n_sft;
     if (producer) {
-        // the warp fetches the window bases of 32 SFTs at a time (one per lane,
-        // so the loads overlap); lane 0 then waits, stages and copies each SFT
-        const int nh = p.n_pos >> 1;
-        const int half = p.w_tab >> 1;
-        const int n0 = (p.w_pairs + 1) >> 1, n1 = p.w_pairs >> 1;
-        // per position 16 + 48 bytes (far field) or 2 x 48 bytes (sinc)
-        const uint32_t bytes = 48u + 32u + (uint32_t)(n0 + n1) * (SINC ? 96u : 64u);
-        int a = 0;
-        bool stop = false;
-        int pslot = 0;            // slot of SFT a
-        uint32_t pparity = 0;     // parity of the empty phase the next reuse of pslot waits for
-        const int n_issue = p.ring_stop >= 0 ? min(p.ring_stop, p.n_sft) : p.n_sft;
-        for (int a0 = 0; a0 < n_issue && !stop; a0 += 32) {
-            int x_lane = 0;
-            int2 cv_lane = make_int2(0, 0x7fffffff);
-            if (COV && a0 + lane < p.n_sft) cv_lane = p.cov[a0 + lane];
-            if (a0 + lane < p.n_sft) {
-                const SkySftMeta* gm = p.meta + meta0 + a0 + lane;
-                x_lane = (int)(((gm->khmin + (long long)j_col0 * gm->dk) >> 32) - p.k_lo) - (D - 1) + p.xoff;
-            }
-            const int n_here = min(32, n_issue - a0);
-            for (int j = 0; j < n_here; ++j) {
-                int x0 = __shfl_sync(0xffffffffu, x_lane, j);
-                const int clo = __shfl_sync(0xffffffffu, cv_lane.x, j);
-                const int chi = __shfl_sync(0xffffffffu, cv_lane.y, j);
-                if (lane == 0) {
-                    a = a0 + j;
-                    if (a >= S && !mbar_wait<128>(empty_bar(pslot), pparity)) {
-                        ctrl[1] = 1;
-                        atomicOr(p.err, 4);
-                        stop = true;
-                    } else if (ctrl[1]) {
-                        stop = true;
-                    } else {
-                        if (x0 < 0 || x0 + p.w_pairs > p.n_pos) {   // outside the padded tables: clamp, flag
-                            atomicOr(p.err, 1);
-                            x0 = max(0, min(x0, p.n_pos - p.w_pairs));
-                        }
-                        unsigned char* st = smem + (size_t)pslot * lay.stage;
-                        *reinterpret_cast<int4*>(st + lay.lo) = make_int4(x0 - p.xoff, 0, clo, chi);
-                        const uint32_t ss = sb + (uint32_t)((size_t)pslot * lay.stage);
-                        const uint32_t fb = full_bar(pslot);
-                        mbar_expect_tx(fb, bytes);
-                        bulk_g2s(ss + (uint32_t)lay.meta, p.meta + meta0 + a, 48, fb);
-                        bulk_g2s(ss + (uint32_t)lay.base, p.base + meta0 + a, 32, fb);
-                        if (L == 1) {   // plain tables: one run of w_pairs positions per plane
-#pragma unroll
-                            for (int hb = 0; hb < 2; ++hb)
-                                bulk_g2s(ss + (uint32_t)(hb * lay.plane),
-                                         p.pcoef + 3 * (((size_t)a * 2 + hb) * p.n_pos + x0),
-                                         (uint32_t)p.w_pairs * 48u, fb);
-                        }
-#pragma unroll
-                        for (int h = 0; h < (L == 2 ? 2 : 0); ++h) {
-                            const int cnt = h ? n1 : n0;
-                            const size_t go = (size_t)a * p.n_pos + (size_t)((x0 + h) & 1) * nh + ((x0 + h) >> 1);
-                            if (SINC) {
-                                const size_t gx = go - (size_t)a * p.n_pos;   // position within the SFT's row
-#pragma unroll
-                                for (int hb = 0; hb < 2; ++hb)
-                                    bulk_g2s(ss + (uint32_t)(hb * lay.plane + (size_t)h * half * 48),
-                                             p.pcoef + 3 * (((size_t)a * 2 + hb) * p.n_pos + gx),
-                                             (uint32_t)cnt * 48u, fb);
-                            } else {
-                                bulk_g2s(ss + (uint32_t)(lay.pairs + (size_t)h * half * 16), p.ptab + go,
-                                         (uint32_t)cnt * 16u, fb);
-                                bulk_g2s(ss + (uint32_t)(lay.coef + (size_t)h * half * 48), p.pcoef + 3 * go,
-                                         (uint32_t)cnt * 48u, fb);
-                            }
-                        }
-                        ++a;
-                        if (++pslot == S) {   // the next use of slot 0 waits for the phase after this one
-                            pslot = 0;
-                            if (a > S) pparity ^= 1u;
-                        }
-                    }
-                }
-                stop = __shfl_sync(0xffffffffu, stop, 0);
-                if (stop) break;
-            }
-        }
-        if (lane == 0) ctrl[0] = a;   // stages issued
+        const int issued = ring_produce<SINC, COV, L>(p, lay, S, smem, sb, ctrl, meta0, j_col0, lane);
+        if (lane == 0) ctrl[0] = issued;   // stages issued
     } else {
         float2 fa[M], fb[M];
 #pragma unroll
@@ -744,6 +759,406 @@ template <int M, int NWC, bool SINC, bool COV, int L>
 __global__ void __launch_bounds__(32 * (NWC + 1), 2) dirichlet_far_ring_kernel(const DirichletParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
     far_ring_block<M, SINC, COV, L>(p, (long long)blockIdx.x, smem);
+}
+
+// Rows form of the sinc polynomial (uniform spindown grid, plain tables).
+// A lane owns one frequency j and R consecutive spindown rows d0 .. d0+R-1;
+// a warp owns 32 consecutive frequencies, so its lanes' windows sit about one
+// bin apart (consecutive records, conflict-free) and their kappa agree to
+// within 32 x |tdot - 1| of a bin: the record changes on the same rows for
+// the whole warp.  Going from row d to d + 1 moves khat by dkh = dfdot dtau
+// tdot T (0 to 0.6 bins on the workunit); a row whose window base and half
+// bin are those of the row before reuses the record held in registers, so
+// each 48-byte record is read once for every run of rows that shares it
+// instead of once per template.  The twiddle steps between rows by the
+// bases' rot = e^{-2 pi i dph}, flipping sign with the parity of k0.
+template <int R>
+__device__ __forceinline__ void rows_sft(const DirichletParams& p, const SkySftMeta& m, const SkySftBase& bs,
+                                         int d0, int j, int lo_rel, const float4* __restrict__ cf, int plane4,
+                                         float2 (&fa)[R], float2 (&fb)[R]) {
+    long long kh = bs.kh0 + (long long)d0 * bs.dkh + (long long)j * m.dk;
+    const unsigned int ph = bs.ph0 + (unsigned int)d0 * bs.dph + (unsigned int)j * m.dphi;
+    // key = 2 k0 + half (32 bits hold it: |k0| < 2^30): the record a row reads
+    int key = (int)(kh >> 31);
+    float sn, cs;
+    __sincosf((float)(int)(ph + ((unsigned int)(key >> 1) << 31)) * kPhaseToRad, &sn, &cs);
+    float tr = cs, ti = -sn;
+    const float2 a2 = make_float2(m.a, m.a), b2 = make_float2(m.b, m.b);
+    // stage position of the record of window k0: k0 - k_lo - lo_rel
+    const int pos_base = -(int)p.k_lo - lo_rel;
+    float4 e0, e1, e2;
+    float centre;   // kappa at the centre of the half bin, in units of 2^32 bins (v = kappa - centre)
+    auto load = [&](int k) {
+        int pos = (k >> 1) + pos_base;
+        if (pos < 0 || pos >= p.w_pairs) {   // outside the staged rows (clamped); cannot happen with the planner's bound
+            atomicOr(p.err, 1);
+            pos = max(0, min(pos, p.w_pairs - 1));
+        }
+        const float4* r = cf + ((k & 1) ? plane4 : 0) + 3 * pos;
+        e0 = r[0];
+        e1 = r[1];
+        e2 = r[2];
+        centre = (k & 1) ? 3221225472.0f : 1073741824.0f;   // 3/4 and 1/4 of 2^32
+    };
+    load(key);
+#pragma unroll
+    for (int d = 0; d < R; ++d) {
+        if (d > 0) {
+            kh += bs.dkh;
+            const float t = fmaf(tr, bs.rot_re, -ti * bs.rot_im);
+            ti = fmaf(tr, bs.rot_im, ti * bs.rot_re);
+            tr = t;
+            const int kd = (int)(kh >> 31);
+            if (kd != key) {
+                if ((kd ^ key) & 2) {   // k0 changed parity: (-1)^k0 flips
+                    tr = -tr;
+                    ti = -ti;
+                }
+                key = kd;
+                load(key);
+            }
+        }
+        // v: kappa relative to the centre of its half bin
+        const float v = ((float)(unsigned int)kh - centre) * 2.3283064365386963e-10f;
+        const float2 vv = make_float2(v, v);
+        float2 P = __ffma2_rn(make_float2(e2.z, e2.w), vv, make_float2(e2.x, e2.y));
+        P = __ffma2_rn(P, vv, make_float2(e1.z, e1.w));
+        P = __ffma2_rn(P, vv, make_float2(e1.x, e1.y));
+        P = __ffma2_rn(P, vv, make_float2(e0.z, e0.w));
+        P = __ffma2_rn(P, vv, make_float2(e0.x, e0.y));
+        const float2 z = make_float2(fmaf(tr, P.x, -ti * P.y), fmaf(tr, P.y, ti * P.x));
+        fa[d] = __ffma2_rn(a2, z, fa[d]);
+        fb[d] = __ffma2_rn(b2, z, fb[d]);
+    }
+}
+
+// A block: one sky point, NWC warps x 32 consecutive frequencies (F = 32 NWC,
+// p.lg_row = F), R spindown rows (p.chunks_per_col row chunks), plus the ring's
+// producer warp; the stages hold plain sinc tables (two planes).
+template <int R, int NWC>
+__device__ __forceinline__ void rows_ring_block(const DirichletParams& p, long long bid, unsigned char* smem) {
+    const int S = p.sft_chunk;
+    const RingSmem lay = ring_smem(S, p.w_tab, true);
+    const int rc = (int)(bid % p.chunks_per_col);
+    bid /= p.chunks_per_col;
+    const int sky = (int)(bid % p.n_sky);
+    const int col = (int)(bid / p.n_sky);
+    const int j_col0 = col * 32 * NWC;
+    const int d0 = rc * R;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool producer = (warp == NWC);
+    const int j = j_col0 + warp * 32 + lane;
+    const bool active = !producer && j < p.n_f;
+    const bool warp_live = __any_sync(0xffffffffu, active);
+
+    const uint32_t sb = smem_u32(smem);
+    volatile int* ctrl = reinterpret_cast<volatile int*>(smem + lay.ctrl);   // [0] issued, [1] abort
+    auto full_bar = [&](int s) { return sb + (uint32_t)(lay.bars + 16 * (size_t)s); };
+    auto empty_bar = [&](int s) { return sb + (uint32_t)(lay.bars + 16 * (size_t)s + 8); };
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(full_bar(s), 1);
+            mbar_init(empty_bar(s), (uint32_t)NWC);
+        }
+        ctrl[0] = 0;
+        ctrl[1] = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    const size_t meta0 = (size_t)sky * p.n_sft;
+    if (producer) {
+        const int issued = ring_produce<true, false, 1>(p, lay, S, smem, sb, ctrl, meta0, j_col0, lane);
+        if (lane == 0) ctrl[0] = issued;
+    } else {
+        float2 fa[R], fb[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) fa[q] = fb[q] = make_float2(0.f, 0.f);
+        const int jj = active ? j : j_col0;   // idle lanes follow a valid frequency
+        int slot = 0;
+        uint32_t parity = 0;
+        for (int a = 0; a < p.n_sft; ++a) {
+            const unsigned char* st = smem + (size_t)slot * lay.stage;
+            if (!mbar_wait(full_bar(slot), parity)) {
+                ctrl[1] = 1;
+                atomicOr(p.err, 4);
+                break;
+            }
+            if (warp_live) {
+                const int lo_rel = *reinterpret_cast<const int*>(st + lay.lo);
+                const SkySftMeta m = *reinterpret_cast<const SkySftMeta*>(st + lay.meta);
+                const SkySftBase bs = *reinterpret_cast<const SkySftBase*>(st + lay.base);
+                rows_sft<R>(p, m, bs, d0, jj, lo_rel, reinterpret_cast<const float4*>(st + lay.coef),
+                            (int)(lay.plane >> 4), fa, fb);
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(empty_bar(slot));
+            if (ctrl[1]) break;
+            if (++slot == S) {
+                slot = 0;
+                parity ^= 1u;
+            }
+        }
+        if (active) {
+            const float4 cm = p.comb[sky];
+#pragma unroll
+            for (int d = 0; d < R; ++d) {
+                if (d0 + d < p.n_fdot) {
+                    const float2 A_ = fa[d], B_ = fb[d];
+                    const float v = cm.x * fmaf(A_.x, A_.x, A_.y * A_.y) + cm.y * fmaf(B_.x, B_.x, B_.y * B_.y) +
+                                    cm.z * fmaf(A_.x, B_.x, A_.y * B_.y);
+                    p.twoF[((size_t)sky * p.n_fdot + d0 + d) * p.n_f + j] = fmaxf(v, 0.0f);
+                }
+            }
+        }
+    }
+    // after a give-up, wait for the copies still in flight (bounded), then
+    // invalidate the barriers
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (ctrl[1]) {
+            const int issued = ctrl[0];
+            for (int a = max(0, issued - S); a < issued; ++a) mbar_wait(full_bar(a % S), (uint32_t)((a / S) & 1));
+        }
+        for (int s = 0; s < S; ++s) {
+            mbar_inval(full_bar(s));
+            mbar_inval(empty_bar(s));
+        }
+    }
+}
+
+template <int R, int NWC>
+__global__ void __launch_bounds__(32 * (NWC + 1)) dirichlet_rows_kernel(const DirichletParams p) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    rows_ring_block<R, NWC>(p, (long long)blockIdx.x, smem);
+}
+
+// Two-row tiles of the sinc form (L = 2, uniform spindown grid): a thread
+// owns the templates j_t + P q (q < M) of two adjacent spindown rows A and B.
+// Per SFT the constants, the twiddle's sine and cosine and the checks are
+// paid once for 2 M templates, and when the rows' windows start at the same
+// bin and take the same half (the rows differ by dkh = dfdot dtau tdot T in
+// khat), each record serves both rows; otherwise each row reads its own.
+// Row B's twiddle is row A's times rot = e^{-2 pi i dph}, with the sign of
+// (-1)^k0 when the windows' parity differs.  Threads whose windows straddle
+// a bin boundary, or whose kappa drifts more than kSincSlack over their
+// templates, run the one-row code for each row.
+template <int M>
+__device__ __forceinline__ void sinc_sft2(const DirichletParams& p, const SkySftMeta& m, const SkySftBase& bs,
+                                          long long kh_row, unsigned int ph0, int lo_rel,
+                                          const float4* __restrict__ cf, int plane4, int half, int j_t,
+                                          float2 (&fa)[2][M], float2 (&fb)[2][M]) {
+    constexpr int D = 8, L = 2;
+    const long long khA = kh_row + (long long)j_t * m.dk;
+    const long long khB = khA + bs.dkh;
+    const int k0A = (int)(khA >> 32), k0B = (int)(khB >> 32);
+    const bool fast = ((int)((khA + m.span) >> 32) == k0A + (M - 1) * L) &&
+                      ((int)((khB + m.span) >> 32) == k0B + (M - 1) * L) &&
+                      fabsf(m.eps) * (float)(M - 1) <= kSincSlack;
+    if (!fast) {
+        sinc_sft<M, L, false>(p, m, kh_row, ph0, lo_rel, cf, plane4, half, j_t, 0, 0x7fffffff, fa[0], fb[0]);
+        sinc_sft<M, L, false>(p, m, kh_row + bs.dkh, ph0 + bs.dph, lo_rel, cf, plane4, half, j_t, 0, 0x7fffffff,
+                              fa[1], fb[1]);
+        return;
+    }
+    const float2 a2 = make_float2(m.a, m.a), b2 = make_float2(m.b, m.b);
+    auto horner = [&](const float4* __restrict__ r, float v) -> float2 {
+        const float4 e0 = r[0], e1 = r[1], e2 = r[2];
+        const float2 vv = make_float2(v, v);
+        float2 P = __ffma2_rn(make_float2(e2.z, e2.w), vv, make_float2(e2.x, e2.y));
+        P = __ffma2_rn(P, vv, make_float2(e1.z, e1.w));
+        P = __ffma2_rn(P, vv, make_float2(e1.x, e1.y));
+        P = __ffma2_rn(P, vv, make_float2(e0.z, e0.w));
+        return __ffma2_rn(P, vv, make_float2(e0.x, e0.y));
+    };
+    auto add = [&](float tr, float ti, float2 P, float2& fa_q, float2& fb_q) {
+        const float2 z = make_float2(fmaf(tr, P.x, -ti * P.y), fmaf(tr, P.y, ti * P.x));
+        fa_q = __ffma2_rn(a2, z, fa_q);
+        fb_q = __ffma2_rn(b2, z, fb_q);
+    };
+    // window start and half bin of each row (the half chosen at its middle template)
+    auto place = [&](long long kh, int k0, const float4*& cq, float& v0) {
+        int bb = (k0 - (int)p.k_lo) - (D - 1) - lo_rel;
+        if (bb < 0 || bb + (M - 1) * L + 2 * (D - 1) >= p.w_pairs) {
+            atomicOr(p.err, 1);
+            bb = max(0, min(bb, p.w_pairs - 1 - (M - 1) * L - 2 * (D - 1)));
+        }
+        const float u0 = frac_to_float((unsigned int)kh) - 0.5f;
+        const bool up = fmaf(0.5f * (float)(M - 1), m.eps, u0) >= 0.f;
+        cq = cf + (up ? plane4 : 0) + 3 * tab_pos<L>(bb + 7, half);
+        v0 = u0 + (up ? -0.25f : 0.25f);
+    };
+    const float4 *cA, *cB;
+    float vA, vB;
+    place(khA, k0A, cA, vA);
+    place(khB, k0B, cB, vB);
+    const unsigned int ph = ph0 + (unsigned int)j_t * m.dphi + ((unsigned int)k0A << 31);
+    float sn, cs;
+    __sincosf((float)(int)ph * kPhaseToRad, &sn, &cs);
+    float ar = cs, ai = -sn;
+    float br = fmaf(ar, bs.rot_re, -ai * bs.rot_im), bi = fmaf(ar, bs.rot_im, ai * bs.rot_re);
+    if ((k0B - k0A) & 1) {
+        br = -br;
+        bi = -bi;
+    }
+    if (cA == cB) {   // both rows read the same records
+#pragma unroll
+        for (int q = 0; q < M; ++q) {
+            const float4* r = cA + 3 * q;
+            const float4 e0 = r[0], e1 = r[1], e2 = r[2];
+            const float2 va = make_float2(fmaf((float)q, m.eps, vA), fmaf((float)q, m.eps, vA));
+            const float2 vb = make_float2(fmaf((float)q, m.eps, vB), fmaf((float)q, m.eps, vB));
+            float2 PA = __ffma2_rn(make_float2(e2.z, e2.w), va, make_float2(e2.x, e2.y));
+            float2 PB = __ffma2_rn(make_float2(e2.z, e2.w), vb, make_float2(e2.x, e2.y));
+            PA = __ffma2_rn(PA, va, make_float2(e1.z, e1.w));
+            PB = __ffma2_rn(PB, vb, make_float2(e1.z, e1.w));
+            PA = __ffma2_rn(PA, va, make_float2(e1.x, e1.y));
+            PB = __ffma2_rn(PB, vb, make_float2(e1.x, e1.y));
+            PA = __ffma2_rn(PA, va, make_float2(e0.z, e0.w));
+            PB = __ffma2_rn(PB, vb, make_float2(e0.z, e0.w));
+            PA = __ffma2_rn(PA, va, make_float2(e0.x, e0.y));
+            PB = __ffma2_rn(PB, vb, make_float2(e0.x, e0.y));
+            add(ar, ai, PA, fa[0][q], fb[0][q]);
+            add(br, bi, PB, fa[1][q], fb[1][q]);
+            if (q + 1 < M) {
+                const float ta = fmaf(ar, m.rot_re, -ai * m.rot_im);
+                ai = fmaf(ar, m.rot_im, ai * m.rot_re);
+                ar = ta;
+                const float tb = fmaf(br, m.rot_re, -bi * m.rot_im);
+                bi = fmaf(br, m.rot_im, bi * m.rot_re);
+                br = tb;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < M; ++q) {
+            add(ar, ai, horner(cA + 3 * q, fmaf((float)q, m.eps, vA)), fa[0][q], fb[0][q]);
+            add(br, bi, horner(cB + 3 * q, fmaf((float)q, m.eps, vB)), fa[1][q], fb[1][q]);
+            if (q + 1 < M) {
+                const float ta = fmaf(ar, m.rot_re, -ai * m.rot_im);
+                ai = fmaf(ar, m.rot_im, ai * m.rot_re);
+                ar = ta;
+                const float tb = fmaf(br, m.rot_re, -bi * m.rot_im);
+                bi = fmaf(br, m.rot_im, bi * m.rot_re);
+                br = tb;
+            }
+        }
+    }
+}
+
+// The ring block with two-row tiles: a lane-group holds rows 2 t and 2 t + 1
+// (t = lane-group row pair); the last pair of an odd row count repeats its
+// first row and stores one.
+template <int M>
+__device__ __forceinline__ void ring2_block(const DirichletParams& p, long long bid, unsigned char* smem) {
+    const int S = p.sft_chunk;
+    const RingSmem lay = ring_smem(S, p.w_tab, true);
+    const int NW = (int)(blockDim.x >> 5) - 1;
+    const int chunk = (int)(bid % p.chunks_per_col);
+    bid /= p.chunks_per_col;
+    const int sky = (int)(bid % p.n_sky);
+    const int col = (int)(bid / p.n_sky);
+    const int PM = p.P * M;
+    const int col_w = p.lg_row * PM;
+    const int j_col0 = col * col_w;
+    const int width = min(col_w, p.n_f - j_col0);
+    const int Gc = (width + PM - 1) / PM;
+    const int n_pairs = (p.n_fdot + 1) >> 1;
+    const int LG = n_pairs * Gc;
+    const int u0 = chunk * p.lg_cta;
+    if (u0 >= LG) return;   // block-uniform, before any barrier exists
+    const int u_end = min(u0 + p.lg_cta, LG);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool producer = (warp == NW);
+    const int r = producer ? 0 : warp % p.P;
+    const int ul = producer ? p.lg_cta : (warp / p.P) * 32 + lane;
+    const int u = u0 + ul;
+    const bool active = !producer && (ul < p.lg_cta) && (u < u_end);
+    const int uu = active ? u : u0;
+    const int pr = uu / Gc;
+    const int g = uu - pr * Gc;
+    const int dA = 2 * pr;
+    const int dB = min(dA + 1, p.n_fdot - 1);
+    const int j_t = j_col0 + g * PM + r;
+    const bool warp_live = __any_sync(0xffffffffu, active);
+
+    const uint32_t sb = smem_u32(smem);
+    volatile int* ctrl = reinterpret_cast<volatile int*>(smem + lay.ctrl);
+    auto full_bar = [&](int s) { return sb + (uint32_t)(lay.bars + 16 * (size_t)s); };
+    auto empty_bar = [&](int s) { return sb + (uint32_t)(lay.bars + 16 * (size_t)s + 8); };
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(full_bar(s), 1);
+            mbar_init(empty_bar(s), (uint32_t)NW);
+        }
+        ctrl[0] = 0;
+        ctrl[1] = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const size_t meta0 = (size_t)sky * p.n_sft;
+    if (producer) {
+        const int issued = ring_produce<true, false, 2>(p, lay, S, smem, sb, ctrl, meta0, j_col0, lane);
+        if (lane == 0) ctrl[0] = issued;
+    } else {
+        float2 fa[2][M], fb[2][M];
+#pragma unroll
+        for (int q = 0; q < M; ++q) fa[0][q] = fb[0][q] = fa[1][q] = fb[1][q] = make_float2(0.f, 0.f);
+        const int half = p.w_tab >> 1;
+        int slot = 0;
+        uint32_t parity = 0;
+        for (int a = 0; a < p.n_sft; ++a) {
+            const unsigned char* st = smem + (size_t)slot * lay.stage;
+            if (!mbar_wait(full_bar(slot), parity)) {
+                ctrl[1] = 1;
+                atomicOr(p.err, 4);
+                break;
+            }
+            if (warp_live) {
+                const int lo_rel = *reinterpret_cast<const int*>(st + lay.lo);
+                const SkySftMeta m = *reinterpret_cast<const SkySftMeta*>(st + lay.meta);
+                SkySftBase bs = *reinterpret_cast<const SkySftBase*>(st + lay.base);
+                const long long kh_row = bs.kh0 + (long long)dA * bs.dkh;
+                const unsigned int ph_row = bs.ph0 + (unsigned int)dA * bs.dph;
+                if (dB == dA) {   // odd row count: the last pair repeats its row (rot = 1, no step)
+                    bs.dkh = 0;
+                    bs.dph = 0u;
+                    bs.rot_re = 1.f;
+                    bs.rot_im = 0.f;
+                }
+                sinc_sft2<M>(p, m, bs, kh_row, ph_row, lo_rel, reinterpret_cast<const float4*>(st + lay.coef),
+                             (int)(lay.plane >> 4), half, j_t, fa, fb);
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(empty_bar(slot));
+            if (ctrl[1]) break;
+            if (++slot == S) {
+                slot = 0;
+                parity ^= 1u;
+            }
+        }
+        if (active) {
+            far_store<M>(p, sky, dA, j_t, j_col0 + width, fa[0], fb[0]);
+            if (dB != dA) far_store<M>(p, sky, dB, j_t, j_col0 + width, fa[1], fb[1]);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (ctrl[1]) {
+            const int issued = ctrl[0];
+            for (int a = max(0, issued - S); a < issued; ++a) mbar_wait(full_bar(a % S), (uint32_t)((a / S) & 1));
+        }
+        for (int s = 0; s < S; ++s) {
+            mbar_inval(full_bar(s));
+            mbar_inval(empty_bar(s));
+        }
+    }
+}
+
+template <int M, int NWC, int MINB>
+__global__ void __launch_bounds__(32 * (NWC + 1), MINB) dirichlet_ring2_kernel(const DirichletParams p) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    ring2_block<M>(p, (long long)blockIdx.x, smem);
 }
 
 // Persistent ring form over many template banks (workunits): every block
@@ -816,6 +1231,19 @@ __global__ void __launch_bounds__(32 * (NWC + 1), 2)
 #define FS_RING_L1_VARIANTS(X) \
     X(18, 5, 8, true)          \
     X(19, 1, 8, true)
+// two-row tiles of the sinc form (L = 2): (ID, M, NWC compute warps, resident blocks per SM)
+#define FS_RING2_VARIANTS(X) \
+    X(27, 5, 8, 2)           \
+    X(28, 3, 10, 2)
+// rows form of the sinc polynomial: (ID, R rows per lane, NWC compute warps)
+#define FS_ROWS_VARIANTS(X) \
+    X(20, 10, 3)            \
+    X(21, 10, 4)            \
+    X(22, 10, 8)            \
+    X(23, 5, 4)             \
+    X(24, 5, 8)             \
+    X(25, 8, 4)             \
+    X(26, 4, 4)
 
 cudaError_t launch_dirichlet_far(int v, const DirichletParams& p, int threads, size_t smem, long long grid,
                                  cudaStream_t s) {
@@ -844,6 +1272,26 @@ cudaError_t launch_dirichlet_far(int v, const DirichletParams& p, int threads, s
         FS_RING_VARIANTS(FS_RCASE_PLAIN)
         FS_RING_COV_VARIANTS(FS_RCASE_COV)
         FS_RING_L1_VARIANTS(FS_RCASE_L1)
+#define FS_ROWCASE(ID, R_, W_)                                                                            \
+    case ID: {                                                                                            \
+        auto fn = dirichlet_rows_kernel<R_, W_>;                                                          \
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        if (e != cudaSuccess) return e;                                                                   \
+        fn<<<(unsigned)grid, threads, smem, s>>>(p);                                                      \
+        return cudaGetLastError();                                                                        \
+    }
+        FS_ROWS_VARIANTS(FS_ROWCASE)
+#undef FS_ROWCASE
+#define FS_R2CASE(ID, M_, W_, B_)                                                                         \
+    case ID: {                                                                                            \
+        auto fn = dirichlet_ring2_kernel<M_, W_, B_>;                                                     \
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        if (e != cudaSuccess) return e;                                                                   \
+        fn<<<(unsigned)grid, threads, smem, s>>>(p);                                                      \
+        return cudaGetLastError();                                                                        \
+    }
+        FS_RING2_VARIANTS(FS_R2CASE)
+#undef FS_R2CASE
 #undef FS_RCASE_L1
 #undef FS_RCASE_COV
 #undef FS_RCASE_PLAIN

@@ -185,7 +185,11 @@ __global__ void __launch_bounds__(kTimingBlock) timing_kernel(const TimingParams
             bs.dkh = llrint(p.dfdot * dtau * tdot * p.T * kTwo32);
             bs.ph0 = frac_fx32(p.f0 * dtau + 0.5 * fd * dtau * dtau);
             bs.dph = frac_fx32(0.5 * p.dfdot * dtau * dtau);
-            bs.pad0 = bs.pad1 = 0u;
+            // twiddle step from one spindown row to the next, e^{-2 pi i dph}
+            double rs, rc;
+            sincos((double)(int)bs.dph / kTwo32 * kTwoPi, &rs, &rc);
+            bs.rot_re = (float)rc;
+            bs.rot_im = (float)(-rs);
             p.base[(size_t)sky * p.n_sft + i] = bs;
             const long long last = bs.kh0 + (long long)(p.n_fdot - 1) * bs.dkh;
             khmin = bs.kh0 < last ? bs.kh0 : last;

@@ -54,10 +54,11 @@ static_assert(sizeof(SkySftMeta) == 48, "SkySftMeta layout");
 // Bases of a uniform spindown grid fdot_d = fdot_0 + d * dfdot, per (sky, SFT):
 //   khat0(d) = kh0 + d * dkh   (32.32 fixed-point bins)
 //   Phi0(d)  = ph0 + d * dph   (0.32 fixed-point cycles, wraps mod 1)
+//   rot = e^{-2 pi i dph}      (FP32, the twiddle step from row d to d + 1)
 struct __align__(16) SkySftBase {
     long long kh0, dkh;
     unsigned int ph0, dph;
-    unsigned int pad0, pad1;
+    float rot_re, rot_im;
 };
 static_assert(sizeof(SkySftBase) == 32, "SkySftBase layout");
 

@@ -99,7 +99,7 @@ def test_sft_timing_and_abcd_match_oracle(lib):
 
 # ---------------------------------------------------------------- kernels (b)-(d): 2F and toplist
 
-ALGOS = ["farpoly", "direct", "sincpoly"]
+ALGOS = ["farpoly", "direct", "sincpoly", "sincrows", "sincpairs"]
 
 
 @pytest.mark.parametrize("algo", ALGOS)
@@ -143,6 +143,22 @@ def test_tile_overrides_keep_parity(lib, tile, algo):
     ref = O.compute_fstat_freq_band(_dets(w, bins), w.T, w.k_lo, w.dterms, w.bank).ravel()
     out = _gpu(lib, w, bins, algo=algo, **tile)
     _assert_parity(out["twoF"], ref, str(tile))
+
+
+@pytest.mark.parametrize("algo,ids", [("sincrows", range(120, 127)), ("sincpairs", range(127, 129))])
+@pytest.mark.parametrize("n_fdot,df_bins", [(4, 1.0), (5, 1.0), (7, 0.5), (10, 1.0), (13, 2.0)])
+def test_row_tiled_forms_on_ragged_row_counts(lib, algo, ids, n_fdot, df_bins):
+    """The two forms that tile spindown rows inside a thread: row counts that
+    leave a partial last row chunk (or an odd last row pair), several columns
+    with a ragged tail, element-wise parity and the toplist."""
+    w = config_mid(n_f=130, n_fdot=n_fdot, n_sky=3, df_bins=df_bins)
+    bins = _oracle_bins(w)
+    ref = O.compute_fstat_freq_band(_dets(w, bins), w.T, w.k_lo, w.dterms, w.bank).ravel()
+    out = _gpu(lib, w, bins, algo=algo)
+    assert out["plan"]["variant"] in ids
+    assert out["flags"] == 0
+    _assert_parity(out["twoF"], ref, f"{algo} n_fdot={n_fdot}")
+    _check_toplist(out["top"], out["twoF"], ref, w.topk)
 
 
 @pytest.mark.parametrize("D", [1, 2, 3, 5, 16])
@@ -266,7 +282,7 @@ def test_errors_are_reported_not_raised_on_device(lib):
         assert e.value.code == lib.FSTAT_EINVAL
         with pytest.raises(lib.FstatError):
             lib.fstat_create(0, dterms=0)
-        for bad_opts in (dict(algo=4), dict(algo="farpoly", dterms=5), dict(algo="farpoly", kahan=True),
+        for bad_opts in (dict(algo=6), dict(algo="farpoly", dterms=5), dict(algo="farpoly", kahan=True),
                          dict(algo="sincpoly", dterms=5)):
             with pytest.raises(lib.FstatError) as e:
                 lib.fstat_create(0, **bad_opts)
