@@ -81,6 +81,8 @@ def parse():
     ap.add_argument("--n-refine", type=int, default=8, help="patches refined per workunit (proposal mode)")
     ap.add_argument("--train-steps", type=int, default=6000, help="Adam steps (proposal mode)")
     ap.add_argument("--proposal-sft", type=int, default=800, help="SFTs per detector (proposal mode)")
+    ap.add_argument("--proposal-lines", type=int, default=3,
+                    help="detector lines per workunit, at most (proposal mode: training and the second held-out set)")
     ap.add_argument("--algo", default="auto", choices=["auto", "direct", "farpoly", "sincpoly", "sincrows", "sincpairs"],
                     help="evaluation of the D-term kernel sum")
     ap.add_argument("--noise-floor", type=int, default=0,
@@ -526,9 +528,12 @@ def run_batch(args):
 def run_proposal(args):
     """Learned proposal: coarse 2F maps of 2 det x 800 SFT workunits (64 x 32
     sky x 900 f), a 8192-256-256-1 network trained on the GPU on windows of
-    the training maps, then on held-out workunits the network's best patches
-    refined on the 8x finer grid; recall against the exhaustive fine grid and
-    end-to-end device time against it."""
+    the training maps (signals, and detector lines in the data), then two
+    held-out sets of the same workunits -- without and with detector lines --
+    where the network's best patches are refined on the 8x finer grid: recall
+    against the exhaustive fine grid at refinement budgets of 1-16 patches for
+    the network, the coarse-max ranking and random patches, and end-to-end
+    device time against the exhaustive grid."""
     import torch
     from paper_0904_1826_gb300 import proposal as PR
     from workload import config4_workunit
@@ -536,7 +541,8 @@ def run_proposal(args):
     search = PR.ProposalSearch(0, hidden=256, max_batch=1024)
     rng = np.random.default_rng(11)
     t0 = time.perf_counter()
-    train = (config4_workunit(i, True, n_sft=args.proposal_sft, n_signals=8) for i in range(args.n_train))
+    train = (config4_workunit(i, True, n_sft=args.proposal_sft, n_signals=8, n_lines=args.proposal_lines)
+             for i in range(args.n_train))
     X, y = search.training_set(train, rng, 16, 256)
     t_set = time.perf_counter() - t0
     search.init_params(np.random.default_rng(1))
@@ -549,33 +555,40 @@ def run_proposal(args):
     train_ms = e0.elapsed_time(e1)
     n_rows, n_pos = int(X.shape[0]), int(y.sum())
     del X
-    test = [config4_workunit(i, False, n_sft=args.proposal_sft) for i in range(args.n_test)]
     sampler = ClockSampler(0)
     sampler.start()
     t1 = time.perf_counter()
-    res = PR.evaluate(search, test, n_refine=args.n_refine, noise_patches_per_wu=24)
+    res = {}
+    for name, nl in (("clean", 0), ("lines", args.proposal_lines)):
+        test = [config4_workunit(i, False, n_sft=args.proposal_sft, n_lines=nl) for i in range(args.n_test)]
+        res[name] = PR.evaluate(search, test, n_refine=args.n_refine, noise_patches_per_wu=24)
     t_eval = time.perf_counter() - t1
-    ex_ms = [PR.exhaustive_ms(search, w) for w in test[:2]]
+    test = [config4_workunit(i, False, n_sft=args.proposal_sft) for i in range(2)]
+    ex_ms = [PR.exhaustive_ms(search, w) for w in test]
     clocks = sampler.stop()
     search.close()
-    ms_learned = res["ms_per_wu_learned"]
+    r0 = res["clean"]
+    ms_learned = r0["ms_per_wu_learned"]
     ms_exh = float(np.mean(ex_ms))
+    keys = ("recall_nn", "recall_coarse_max", "recall_random", "n_signal", "n_detected_exhaustive", "threshold",
+            "n_noise_patches", "budgets", "curve", "n_low_rho", "curve_low_rho", "low_rho", "line_patches_in_top")
     line = {"metric": "learned-proposal device time per workunit vs exhaustive fine grid, at stated recall",
             "value": ms_exh / ms_learned, "unit": "x (speedup)", "n_gpus": 1, "steps": args.n_test, "warmup": 0,
             "ms_per_step": ms_learned, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32 2F, bf16 network (fp32 accumulate)", "data": "synthetic",
             "config": {"workload": f"learned proposal: 2 det x {args.proposal_sft} SFTs, coarse 64x32 sky x 900 f "
                                    f"(0.5 Hz at 1/T), patches 16x16x32, fine grid 4x2 sky x 8 f per patch; "
-                                   f"{args.n_train} training WUs (8 signals each or noise), {args.n_test} held-out "
-                                   f"WUs (1 signal or noise), rho log-uniform 4-40, {args.n_refine} of "
-                                   f"{res['n_patches']} patches refined",
+                                   f"{args.n_train} training WUs (8 signals each or noise, 1-{args.proposal_lines} "
+                                   f"detector lines), {args.n_test} held-out WUs (1 signal or noise) without and "
+                                   f"with 1-{args.proposal_lines} detector lines, rho log-uniform 4-40, "
+                                   f"{args.n_refine} of {r0['n_patches']} patches refined",
                        "network": "8192-256-256-1 ReLU, BF16 weights/activations, FP32 accumulate, Adam lr 1e-4, "
                                   f"batch 256, {args.train_steps} steps"},
-            "recall": {k: res[k] for k in ("recall_nn", "recall_coarse_max", "recall_random", "n_signal",
-                                           "n_detected_exhaustive", "threshold", "n_noise_patches")},
-            "ms_per_wu": {"learned_total": ms_learned, "coarse": res["ms_coarse"], "network": res["ms_mlp"],
-                          "refine": res["ms_refine"], "exhaustive_measured": ms_exh,
-                          "exhaustive_from_patch_time": res["ms_per_wu_exhaustive"]},
+            "recall": {k: r0[k] for k in keys},
+            "recall_with_lines": {k: res["lines"][k] for k in keys},
+            "ms_per_wu": {"learned_total": ms_learned, "coarse": r0["ms_coarse"], "network": r0["ms_mlp"],
+                          "refine": r0["ms_refine"], "exhaustive_measured": ms_exh,
+                          "exhaustive_from_patch_time": r0["ms_per_wu_exhaustive"]},
             "train": {"rows": n_rows, "positives": n_pos, "device_ms": train_ms, "loss_first": hist[0],
                       "loss_last": hist[-1], "set_s": t_set},
             "eval_wall_s": t_eval, "clocks": clocks}

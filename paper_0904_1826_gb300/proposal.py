@@ -258,41 +258,72 @@ class ProposalSearch:
         return res, ms
 
 
+def line_patches(w) -> set:
+    """Patches whose frequency span lies within 24 coarse bins of a detector
+    line of the workunit (the line's Doppler-smeared footprint)."""
+    fs = f_starts(w.bank.n_f)
+    n_q = len(fs)
+    out = set()
+    for ln in getattr(w, "lines", []):
+        fj = int(round((ln.k / w.T - w.bank.f0) / w.bank.df))
+        for q, f in enumerate(fs):
+            if f - 24 <= fj < f + N_FP + 24:
+                for sp in range((N_A // S_A) * (N_D // S_D)):
+                    out.add(sp * n_q + q)
+    return out
+
+
 def evaluate(search: ProposalSearch, test_wus, n_refine: int, threshold: float | None = None,
-             noise_patches_per_wu: int | None = None):
-    """Recall of the learned proposal (top n_refine patches by network score),
-    of the coarse-max ranking and of a random choice, against the exhaustive
-    fine-grid judge (fine max 2F in the signal's patch above the threshold set
-    for 1 % false alarm per patch on the noise-only workunits)."""
+             noise_patches_per_wu: int | None = None, budgets=(1, 2, 4, 8, 16), low_rho: float = 10.0):
+    """Recall of the learned proposal (top-b patches by network score), of the
+    coarse-max ranking and of a random choice, for each budget b, against the
+    exhaustive fine-grid judge: a signal counts when the fine-grid max 2F in
+    its patch exceeds the threshold set for 1 % false alarm per patch on the
+    noise-only workunits' patches away from detector lines.  Device time of
+    the learned pipeline at n_refine patches against the exhaustive grid."""
     rng = np.random.default_rng(77)
     noise_max = []
     rows = []
     t_coarse = t_mlp = t_ref = 0.0
+    n_line_top_nn = n_line_top_cm = n_line_wu = 0
     for w in test_wus:
         m = search.coarse(w)
         t0 = time.perf_counter()
         sc = search.scores(m.patches)
         t_mlp += 1e3 * (time.perf_counter() - t0)
         t_coarse += m.coarse_ms
-        top_nn = list(np.argsort(-sc)[:n_refine])
-        top_cm = list(np.argsort(-m.coarse_max)[:n_refine])
-        top_rd = list(rng.choice(len(sc), n_refine, replace=False))
+        rank_nn = list(np.argsort(-sc, kind="stable"))
+        rank_cm = list(np.argsort(-m.coarse_max, kind="stable"))
+        rank_rd = list(rng.permutation(len(sc)))
+        lp = line_patches(w)
+        if lp:
+            n_line_wu += 1
+            n_line_top_nn += sum(p in lp for p in rank_nn[:n_refine])
+            n_line_top_cm += sum(p in lp for p in rank_cm[:n_refine])
+        _, ms = search.refine(w, rank_nn[:n_refine])
+        t_ref += ms
         if not m.has_signal:
-            cand = np.arange(len(sc)) if noise_patches_per_wu is None else rng.choice(len(sc), noise_patches_per_wu,
-                                                                                      replace=False)
+            free = [p for p in range(len(sc)) if p not in lp]
+            cand = free if noise_patches_per_wu is None else list(rng.choice(free, noise_patches_per_wu, replace=False))
             v, _ = search.refine(w, cand)
             noise_max.extend(v.tolist())
-            v2, ms = search.refine(w, top_nn)
-            t_ref += ms
             continue
         sp = sorted(set(m.sig_patches))
         v_sig, _ = search.refine(w, sp)
-        _, ms = search.refine(w, top_nn)
-        t_ref += ms
-        rows.append(dict(fine_max=float(v_sig.max()), in_nn=any(p in top_nn for p in sp),
-                         in_cm=any(p in top_cm for p in sp), in_rd=any(p in top_rd for p in sp)))
+
+        def first(rank):
+            return min(rank.index(p) for p in sp)
+
+        rows.append(dict(fine_max=float(v_sig.max()), rho=float(w.injections[0].rho), r_nn=first(rank_nn),
+                         r_cm=first(rank_cm), r_rd=first(rank_rd), lines=bool(lp)))
     thr = threshold if threshold is not None else float(np.percentile(noise_max, 99.0))
     judged = [r for r in rows if r["fine_max"] > thr]
+
+    def curve(sel):
+        n = max(1, len(sel))
+        return {k: [sum(r["r_" + k] < b for r in sel) / n for b in budgets] for k in ("nn", "cm", "rd")}
+
+    low = [r for r in judged if r["rho"] < low_rho]
     n = max(1, len(judged))
     n_wu = max(1, len(test_wus))
     n_patch = patch_count(test_wus[0].bank.n_f)
@@ -300,8 +331,11 @@ def evaluate(search: ProposalSearch, test_wus, n_refine: int, threshold: float |
     ms_learned = (t_coarse + t_mlp + t_ref) / n_wu
     ms_exhaustive = n_patch * ms_patch
     return dict(threshold=thr, n_signal=len(rows), n_detected_exhaustive=len(judged),
-                recall_nn=sum(r["in_nn"] for r in judged) / n, recall_coarse_max=sum(r["in_cm"] for r in judged) / n,
-                recall_random=sum(r["in_rd"] for r in judged) / n, n_refine=n_refine, n_patches=n_patch,
+                recall_nn=sum(r["r_nn"] < n_refine for r in judged) / n,
+                recall_coarse_max=sum(r["r_cm"] < n_refine for r in judged) / n,
+                recall_random=sum(r["r_rd"] < n_refine for r in judged) / n, n_refine=n_refine, n_patches=n_patch,
+                budgets=list(budgets), curve=curve(judged), curve_low_rho=curve(low), n_low_rho=len(low),
+                low_rho=low_rho, line_patches_in_top=dict(nn=n_line_top_nn, cm=n_line_top_cm, workunits=n_line_wu),
                 ms_per_wu_learned=ms_learned, ms_per_wu_exhaustive=ms_exhaustive,
                 speedup=ms_exhaustive / ms_learned, ms_coarse=t_coarse / n_wu, ms_mlp=t_mlp / n_wu,
                 ms_refine=t_ref / n_wu, n_test=len(test_wus), n_noise_patches=len(noise_max))

@@ -20,7 +20,7 @@ import numpy as np
 
 __all__ = [
     "T_SFT", "T0", "DET_H", "DET_L", "DetectorData", "TemplateBank", "Injection",
-    "Workload", "philox", "cn_noise", "contiguous_timestamps", "gapped_timestamps",
+    "Workload", "Line", "add_lines", "philox", "cn_noise", "contiguous_timestamps", "gapped_timestamps",
     "fibonacci_sky", "random_sky", "draw_injections", "config0", "config1",
     "config_mid", "config3_workunit", "config3_specs", "config4_workunit",
     "n_templates", "template_index", "template_params",
@@ -150,6 +150,7 @@ class Workload:
     detectors: list
     bank: TemplateBank
     injections: list = field(default_factory=list)
+    lines: list = field(default_factory=list)       # detector lines (Line) added to the bins
 
     @property
     def n_sft_total(self) -> int:
@@ -328,13 +329,40 @@ def config3_workunit(spec: dict, n_sky: int | None = None, n_sft_total: int | No
     return Workload(f"batch-wu seed {seed}", T, k_lo, n_bins, dterms, 100, dets, bank, injs)
 
 
+_S_LINE = 100
+
+
+@dataclass
+class Line:
+    """A detector line: a sinusoid fixed in the detector's frame at the centre
+    of stored bin `k` (absolute), amplitude `amp` per SFT bin (noise bins have
+    E|X|^2 = 1), phase `phi` at the SFT starts."""
+    det: int
+    k: int
+    amp: float
+    phi: float
+
+
+def add_lines(dets, k_lo: int, lines) -> None:
+    """Add each line to its detector's bins in place: a sinusoid at a bin
+    centre, sampled at SFT starts on the SFT grid, is the same complex number
+    amp e^{i phi} in that one bin of every SFT."""
+    for ln in lines:
+        b = dets[ln.det].bins
+        b[:, ln.k - k_lo] += np.complex64(ln.amp * complex(math.cos(ln.phi), math.sin(ln.phi)))
+
+
 def config4_workunit(index: int, train: bool = True, n_sft: int = 800, noise_only_frac: float = 0.25,
-                     seed_base: int = 4000, n_signals: int = 1) -> Workload:
+                     seed_base: int = 4000, n_signals: int = 1, n_lines: int = 0,
+                     line_amp: tuple = (1.5, 15.0)) -> Workload:
     """Learned-proposal workunit: 2 detectors x 800 SFTs, 0.5 Hz band, coarse
     grid 64 x 32 sky (alpha, sin delta) x 900 f x 1 fdot.  A quarter of the
     workunits are noise only; the rest carry n_signals signals (one in the
     held-out set; training sets may take more) with log-uniform rho in
-    [4, 40], each placed on a coarse template."""
+    [4, 40], each placed on a coarse template.  n_lines > 0 adds up to that
+    many detector lines (uniform count 1..n_lines, random detector,
+    log-uniform amplitude in line_amp), each at least 64 coarse frequencies
+    from every signal; they are listed in the workload's `lines`."""
     T = T_SFT
     seed = seed_base + (0 if train else 100000) + index
     dterms = 8
@@ -369,5 +397,19 @@ def config4_workunit(index: int, train: bool = True, n_sft: int = 800, noise_onl
     A, SD = np.meshgrid(a, sd, indexing="ij")
     sky = np.stack([A.ravel(), np.arcsin(SD.ravel())], axis=1)
     bank = TemplateBank(sky=sky, f0=k0 / T, df=1.0 / T, n_f=n_f, fdot=np.zeros(1), t_ref=T0)
-    return Workload(f"proposal-wu {'train' if train else 'test'} {index}", T, k_lo, n_bins, dterms,
-                    100, dets, bank, injs)
+    w = Workload(f"proposal-wu {'train' if train else 'test'} {index}", T, k_lo, n_bins, dterms,
+                 100, dets, bank, injs)
+    if n_lines > 0:
+        gl = philox(seed, _S_LINE)
+        sig_f = [int(round((inj.f - k0 / T) * T)) for inj in injs]
+        n_here = int(gl.integers(1, n_lines + 1))
+        tries = 0
+        while len(w.lines) < n_here and tries < 1000:
+            tries += 1
+            fj = int(gl.integers(20, n_f - 20))
+            if any(abs(fj - q) < 64 for q in sig_f) or any(abs(fj + k0 - ln.k) < 8 for ln in w.lines):
+                continue
+            amp = math.exp(gl.uniform(math.log(line_amp[0]), math.log(line_amp[1])))
+            w.lines.append(Line(int(gl.integers(0, 2)), k0 + fj, amp, gl.uniform(0.0, 2.0 * math.pi)))
+        add_lines(dets, k_lo, w.lines)
+    return w
