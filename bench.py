@@ -504,6 +504,11 @@ def run_batch(args):
         torch.cuda.synchronize()
         seq.append(a.elapsed_time(b))
     total_pairs = float(sum(pairs))
+    plans = [fs.fstat_batch_get_plan(ctx, i) for i in range(len(specs))]
+    per_wu = [{"wu": i, "pairs": int(pairs[i]), "ms": float(seq[i]), "pairs_per_s": float(pairs[i] / (seq[i] / 1e3)),
+               "n_sft": int(sp["n_sft_total"]), "n_det": int(sp["n_det"]), "n_f": max(1, int(round(sp["band"] * 1800))),
+               "n_sky": int(sp["n_sky"]), "n_fdot": int(sp["n_fdot"]), "plan": plans[i]}
+              for i, sp in enumerate(specs)]
     value = total_pairs * args.steps / (ms / 1e3)
     seq_value = total_pairs / (sum(seq) / 1e3)
     seq_cum = np.cumsum(seq)
@@ -520,6 +525,7 @@ def run_batch(args):
                                  "graph_total": total},
             "sequential_latency_ms": {"median_wu_done": float(np.median(seq_cum)), "max_wu_done": float(seq_cum[-1])},
             "speedup_vs_one_launch_per_workunit": value / seq_value,
+            "per_workunit": per_wu,
             "clocks": clocks}
     fs.fstat_destroy(ctx)
     print(json.dumps(line))

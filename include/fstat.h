@@ -372,6 +372,11 @@ int fstat_batch_get_2f(fstat_ctx *ctx, int32_t wu, float *out, int64_t offset, i
  * (CUDA events on the stream).  Synchronises. */
 int fstat_batch_get_times(fstat_ctx *ctx, double *wu_done_ms, double *total_ms);
 
+/* Inspection: the tile plan workunit wu runs with, in fstat_get_plan's
+ * layout (out[8], host).  Errors: EINVAL (no such workunit), as
+ * fstat_get_plan otherwise. */
+int fstat_batch_get_plan(fstat_ctx *ctx, int32_t wu, int32_t *out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -92,6 +92,7 @@ SIGNATURES = {
     "fstat_batch_get_toplist": (ctypes.c_int, [_P, _I32, _I32, _P, _P]),
     "fstat_batch_get_2f": (ctypes.c_int, [_P, _I32, _P, _I64, _I64, _I32]),
     "fstat_batch_get_times": (ctypes.c_int, [_P, _P, ctypes.POINTER(_D)]),
+    "fstat_batch_get_plan": (ctypes.c_int, [_P, _I32, _P]),
     "fstat_extract_patches": (ctypes.c_int, [_P, _I32, _I32, _I32, _I32, _I32, _P, _I32, ctypes.c_float,
                                              ctypes.c_float, _P]),
     "fstat_extract_windows": (ctypes.c_int, [_P, _I32, _I32, _I32, _I32, _I32, _P, _I32, ctypes.c_float,
@@ -373,6 +374,13 @@ def fstat_batch_get_2f(ctx, wu: int, offset: int, count: int):
     out = np.empty(count, dtype=np.float32)
     _check(ctx, _lib.fstat_batch_get_2f(ctx, wu, _host_ptr(out), offset, count, FSTAT_MEM_HOST))
     return out
+
+
+def fstat_batch_get_plan(ctx, wu: int) -> dict:
+    out = np.zeros(8, dtype=np.int32)
+    _check(ctx, _lib.fstat_batch_get_plan(ctx, wu, _host_ptr(out)))
+    keys = ("P", "L", "M", "warps", "sft_chunk", "lg_row", "w_pairs", "variant")
+    return {k: int(v) for k, v in zip(keys, out)}
 
 
 def fstat_batch_get_times(ctx, n_wu: int):

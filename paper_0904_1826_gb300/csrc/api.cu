@@ -62,7 +62,10 @@ const FarRow kFarVariants[] = {{7, 2, 0, false, false, 0},  {5, 2, 0, false, fal
                                {1, 1, 4, true, false, 5},   {1, 1, 8, true, false, 5},   {1, 1, 4, true, false, 8},
                                {1, 1, 4, true, false, 4},
                                // two-row tiles, in the order of FS_RING2_VARIANTS: (M, NWC, blocks per SM)
-                               {5, 2, 8, true, false, 0, 2},  {3, 2, 10, true, false, 0, 2}};
+                               {5, 2, 8, true, false, 0, 2},  {3, 2, 10, true, false, 0, 2},
+                               // one-row sinc ring with 4 and 2 compute warps (few spindowns: full blocks
+                               // with narrow columns), in FS_RING_VARIANTS
+                               {5, 2, 4, true, false, 0, 0},  {5, 2, 2, true, false, 0, 0}};
 constexpr int kNumFar = sizeof(kFarVariants) / sizeof(kFarVariants[0]);
 constexpr int kFarIdBase = 100;   // variant ids reported for the far-field form
 
@@ -182,6 +185,10 @@ struct fstat_ctx {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
     cudaStream_t cap_stream = nullptr;
+    // groups after the first run on side streams forked from and joined to the
+    // batch stream, so that one group's blocks fill the SMs another leaves
+    std::vector<cudaStream_t> side_streams;
+    std::vector<cudaEvent_t> side_events;   // [0] fork, [1 + g] join of side stream g
     DirichletParams* d_banks = nullptr;
     long long* d_prefix = nullptr;
     int* d_rem_init = nullptr;
@@ -516,19 +523,26 @@ bool make_far_plan(fstat_ctx* c, int P, int L, bool found, Plan& best) {
                            c->opts.algo == FSTAT_ALGO_SINCROWS || c->opts.algo == FSTAT_ALGO_SINCPAIRS;
     // L = 1 (P = 8) runs the ring in the sinc form only, with plain tables
     const bool ring_l = L == 2 || (L == 1 && want_sinc && !c->have_cov);
-    if (found && ring_l && c->fdot_uniform && (c->opts.tile_warps == 0 || c->opts.tile_warps >= 9)) {
+    const int tw = c->opts.tile_warps;
+    if (found && ring_l && c->fdot_uniform && (tw == 0 || tw >= 9 || (want_sinc && L == 2 && (tw == 3 || tw == 5)))) {
         // M = 5 with 8 stages measured fastest on GB300 (1105 ms on the workunit; M = 7: 1139 ms).
         // For L = 1, M = 1 competes: narrow banks leave an M = 5 lane-group's lanes idle.
         std::vector<int> Mr = {5};
         if (L == 1) Mr = {5, 1};
         if (c->opts.tile_m > 0) Mr = {c->opts.tile_m};
-        int nwc = c->opts.tile_warps ? c->opts.tile_warps - 1 : 10;   // the last warp produces
+        int nwc0 = c->opts.tile_warps ? c->opts.tile_warps - 1 : 10;   // the last warp produces
         // every lane-group needs all P of its threads: P must divide the compute
         // warps (P = 4 takes 8 compute warps unless the caller fixed them)
-        if (nwc % P != 0 && !c->opts.tile_warps && 8 % P == 0) nwc = 8;
+        if (nwc0 % P != 0 && !c->opts.tile_warps && 8 % P == 0) nwc0 = 8;
         double best_r = 1e300;
-        if (nwc % P != 0) Mr.clear();
-        for (int M_ : Mr) {
+        if (nwc0 % P != 0) Mr.clear();
+        // without a warp count from the caller, blocks of 4 and 2 compute warps
+        // compete: banks with few spindowns fill them with narrower columns
+        std::vector<int> nwcs = {nwc0};
+        if (!c->opts.tile_warps && want_sinc && L == 2 && !c->have_cov) nwcs = {nwc0, 4, 2};
+        for (int M_ : Mr)
+        for (int nwc : nwcs) {
+            if (nwc % P != 0) continue;
             int fid = -1;
             for (int i = 0; i < kNumFar; ++i)
                 if (kFarVariants[i].ring == nwc && kFarVariants[i].M == M_ && kFarVariants[i].L == L &&
@@ -540,17 +554,18 @@ bool make_far_plan(fstat_ctx* c, int P, int L, bool found, Plan& best) {
             const int lg_cta = 32 * nwc / P;
             const int lg_max = std::min((c->n_f + PM - 1) / PM, lg_cta);
             for (int lg_row = 1; lg_row <= lg_max; ++lg_row) {
+                // a quarter-warp (8 lane-groups) must not straddle two spindown rows:
+                // its lanes' records then sit 5 positions apart and read conflict-free
+                // (a straddling layout measured 23 % slower on the workunit)
+                if (c->n_fdot > 1 && lg_row % 8 != 0 && lg_row < lg_max) continue;
                 const int col_w = lg_row * PM;
                 const int n_col = (c->n_f + col_w - 1) / col_w;
                 const int w_pairs = std::max(pairs_needed(c, col_w, 8), (M_ - 1) * L + 2 * 8 + 2);
                 int hf = (w_pairs + 1) / 2;
                 hf += ((4 - hf % 8) + 8) % 8;
                 const int w_tab = L == 2 ? 2 * hf : w_pairs;
-                int S = c->opts.sft_chunk > 0 ? c->opts.sft_chunk : 8;
-                while (S > 3 && ring_smem(S, w_tab, want_sinc).total > 110 * 1024) --S;
-                const size_t smem = ring_smem(S, w_tab, want_sinc).total;
-                if (smem > 220 * 1024) continue;
-                double cost = 0.0;
+                // live warps of every block (a block's idle warps still hold its place on the SM)
+                double live = 0.0, blocks = 0.0;
                 int chunks_max = 0;
                 for (int col = 0; col < n_col; ++col) {
                     const int width = std::min(col_w, c->n_f - col * col_w);
@@ -560,32 +575,52 @@ bool make_far_plan(fstat_ctx* c, int P, int L, bool found, Plan& best) {
                     chunks_max = std::max(chunks_max, chunks);
                     for (int k = 0; k < chunks; ++k) {
                         const long long lgs = std::min<long long>(lg_cta, LG - (long long)k * lg_cta);
-                        const long long warps = (lgs + 31) / 32 * P;
-                        // fewer stages leave less slack between the fastest and slowest warp
-                        cost += (double)warps * 32.0 * (40.0 + 50.0 * M_) * (1.0 + 0.2 / S) + 0.05 * w_pairs * 64.0;
+                        live += (double)((lgs + 31) / 32 * P);
+                        blocks += 1.0;
                     }
                 }
-                if (cost < best_r * 0.999) {
-                    best_r = cost;
-                    best = Plan{};
-                    best.P = P;
-                    best.L = L;
-                    best.M = M_;
-                    best.W = nwc + 1;
-                    best.C = S;
-                    best.lg_row = lg_row;
-                    best.lg_cta = lg_cta;
-                    best.n_col = n_col;
-                    best.chunks_per_col = chunks_max;
-                    best.w_pairs = w_pairs;
-                    best.w_tab = w_tab;
-                    best.variant = fid;
-                    best.far = true;
-                    best.ring = true;
-                    best.sinc = want_sinc;
-                    best.smem = smem;
-                    best.grid = (long long)c->n_sky * n_col * chunks_max;
-                    have_ring = true;
+                const int S_hi = c->opts.sft_chunk > 0 ? c->opts.sft_chunk : 8;
+                const int S_lo = c->opts.sft_chunk > 0 ? c->opts.sft_chunk : 3;
+                for (int S = S_hi; S >= S_lo; --S) {
+                    const size_t smem = ring_smem(S, w_tab, want_sinc).total;
+                    if (smem > 220 * 1024) continue;
+                    // Time ~ work / concurrency: the kernel saturates its SM (shared-memory
+                    // loads) at about 20 live compute warps; fewer resident live warps
+                    // (blocks per SM limited by shared memory, threads or ~80 registers
+                    // a thread) leave it latency-bound.  Per live warp and SFT ~40
+                    // instructions of set-up and ~50 per template; staging ~0.05 per
+                    // staged byte; fewer stages leave less slack between warps.
+                    const int threads = 32 * (nwc + 1);
+                    int resident = (int)((227 * 1024) / (smem + 1024));
+                    resident = std::min(resident, 2048 / threads);
+                    resident = std::min(resident, 65536 / (80 * threads));
+                    if (resident < 1) continue;
+                    const double conc = std::min(20.0, resident * live / blocks);
+                    const double work = live * 32.0 * (40.0 + 50.0 * M_) * (1.0 + 0.2 / S) +
+                                        blocks * 0.05 * w_pairs * (want_sinc ? 96.0 : 64.0);
+                    const double cost = work / conc;
+                    if (cost < best_r * 0.999) {
+                        best_r = cost;
+                        best = Plan{};
+                        best.P = P;
+                        best.L = L;
+                        best.M = M_;
+                        best.W = nwc + 1;
+                        best.C = S;
+                        best.lg_row = lg_row;
+                        best.lg_cta = lg_cta;
+                        best.n_col = n_col;
+                        best.chunks_per_col = chunks_max;
+                        best.w_pairs = w_pairs;
+                        best.w_tab = w_tab;
+                        best.variant = fid;
+                        best.far = true;
+                        best.ring = true;
+                        best.sinc = want_sinc;
+                        best.smem = smem;
+                        best.grid = (long long)c->n_sky * n_col * chunks_max;
+                        have_ring = true;
+                    }
                 }
             }
         }
@@ -958,6 +993,8 @@ void fstat_destroy(fstat_ctx* c) {
     cudaDeviceSynchronize();
     fstat_batch_clear(c);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    for (cudaStream_t st : c->side_streams) cudaStreamDestroy(st);
+    for (cudaEvent_t ev : c->side_events) cudaEventDestroy(ev);
     if (c->bev0) cudaEventDestroy(c->bev0);
     if (c->bev1) cudaEventDestroy(c->bev1);
     void* ptrs[] = {c->d_fstart, c->d_base, c->d_bins, c->d_bins16, c->d_scale, c->d_state, c->d_tstart, c->d_det_of, c->d_sky,
@@ -1829,8 +1866,25 @@ int enqueue_batch(fstat_ctx* c, const std::vector<int>& order, const std::vector
     CUDA_TRY(c, cudaMemcpyAsync(c->d_rem, c->d_rem_init, sizeof(int) * n, cudaMemcpyDeviceToDevice, s));
     CUDA_TRY(c, cudaMemsetAsync(c->d_queue, 0, sizeof(unsigned long long) * groups.size(), s));
     const int dev_sms = current_sm_count();
+    const size_t n_side = groups.empty() ? 0 : groups.size() - 1;
+    while (c->side_streams.size() < n_side) {
+        cudaStream_t st;
+        CUDA_TRY(c, cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        c->side_streams.push_back(st);
+    }
+    while (c->side_events.size() < n_side + 1) {
+        cudaEvent_t ev;
+        CUDA_TRY(c, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        c->side_events.push_back(ev);
+    }
+    if (n_side) CUDA_TRY(c, cudaEventRecord(c->side_events[0], s));
     for (size_t g = 0; g < groups.size(); ++g) {
         const BatchGroup& G = groups[g];
+        cudaStream_t gs = s;   // the group's stream
+        if (g > 0) {
+            gs = c->side_streams[g - 1];
+            CUDA_TRY(c, cudaStreamWaitEvent(gs, c->side_events[0], 0));
+        }
         DirichletBatch b{};
         b.banks = c->d_banks + G.first;
         b.item_prefix = c->d_prefix + G.first + g;   // each group's prefix has count + 1 entries
@@ -1843,9 +1897,10 @@ int enqueue_batch(fstat_ctx* c, const std::vector<int>& order, const std::vector
         if (G.ring) {
             e = dirichlet_far_batch_occupancy(G.variant, G.W * 32, G.smem, &occ);
             if (e != cudaSuccess) return fail(c, FSTAT_ECUDA, "occupancy: %s", cudaGetErrorString(e));
-            e = launch_dirichlet_far_batch(G.variant, b, G.W * 32, G.smem, std::max(1, occ) * dev_sms, s);
+            e = launch_dirichlet_far_batch(G.variant, b, G.W * 32, G.smem, std::max(1, occ) * dev_sms, gs);
             if (e != cudaSuccess) return fail(c, FSTAT_ECUDA, "batch Dirichlet launch: %s", cudaGetErrorString(e));
             c->launches += 1;
+            if (g > 0) CUDA_TRY(c, cudaEventRecord(c->side_events[g], gs));
             continue;
         }
         if (G.form == FSTAT_BINS_C64) e = dirichlet_occupancy_c64(G.variant, G.W * 32, G.smem, &occ);
@@ -1853,12 +1908,14 @@ int enqueue_batch(fstat_ctx* c, const std::vector<int>& order, const std::vector
         else e = dirichlet_occupancy_bf16(G.variant, G.W * 32, G.smem, &occ);
         if (e != cudaSuccess) return fail(c, FSTAT_ECUDA, "occupancy: %s", cudaGetErrorString(e));
         const int grid = std::max(1, occ) * dev_sms;
-        if (G.form == FSTAT_BINS_C64) e = launch_dirichlet_batch_c64(G.variant, b, c->opts.dterms, G.W * 32, G.smem, grid, s);
-        else if (G.form == FSTAT_BINS_F16) e = launch_dirichlet_batch_f16(G.variant, b, c->opts.dterms, G.W * 32, G.smem, grid, s);
-        else e = launch_dirichlet_batch_bf16(G.variant, b, c->opts.dterms, G.W * 32, G.smem, grid, s);
+        if (G.form == FSTAT_BINS_C64) e = launch_dirichlet_batch_c64(G.variant, b, c->opts.dterms, G.W * 32, G.smem, grid, gs);
+        else if (G.form == FSTAT_BINS_F16) e = launch_dirichlet_batch_f16(G.variant, b, c->opts.dterms, G.W * 32, G.smem, grid, gs);
+        else e = launch_dirichlet_batch_bf16(G.variant, b, c->opts.dterms, G.W * 32, G.smem, grid, gs);
         if (e != cudaSuccess) return fail(c, FSTAT_ECUDA, "batch Dirichlet launch: %s", cudaGetErrorString(e));
         c->launches += 1;
+        if (g > 0) CUDA_TRY(c, cudaEventRecord(c->side_events[g], gs));
     }
+    for (size_t g = 1; g < groups.size(); ++g) CUDA_TRY(c, cudaStreamWaitEvent(s, c->side_events[g], 0));
     for (fstat_ctx* w : c->wus) {
         int rc = enqueue_topk(w, s);
         if (rc != FSTAT_OK) return fail(c, rc, "%s", w->err.c_str());
@@ -1894,12 +1951,15 @@ int fstat_batch_compute(fstat_ctx* c, void* cuda_stream) {
         cudaEventCreate(&c->bev0);
         cudaEventCreate(&c->bev1);
     }
-    // group workunits by kernel variant and block size (usually one group)
+    // group workunits by kernel variant, block size and blocks resident per SM
+    // (the persistent launch of a group takes its largest shared-memory need,
+    // so a workunit with wide stages must not set the residency of small ones)
     std::vector<int> order(n);
     for (int i = 0; i < n; ++i) order[i] = i;
     auto key = [&](int i) {
         const Plan& pl = c->wus[i]->plan;
-        return (pl.ring ? 1 << 20 : 0) + pl.variant * 64 + pl.W;
+        const int resident = (int)std::min<size_t>(15, (227 * 1024) / (pl.smem + 1024));
+        return (pl.ring ? 1 << 20 : 0) + pl.variant * 1024 + pl.W * 16 + resident;
     };
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return key(a) < key(b); });
     if (!c->graph_valid) {
@@ -1991,6 +2051,15 @@ int fstat_batch_get_2f(fstat_ctx* c, int32_t wu, float* out, int64_t offset, int
     if (!c) return FSTAT_EINVAL;
     if (wu < 0 || wu >= (int)c->wus.size()) return fail(c, FSTAT_EINVAL, "no workunit %d", wu);
     int rc = fstat_get_2f(c->wus[wu], out, offset, count, mem);
+    if (rc != FSTAT_OK) return fail(c, rc, "%s", c->wus[wu]->err.c_str());
+    return FSTAT_OK;
+}
+
+int fstat_batch_get_plan(fstat_ctx* c, int32_t wu, int32_t* out) {
+    if (!c || !out) return FSTAT_EINVAL;
+    c->err.clear();
+    if (wu < 0 || wu >= (int)c->wus.size()) return fail(c, FSTAT_EINVAL, "no workunit %d", wu);
+    const int rc = fstat_get_plan(c->wus[wu], out);
     if (rc != FSTAT_OK) return fail(c, rc, "%s", c->wus[wu]->err.c_str());
     return FSTAT_OK;
 }

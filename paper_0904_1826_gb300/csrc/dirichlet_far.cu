@@ -1222,7 +1222,9 @@ __global__ void __launch_bounds__(32 * (NWC + 1), 2)
     X(12, 5, 10, true)      \
     X(13, 7, 10, true)      \
     X(14, 5, 8, true)       \
-    X(15, 7, 8, true)
+    X(15, 7, 8, true)       \
+    X(29, 5, 4, true)       \
+    X(30, 5, 2, true)
 // the same kernels with per-SFT frequency coverage (single launches only)
 #define FS_RING_COV_VARIANTS(X) \
     X(16, 5, 10, true)          \
