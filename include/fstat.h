@@ -155,7 +155,10 @@ void fstat_destroy(fstat_ctx *ctx);
 /* Message of the last failed call on ctx ("" if none; ctx may be NULL). */
 const char *fstat_last_error(const fstat_ctx *ctx);
 
-/* Load the SFTs of detector `det_index` (0 <= det_index < 8).  All detectors
+/* Load the SFTs of detector `det_index` (0 <= det_index < 8): the "load SFTs"
+ * step, one detector's SFTs into the flat data array with its offsets
+ * (Section "CUDA", version 2 data structure; the per-detector SFT loop of
+ * Listing 1's ComputeFStat reads them).  All detectors
  * of a context share T, k_lo and n_bins.  Loading a detector again replaces
  * its SFTs.
  *   det      geometry of the detector (host)
@@ -173,7 +176,9 @@ int fstat_set_sfts(fstat_ctx *ctx, int32_t det_index, const fstat_detector *det,
                    const float *bins, int32_t mem);
 
 /* Set the template bank: n_sky sky positions x n_fdot spindowns x n_f
- * frequencies f_j = f0 + j df, all at reference time t_ref.
+ * frequencies f_j = f0 + j df, all at reference time t_ref (the frequency
+ * band that Listing 1's ComputeFStatFreqBand loops over, for each sky
+ * position and spindown).
  *   sky   [n_sky][2] (alpha, delta) radians, host
  *   fdot  [n_fdot] Hz/s, host
  * Errors: EINVAL (counts < 1, df <= 0, non-finite values, more than 2^40
@@ -182,7 +187,10 @@ int fstat_set_templates(fstat_ctx *ctx, const double *sky, int32_t n_sky, double
                         int32_t n_f, const double *fdot, int32_t n_fdot, double t_ref);
 
 /* Compute 2F of every template and the top-K toplist, asynchronously on
- * `cuda_stream` (a cudaStream_t; NULL = the legacy default stream).
+ * `cuda_stream` (a cudaStream_t; NULL = the legacy default stream): the whole
+ * of Listing 1 (Section "Einstein@Home") -- ComputeFaFb's sum of
+ * some_calculations over each detector's SFTs, ComputeFStat's sum over
+ * detectors and the normalized combine, for every frequency of the band.
  * Runs: per-SFT detector state, per-(sky, SFT) timing / antenna / phase and
  * bin bases in FP64, the Dirichlet accumulation and 2F combine in FP32, and
  * the toplist selection.  Results stay on the device until read.
@@ -190,7 +198,8 @@ int fstat_set_templates(fstat_ctx *ctx, const double *sky, int32_t n_sky, double
 int fstat_compute(fstat_ctx *ctx, void *cuda_stream);
 
 /* Copy 2F of templates [offset, offset + count) to `out` (host or device per
- * `mem`), after synchronising the context's stream.  FP32.
+ * `mem`), after synchronising the context's stream.  FP32.  (The per-frequency
+ * result ComputeFStat returns in Listing 1.)
  * Errors: ESTATE (nothing computed), EINVAL (range); ETIMEOUT (flag bit 2)
  * or ERANGE (flag bit 0) if the computation raised that device flag, with
  * `out` written all the same. */
@@ -198,6 +207,9 @@ int fstat_get_2f(fstat_ctx *ctx, float *out, int64_t offset, int64_t count, int3
 
 /* Copy the first k (<= topk) toplist entries, ordered by 2F descending then
  * template index ascending, to host arrays idx[k] and twoF[k].  Synchronises.
+ * (The candidates the Einstein@Home client keeps from the F-statistic stage
+ * for its later stage, Section "Einstein@Home"; the ordering of equal values
+ * by index is this library's.)
  * Errors: ESTATE, EINVAL (k out of range); ETIMEOUT / ERANGE as for
  * fstat_get_2f, with the entries written all the same. */
 int fstat_get_toplist(fstat_ctx *ctx, int32_t k, int64_t *idx, float *twoF);
