@@ -82,3 +82,49 @@ def test_precision_forms_on_workunit_data(lib, case):
             assert r["max_rel"] < 5e-3 and r["top1000_overlap"] >= 990, r
         else:
             assert r["max_rel"] < 4e-2 and r["top1000_overlap"] >= 980, r
+
+
+def test_precision_forms_on_the_whole_workunit(lib):
+    """Every form on the whole workunit (1.8e8 templates, the bench's bank),
+    against the FP64 oracle's run over all of it (tests/golden/): overlap of
+    the form's top-1000 with the oracle's top-1000, and |d2F| at the oracle's
+    first 1200 templates and at every sky point's maximum.  The FP32 form
+    keeps the toplist up to near-ties; the 16-bit forms stay at their
+    format's level."""
+    from tests.test_gpu_fullsize import _read_golden
+    from oracle import fstat_oracle as O
+    head, g_idx, g_val, sky_max = _read_golden()
+    w = config1()
+    bins = O.inject(w.detectors, w.T, w.k_lo, w.injections, w.bank.t_ref)
+    top_ref = set(g_idx[:1000].tolist())
+    rows = []
+    for form, kahan, algo in (("c64", False, "auto"), ("c64", True, "direct"), ("f16", False, "auto"),
+                              ("bf16", False, "auto")):
+        g = lib.FStat(0, dterms=w.dterms, topk=1000, bins_form=form, kahan=kahan, algo=algo)
+        try:
+            g.load_workload(w, bins_override=bins)
+            g.compute()
+            assert g.error_flags() == 0
+            idx, _ = g.toplist(1000)
+            allv = g.twoF()
+        finally:
+            g.close()
+        e_top = np.abs(allv[g_idx].astype(np.float64) - g_val)
+        smax = allv.reshape(w.bank.n_sky, -1).max(axis=1).astype(np.float64)
+        e_sky = np.abs(smax - sky_max)
+        rows.append(dict(form=form, kahan=kahan, algo=algo, top1000_overlap=len(set(idx.tolist()) & top_ref),
+                         max_abs_top=float(e_top.max()), p99_abs_top=float(np.percentile(e_top, 99)),
+                         max_rel_top=float(np.max(e_top / (g_val + 1.0))), max_abs_skymax=float(e_sky.max()),
+                         p99_abs_skymax=float(np.percentile(e_sky, 99))))
+    out = os.environ.get("FSTAT_PRECISION_OUT")
+    if out:
+        with open(out.replace(".json", "_whole.json"), "w") as fh:
+            json.dump(dict(templates=int(head["n_templates"]), forms=rows), fh, indent=1)
+    for r in rows:
+        print(r)
+        if r["form"] == "c64":
+            assert r["top1000_overlap"] >= 990 and r["max_abs_top"] <= REL * g_val.max() + ABS, r
+        elif r["form"] == "f16":
+            assert r["top1000_overlap"] >= 950 and r["max_rel_top"] < 5e-3, r
+        else:
+            assert r["top1000_overlap"] >= 800 and r["max_rel_top"] < 4e-2, r
