@@ -385,11 +385,11 @@ void far_extent(const fstat_ctx* c, int w_pairs, int* xoff, int* n_pos) {
 // per block and SFT: ~40 instructions of set-up per thread plus ~58 per
 // template (polynomial, two near pairs, twiddle, accumulation, 6 table
 // loads), ~8 per staged table entry and plane, ~2000 per round (barrier).
-// Plan of the rows form (AUTO or SINCROWS, uniform spindown grid, no
-// coverage, at least 4 spindowns): the (R, NWC) variant with the least
-// modelled work.  Per lane and SFT ~45 instructions of set-up and ~26 per
-// row, idle lanes of the last column and idle rows of the last row chunk
-// included; ~0.05 per staged position and byte; blocks of the last wave.
+// Plan of the rows form (SINCROWS, uniform spindown grid, no coverage, at
+// least 4 spindowns): the (R, NWC) variant with the least modelled work.
+// Per lane and SFT ~45 instructions of set-up and ~26 per row, idle lanes of
+// the last column and idle rows of the last row chunk included; ~0.05 per
+// staged position and byte.
 bool make_rows_plan(fstat_ctx* c, Plan& best) {
     if (!c->fdot_uniform || c->have_cov || c->n_fdot < 4) return false;
     if (c->opts.algo != FSTAT_ALGO_SINCROWS) return false;
