@@ -108,11 +108,11 @@ def algo_of(variant: int) -> str:
     """Form of a plan's kernel variant id (include/fstat.h, fstat_get_plan)."""
     if variant < 100:
         return "direct"
-    if variant >= 127:
+    if variant in (127, 128):
         return "sincpairs"
-    if variant >= 120:
+    if 120 <= variant <= 126:
         return "sincrows"
-    return "sincpoly" if variant in (112, 113, 114, 115, 116, 118, 119) else "farpoly"
+    return "sincpoly" if variant in (112, 113, 114, 115, 116, 118, 119) or variant >= 129 else "farpoly"
 
 
 def kernel_hash(algo: str) -> str:
