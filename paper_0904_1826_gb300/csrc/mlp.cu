@@ -1,6 +1,6 @@
-// Patch-scoring network of the learned-proposal search: BF16 tensor-core
-// matrix products (mma.sync m16n8k16, FP32 accumulation) for the two hidden
-// layers forward and backward, FP32 output layer, loss and Adam.
+// Patch-scoring network of the learned-proposal search: BF16 matrix products
+// on the tcgen05 tensor cores (FP32 accumulation in tensor memory) for the two
+// hidden layers forward and backward, FP32 output layer, loss and Adam.
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -16,138 +16,279 @@ using bf16 = __nv_bfloat16;
 namespace fs {
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 32, KPAD = 8;
-
-__device__ __forceinline__ unsigned int ld_pair(const bf16* p) { return *reinterpret_cast<const unsigned int*>(p); }
-
-__device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned int (&a)[4], const unsigned int (&b)[2]) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
 enum { EPI_F32 = 0, EPI_RELU = 1, EPI_MASK = 2 };
 
+// ---- matrix products on the tcgen05 tensor cores ----------------------------
 // C(m, n) = sum_k A(m, k) B(k, n) (+ bias(n)), A(m, k) = TA ? A[k lda + m] : A[m lda + k],
 // B(k, n) = TB ? B[n ldb + k] : B[k ldb + n]; K, lda, ldb multiples of 8.
 // EPI_F32: Cf = C.  EPI_RELU: Cf = C (pre-activation), Cb = bf16(max(C, 0)).
 // EPI_MASK: C *= (zref > 0); Cf = C, Cb = bf16(C).
-template <bool TA, bool TB, int EPI>
-__global__ void __launch_bounds__(128) gemm_bf16_kernel(int M, int N, int K, const bf16* __restrict__ A, int lda,
-                                                        const bf16* __restrict__ B, int ldb,
-                                                        const float* __restrict__ bias, float* __restrict__ Cf,
-                                                        bf16* __restrict__ Cb, const float* __restrict__ zref,
-                                                        int ldc) {
-    __shared__ __align__(16) bf16 As[BM][BK + KPAD];
-    __shared__ __align__(16) bf16 Bs[BN][BK + KPAD];
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-    const int g = lane >> 2, t = lane & 3;
-    float acc[2][4][4];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
-    const bf16 zero = __float2bfloat16(0.f);
-    for (int k0 = 0; k0 < K; k0 += BK) {
-        // A tile, 8-element vectors along the contiguous axis
-        for (int v = tid; v < BM * BK / 8; v += 128) {
-            if (!TA) {
-                const int mm = v / (BK / 8), kk = (v % (BK / 8)) * 8;
-                const int gm = m0 + mm, gk = k0 + kk;
-                uint4 q = make_uint4(0, 0, 0, 0);
-                if (gm < M && gk < K) q = *reinterpret_cast<const uint4*>(A + (size_t)gm * lda + gk);
-                *reinterpret_cast<uint4*>(&As[mm][kk]) = q;
-            } else {
-                const int kk = v / (BM / 8), mm = (v % (BM / 8)) * 8;
-                const int gm = m0 + mm, gk = k0 + kk;
-                bf16 e[8];
-                if (gk < K && gm + 7 < M) {
-                    *reinterpret_cast<uint4*>(e) = *reinterpret_cast<const uint4*>(A + (size_t)gk * lda + gm);
-                } else {
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) e[i] = (gk < K && gm + i < M) ? A[(size_t)gk * lda + gm + i] : zero;
-                }
-#pragma unroll
-                for (int i = 0; i < 8; ++i) As[mm + i][kk] = e[i];
-            }
-        }
-        for (int v = tid; v < BN * BK / 8; v += 128) {
-            if (TB) {
-                const int nn = v / (BK / 8), kk = (v % (BK / 8)) * 8;
-                const int gn = n0 + nn, gk = k0 + kk;
-                uint4 q = make_uint4(0, 0, 0, 0);
-                if (gn < N && gk < K) q = *reinterpret_cast<const uint4*>(B + (size_t)gn * ldb + gk);
-                *reinterpret_cast<uint4*>(&Bs[nn][kk]) = q;
-            } else {
-                const int kk = v / (BN / 8), nn = (v % (BN / 8)) * 8;
-                const int gn = n0 + nn, gk = k0 + kk;
-                bf16 e[8];
-                if (gk < K && gn + 7 < N) {
-                    *reinterpret_cast<uint4*>(e) = *reinterpret_cast<const uint4*>(B + (size_t)gk * ldb + gn);
-                } else {
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) e[i] = (gk < K && gn + i < N) ? B[(size_t)gk * ldb + gn + i] : zero;
-                }
-#pragma unroll
-                for (int i = 0; i < 8; ++i) Bs[nn + i][kk] = e[i];
-            }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < BK; kk += 16) {
-            unsigned int a[2][4], b[4][2];
-#pragma unroll
-            for (int im = 0; im < 2; ++im) {
-                const int r = wm + im * 16 + g;
-                a[im][0] = ld_pair(&As[r][kk + 2 * t]);
-                a[im][1] = ld_pair(&As[r + 8][kk + 2 * t]);
-                a[im][2] = ld_pair(&As[r][kk + 8 + 2 * t]);
-                a[im][3] = ld_pair(&As[r + 8][kk + 8 + 2 * t]);
-            }
-#pragma unroll
-            for (int in = 0; in < 4; ++in) {
-                const int c = wn + in * 8 + g;
-                b[in][0] = ld_pair(&Bs[c][kk + 2 * t]);
-                b[in][1] = ld_pair(&Bs[c][kk + 8 + 2 * t]);
-            }
-#pragma unroll
-            for (int im = 0; im < 2; ++im)
-#pragma unroll
-                for (int in = 0; in < 4; ++in) mma_bf16(acc[im][in], a[im], b[in]);
-        }
-        __syncthreads();
+// One CTA (4 warps) computes a TC_M x TC_N tile of C over the K range of its
+// chunk (blockIdx.z).  Per TC_K-wide slice of K the threads stage A (TC_M x TC_K)
+// and B (TC_N x TC_K, i.e. B^T) into shared memory in the K-major core-matrix
+// layout without swizzle: a core matrix is 8 rows x 8 elements (8 x 16 bytes,
+// rows 16 bytes apart), and the core matrix of rows 8i.. and columns 8j.. of
+// an R-row tile sits at byte (j * R / 8 + i) * 128.  One thread then issues
+// TC_K / 16 MMAs of kind::f16 (BF16 A and B, FP32 D, M = 128, N = 64, K = 16)
+// on shared-memory descriptors (leading-dimension step: the next 8 columns,
+// R * 16 bytes; stride step: the next 8 rows, 128 bytes) into a TMEM
+// accumulator of 64 columns and commits them to the stage's mbarrier.  Two
+// stages: the threads stage slice k + 1 while the tensor core runs slice k,
+// and wait (bounded) for slice k - 1's MMAs before reusing its stage.  The
+// epilogue reads the tile back with tcgen05.ld (warp w owns TMEM lanes, i.e.
+// rows, 32w .. 32w + 31); with several K chunks it writes the raw FP32 tile of
+// its chunk to part[z][M][N] and splitk_epi_kernel finishes the sum.
+constexpr int TC_M = 128, TC_N = 64, TC_K = 64;
+constexpr int TC_A_BYTES = TC_M * TC_K * 2, TC_B_BYTES = TC_N * TC_K * 2;
+constexpr int TC_STAGE_BYTES = TC_A_BYTES + TC_B_BYTES;
+constexpr int TC_SMEM = 2 * TC_STAGE_BYTES + 32;   // two stages, two mbarriers, the TMEM address
+// instruction descriptor: D F32 (bits 4-5 = 1), A and B BF16 (bits 7-9, 10-12 = 1),
+// both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28
+constexpr uint32_t TC_IDESC =
+    (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_N >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
+
+// Shared-memory matrix descriptor: start address >> 4 (bits 0-13), leading-
+// dimension byte offset >> 4 (16-29), stride-dimension byte offset >> 4
+// (32-45), the fixed value 1 at bits 46-48, no swizzle (bits 61-63 = 0).
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+           (1ull << 46);
+}
+
+__device__ __forceinline__ uint32_t tc_smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Byte offset of element (r, k) of an R-row tile in the core-matrix layout.
+__device__ __forceinline__ uint32_t tc_off(int R, int r, int k) {
+    return (uint32_t)((((k >> 3) * (R >> 3) + (r >> 3)) << 7) + ((r & 7) << 4) + ((k & 7) << 1));
+}
+
+// Bounded wait (about two seconds) for the phase of parity `parity`; every
+// thread of the block takes the same decision.
+__device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t parity) {
+    uint32_t done = 0;
+    unsigned long long t0 = 0;
+    for (unsigned int it = 0;; ++it) {
+        asm volatile(
+            "{\n"
+            " .reg .pred p;\n"
+            " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n"
+            "}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) break;
+        unsigned long long t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        if (it == 0) t0 = t;
+        else if (t - t0 > 2000000000ull) break;
     }
+    return __syncthreads_and(done != 0) != 0;
+}
+
+template <bool TA, bool TB>
+__device__ __forceinline__ void tc_stage(unsigned char* As, unsigned char* Bs, int M, int N, int K, const bf16* A,
+                                         int lda, const bf16* B, int ldb, int m0, int n0, int k0, int kend) {
+    const int tid = threadIdx.x;
+    const bf16 zero = __float2bfloat16(0.f);
+    // A slice: TC_M rows x TC_K columns (K-major in shared memory)
+    for (int v = tid; v < TC_M * TC_K / 8; v += 128) {
+        if (!TA) {   // 8 consecutive k of one row
+            const int r = v / (TC_K / 8), kk = (v % (TC_K / 8)) * 8;
+            const int gm = m0 + r, gk = k0 + kk;
+            uint4 q = make_uint4(0, 0, 0, 0);
+            if (gm < M && gk < kend) q = *reinterpret_cast<const uint4*>(A + (size_t)gm * lda + gk);
+            *reinterpret_cast<uint4*>(As + tc_off(TC_M, r, kk)) = q;
+        } else {     // 8 consecutive rows of one k
+            const int kk = v / (TC_M / 8), r = (v % (TC_M / 8)) * 8;
+            const int gm = m0 + r, gk = k0 + kk;
+            bf16 e[8];
+            if (gk < kend && gm + 7 < M) {
+                *reinterpret_cast<uint4*>(e) = *reinterpret_cast<const uint4*>(A + (size_t)gk * lda + gm);
+            } else {
 #pragma unroll
-    for (int im = 0; im < 2; ++im)
+                for (int i = 0; i < 8; ++i) e[i] = (gk < kend && gm + i < M) ? A[(size_t)gk * lda + gm + i] : zero;
+            }
 #pragma unroll
-        for (int in = 0; in < 4; ++in)
+            for (int i = 0; i < 8; ++i) *reinterpret_cast<bf16*>(As + tc_off(TC_M, r + i, kk)) = e[i];
+        }
+    }
+    // B slice as B^T: TC_N rows (n) x TC_K columns (k)
+    for (int v = tid; v < TC_N * TC_K / 8; v += 128) {
+        if (TB) {    // 8 consecutive k of one n
+            const int r = v / (TC_K / 8), kk = (v % (TC_K / 8)) * 8;
+            const int gn = n0 + r, gk = k0 + kk;
+            uint4 q = make_uint4(0, 0, 0, 0);
+            if (gn < N && gk < kend) q = *reinterpret_cast<const uint4*>(B + (size_t)gn * ldb + gk);
+            *reinterpret_cast<uint4*>(Bs + tc_off(TC_N, r, kk)) = q;
+        } else {     // 8 consecutive n of one k
+            const int kk = v / (TC_N / 8), r = (v % (TC_N / 8)) * 8;
+            const int gn = n0 + r, gk = k0 + kk;
+            bf16 e[8];
+            if (gk < kend && gn + 7 < N) {
+                *reinterpret_cast<uint4*>(e) = *reinterpret_cast<const uint4*>(B + (size_t)gk * ldb + gn);
+            } else {
 #pragma unroll
-            for (int h = 0; h < 2; ++h)
+                for (int i = 0; i < 8; ++i) e[i] = (gk < kend && gn + i < N) ? B[(size_t)gk * ldb + gn + i] : zero;
+            }
 #pragma unroll
-                for (int j = 0; j < 2; ++j) {
-                    const int row = m0 + wm + im * 16 + g + 8 * h;
-                    const int col = n0 + wn + in * 8 + 2 * t + j;
-                    if (row >= M || col >= N) continue;
-                    float v = acc[im][in][2 * h + j];
-                    if (bias) v += bias[col];
+            for (int i = 0; i < 8; ++i) *reinterpret_cast<bf16*>(Bs + tc_off(TC_N, r + i, kk)) = e[i];
+        }
+    }
+}
+
+template <bool TA, bool TB, int EPI>
+__global__ void __launch_bounds__(128) gemm_tc_kernel(int M, int N, int K, const bf16* __restrict__ A, int lda,
+                                                      const bf16* __restrict__ B, int ldb,
+                                                      const float* __restrict__ bias, float* __restrict__ Cf,
+                                                      bf16* __restrict__ Cb, const float* __restrict__ zref, int ldc,
+                                                      float* __restrict__ part, int kchunk, int* __restrict__ flag) {
+    extern __shared__ __align__(128) unsigned char tsm[];
+    uint64_t* bars = reinterpret_cast<uint64_t*>(tsm + 2 * TC_STAGE_BYTES);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(tsm + 2 * TC_STAGE_BYTES + 16);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.y * TC_M, n0 = blockIdx.x * TC_N;
+    const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
+    const int n_sl = (ke - kb + TC_K - 1) / TC_K;   // >= 1 (the host makes every chunk non-empty)
+    const uint32_t bar0 = tc_smem_u32(bars);
+    if (warp == 0) {   // the whole warp allocates the 64 accumulator columns
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(tc_smem_u32(tslot))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+    uint32_t ph0 = 0, ph1 = 0;   // parity of the next wait on each stage's barrier
+    bool ok = true;
+    int it = 0;
+    for (; it < n_sl; ++it) {
+        const int st = it & 1;
+        if (it >= 2) {   // the MMAs of slice it - 2 read this stage
+            ok = tc_wait(bar0 + 8 * st, st ? ph1 : ph0);
+            if (st) ph1 ^= 1u; else ph0 ^= 1u;
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        }
+        unsigned char* As = tsm + st * TC_STAGE_BYTES;
+        unsigned char* Bs = As + TC_A_BYTES;
+        tc_stage<TA, TB>(As, Bs, M, N, K, A, lda, B, ldb, m0, n0, kb + it * TC_K, ke);
+        // the tensor core reads shared memory through the async proxy
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a_base = tc_smem_u32(As), b_base = tc_smem_u32(Bs);
+#pragma unroll
+            for (int s = 0; s < TC_K / 16; ++s) {
+                const uint64_t ad = tc_desc(a_base + (uint32_t)(2 * s * (TC_M / 8) * 128), (TC_M / 8) * 128, 128);
+                const uint64_t bd = tc_desc(b_base + (uint32_t)(2 * s * (TC_N / 8) * 128), (TC_N / 8) * 128, 128);
+                const uint32_t acc = (it > 0 || s > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n"
+                    " .reg .pred p;\n"
+                    " setp.ne.u32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
+                    "}\n" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(TC_IDESC), "r"(acc)
+                    : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             bar0 + 8 * st)
+                         : "memory");
+        }
+    }
+    // drain: the commits of the last two slices
+    if (ok) {
+        for (int j = max(0, n_sl - 2); j < n_sl && ok; ++j) {
+            const int st = j & 1;
+            ok = tc_wait(bar0 + 8 * st, st ? ph1 : ph0);
+            if (st) ph1 ^= 1u; else ph0 ^= 1u;
+        }
+    }
+    if (!ok && tid == 0) atomicOr(flag, 1);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+        const int row = m0 + warp * 32 + lane;
+        float* pz = part ? part + (size_t)blockIdx.z * M * N : nullptr;
+#pragma unroll 1
+        for (int c0 = 0; c0 < TC_N; c0 += 16) {
+            uint32_t v[16];
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                "[%16];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                  "=r"(v[15])
+                : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (row < M) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int col = n0 + c0 + j;
+                    if (col >= N) continue;
+                    float x = __uint_as_float(v[j]);
+                    if (pz) {   // one K chunk of several: raw partial sum
+                        pz[(size_t)row * N + col] = x;
+                        continue;
+                    }
+                    if (bias) x += bias[col];
                     const size_t o = (size_t)row * ldc + col;
                     if (EPI == EPI_F32) {
-                        Cf[o] = v;
+                        Cf[o] = x;
                     } else if (EPI == EPI_RELU) {
-                        Cf[o] = v;
-                        Cb[o] = __float2bfloat16_rn(fmaxf(v, 0.f));
+                        Cf[o] = x;
+                        Cb[o] = __float2bfloat16_rn(fmaxf(x, 0.f));
                     } else {
-                        v = zref[o] > 0.f ? v : 0.f;
-                        Cf[o] = v;
-                        Cb[o] = __float2bfloat16_rn(v);
+                        x = zref[o] > 0.f ? x : 0.f;
+                        Cf[o] = x;
+                        Cb[o] = __float2bfloat16_rn(x);
                     }
                 }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem) : "memory");
+    }
+    if (ok && tid == 0) {
+        asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar0) : "memory");
+        asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar0 + 8) : "memory");
+    }
+}
+
+// Sum of the K chunks' partial tiles in chunk order, then the epilogue.
+template <int EPI>
+__global__ void splitk_epi_kernel(int M, int N, int splits, const float* __restrict__ part,
+                                  const float* __restrict__ bias, float* __restrict__ Cf, bf16* __restrict__ Cb,
+                                  const float* __restrict__ zref, int ldc) {
+    const long long MN = (long long)M * N;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < MN; i += (long long)gridDim.x * blockDim.x) {
+        float x = part[i];
+        for (int z = 1; z < splits; ++z) x += part[z * MN + i];
+        const int row = (int)(i / N), col = (int)(i - (long long)row * N);
+        if (bias) x += bias[col];
+        const size_t o = (size_t)row * ldc + col;
+        if (EPI == EPI_F32) {
+            Cf[o] = x;
+        } else if (EPI == EPI_RELU) {
+            Cf[o] = x;
+            Cb[o] = __float2bfloat16_rn(fmaxf(x, 0.f));
+        } else {
+            x = zref[o] > 0.f ? x : 0.f;
+            Cf[o] = x;
+            Cb[o] = __float2bfloat16_rn(x);
+        }
+    }
 }
 
 // Output layer and loss, one warp per row: s = relu(z2) . w3 + b3;
@@ -270,11 +411,40 @@ __global__ void window_kernel(const float* __restrict__ twoF, int n_f, int n_a, 
     }
 }
 
+// Device scratch of the products: the give-up flag and the K-chunk partial
+// tiles (capacity `cap` floats).
+struct TcWork {
+    int* flag = nullptr;
+    float* part = nullptr;
+    size_t cap = 0;
+};
+
+// Tiles of the tcgen05 form; a product with few tiles splits K into chunks
+// (at least 4 slices each) so that about two CTAs per SM run, and sums them
+// in chunk order.
 template <bool TA, bool TB, int EPI>
 cudaError_t gemm(int M, int N, int K, const bf16* A, int lda, const bf16* B, int ldb, const float* bias, float* Cf,
-                 bf16* Cb, const float* zref, int ldc, cudaStream_t s) {
-    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
-    gemm_bf16_kernel<TA, TB, EPI><<<grid, 128, 0, s>>>(M, N, K, A, lda, B, ldb, bias, Cf, Cb, zref, ldc);
+                 bf16* Cb, const float* zref, int ldc, cudaStream_t s, const TcWork& w) {
+    float* part = w.part;
+    int* flag = w.flag;
+    const size_t cap = w.cap;
+    auto fn = gemm_tc_kernel<TA, TB, EPI>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+    if (e != cudaSuccess) return e;
+    const int tiles = ((N + TC_N - 1) / TC_N) * ((M + TC_M - 1) / TC_M);
+    const int n_sl = (K + TC_K - 1) / TC_K;
+    int splits = std::min((2 * current_sm_count() + tiles - 1) / tiles, std::max(1, n_sl / 4));
+    while (splits > 1 && (size_t)splits * M * N > cap) --splits;
+    const int kchunk = ((n_sl + splits - 1) / splits) * TC_K;
+    splits = (K + kchunk - 1) / kchunk;   // every chunk non-empty
+    dim3 grid((N + TC_N - 1) / TC_N, (M + TC_M - 1) / TC_M, splits);
+    fn<<<grid, 128, TC_SMEM, s>>>(M, N, K, A, lda, B, ldb, bias, Cf, Cb, zref, ldc, splits > 1 ? part : nullptr,
+                                  kchunk, flag);
+    if (splits > 1) {
+        const long long MN = (long long)M * N;
+        const int g = (int)std::min<long long>((MN + 255) / 256, 4LL * current_sm_count());
+        splitk_epi_kernel<EPI><<<g, 256, 0, s>>>(M, N, splits, part, bias, Cf, Cb, zref, ldc);
+    }
     return cudaGetLastError();
 }
 
@@ -312,6 +482,7 @@ struct fstat_mlp {
     float *dz2 = nullptr, *dz1 = nullptr;
     bf16 *dz2b = nullptr, *dz1b = nullptr;
     int t = 0;
+    TcWork tcw;                 // flag (bit 0: a tensor-core wait gave up) and K-chunk partial products
     cudaStream_t stream = nullptr;
     std::vector<void*> allocs;
 };
@@ -342,6 +513,15 @@ int alloc(fstat_mlp* m, T** p, size_t n) {
     return cudaMemset(*p, 0, std::max<size_t>(n, 1) * sizeof(T)) == cudaSuccess ? FSTAT_OK : FSTAT_ECUDA;
 }
 
+// After a synchronisation: a tensor-core completion wait that gave up makes
+// the call fail (its products were not written).
+int check_flag(fstat_mlp* m) {
+    int f = 0;
+    MLP_TRY(m, cudaMemcpy(&f, m->tcw.flag, sizeof(int), cudaMemcpyDeviceToHost));
+    if (f) return mfail(m, FSTAT_ECUDA, "a tensor-core completion wait gave up (flag %d)", f);
+    return FSTAT_OK;
+}
+
 // Stage X (host or device) into the network's BF16 input buffer.
 int stage_input(fstat_mlp* m, const uint16_t* X, int B, int mem, cudaStream_t s, const bf16** Xd) {
     if (mem == FSTAT_MEM_DEVICE) {
@@ -355,8 +535,10 @@ int stage_input(fstat_mlp* m, const uint16_t* X, int B, int mem, cudaStream_t s,
 
 int run_forward(fstat_mlp* m, const bf16* X, int B, cudaStream_t s) {
     const int n_in = m->n_in, H = m->H;
-    MLP_TRY(m, (gemm<false, false, EPI_RELU>(B, H, n_in, X, n_in, m->W1b, H, m->b1, m->z1, m->h1, nullptr, H, s)));
-    MLP_TRY(m, (gemm<false, false, EPI_RELU>(B, H, H, m->h1, H, m->W2b, H, m->b2, m->z2, m->h2, nullptr, H, s)));
+    MLP_TRY(m, (gemm<false, false, EPI_RELU>(B, H, n_in, X, n_in, m->W1b, H, m->b1, m->z1, m->h1,
+                                             nullptr, H, s, m->tcw)));
+    MLP_TRY(m, (gemm<false, false, EPI_RELU>(B, H, H, m->h1, H, m->W2b, H, m->b2, m->z2, m->h2,
+                                             nullptr, H, s, m->tcw)));
     return FSTAT_OK;
 }
 
@@ -403,6 +585,9 @@ int fstat_mlp_create(fstat_mlp** out, int device, int32_t n_in, int32_t n_hidden
     if (rc == FSTAT_OK) rc = alloc(m, &m->dz1, Bm * H);
     if (rc == FSTAT_OK) rc = alloc(m, &m->dz2b, Bm * H);
     if (rc == FSTAT_OK) rc = alloc(m, &m->dz1b, Bm * H);
+    if (rc == FSTAT_OK) rc = alloc(m, &m->tcw.flag, 1);
+    m->tcw.cap = 16 * std::max(Bm, H) * H;
+    if (rc == FSTAT_OK) rc = alloc(m, &m->tcw.part, m->tcw.cap);
     if (rc != FSTAT_OK) {
         fstat_mlp_destroy(m);
         return rc;
@@ -475,6 +660,7 @@ int fstat_mlp_forward(fstat_mlp* m, const uint16_t* X, int32_t B, float* logits,
     } else {
         MLP_TRY(m, cudaMemcpyAsync(logits, m->s, B * sizeof(float), cudaMemcpyDeviceToHost, s));
         MLP_TRY(m, cudaStreamSynchronize(s));
+        return check_flag(m);
     }
     return FSTAT_OK;
 }
@@ -502,10 +688,13 @@ int fstat_mlp_train_step(fstat_mlp* m, const uint16_t* X, const float* y, int32_
     colsum_kernel<<<(H + 127) / 128, 128, 0, s>>>(m->dz2, B, H, m->gb2);
     MLP_TRY(m, cudaGetLastError());
     // dW2 = h1^T dz2;  dz1 = (dz2 W2^T) * (z1 > 0);  dW1 = X^T dz1
-    MLP_TRY(m, (gemm<true, false, EPI_F32>(H, H, B, m->h1, H, m->dz2b, H, nullptr, m->gW2, nullptr, nullptr, H, s)));
-    MLP_TRY(m, (gemm<false, true, EPI_MASK>(B, H, H, m->dz2b, H, m->W2b, H, nullptr, m->dz1, m->dz1b, m->z1, H, s)));
+    MLP_TRY(m, (gemm<true, false, EPI_F32>(H, H, B, m->h1, H, m->dz2b, H, nullptr, m->gW2, nullptr,
+                                           nullptr, H, s, m->tcw)));
+    MLP_TRY(m, (gemm<false, true, EPI_MASK>(B, H, H, m->dz2b, H, m->W2b, H, nullptr, m->dz1, m->dz1b,
+                                            m->z1, H, s, m->tcw)));
     colsum_kernel<<<(H + 127) / 128, 128, 0, s>>>(m->dz1, B, H, m->gb1);
-    MLP_TRY(m, (gemm<true, false, EPI_F32>(I, H, B, Xd, I, m->dz1b, H, nullptr, m->gW1, nullptr, nullptr, H, s)));
+    MLP_TRY(m, (gemm<true, false, EPI_F32>(I, H, B, Xd, I, m->dz1b, H, nullptr, m->gW1, nullptr,
+                                           nullptr, H, s, m->tcw)));
     // Adam
     m->t += 1;
     const float c1 = 1.f / (1.f - powf(0.9f, (float)m->t)), c2 = 1.f / (1.f - powf(0.999f, (float)m->t));
@@ -520,6 +709,7 @@ int fstat_mlp_train_step(fstat_mlp* m, const uint16_t* X, const float* y, int32_
     if (loss) {
         MLP_TRY(m, cudaMemcpyAsync(loss, m->loss, sizeof(float), cudaMemcpyDeviceToHost, s));
         MLP_TRY(m, cudaStreamSynchronize(s));
+        return check_flag(m);
     }
     return FSTAT_OK;
 }
@@ -533,7 +723,7 @@ int fstat_mlp_get_grads(fstat_mlp* m, float* dW1, float* db1, float* dW2, float*
     const float* src[6] = {m->gW1, m->gb1, m->gW2, m->gb2, m->gw3, m->gb3};
     const size_t n[6] = {I * H, H, H * H, H, H, 1};
     for (int i = 0; i < 6; ++i) MLP_TRY(m, cudaMemcpy(dst[i], src[i], n[i] * sizeof(float), cudaMemcpyDeviceToHost));
-    return FSTAT_OK;
+    return check_flag(m);
 }
 
 }  // extern "C"
