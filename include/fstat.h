@@ -112,7 +112,9 @@ typedef struct {
  *   and are slower than SINCPOLY on the workunit-sized bank; they are kept as
  *   options.  Batched workunits use the TMA-ring form where it applies, else
  *   DIRECT.
- * AUTO: SINCPOLY where the TMA ring applies, else FARPOLY where it applies,
+ * AUTO: SINCPOLY where the TMA ring applies, except on a bank of one
+ *   spindown with L = 2, where the ring is bound by its table copies and
+ *   FARPOLY's smaller records are faster; else FARPOLY where it applies,
  *   else DIRECT. */
 typedef enum {
     FSTAT_ALGO_AUTO = 0,
@@ -319,6 +321,8 @@ int fstat_take_kernel_time(fstat_ctx *ctx, double *ms_dirichlet, double *ms_tota
  * points, a few waves of blocks) and keep the fastest as the context's tile
  * choice for later computes.  out[4] (host, may be NULL) receives
  * (M, sft_chunk, warps, best kernel time on the slice in microseconds).
+ * A batch context (workunits only) tunes on its largest workunit and gives
+ * every workunit that M; each keeps the stage count its own plan chooses.
  * Synchronises.  Errors: ESTATE (no SFTs or templates). */
 int fstat_autotune(fstat_ctx *ctx, void *cuda_stream, int32_t *out);
 

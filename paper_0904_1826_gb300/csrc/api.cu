@@ -517,13 +517,18 @@ bool make_far_plan(fstat_ctx* c, int P, int L, bool found, Plan& best) {
     bool have_ring = false;
     // TMA-ring form first: L = 2, compact spindown bases
     // default: 10 compute warps + 1 copy warp (measured fastest on GB300); tile_warps 9 / 11 choose 8 / 10
-    // AUTO takes the sinc-polynomial form where the ring applies (1027 ms per
-    // workunit launch on GB300 against 1105 ms for near pairs + far polynomial)
-    const bool want_sinc = c->opts.algo == FSTAT_ALGO_SINCPOLY || c->opts.algo == FSTAT_ALGO_AUTO ||
-                           c->opts.algo == FSTAT_ALGO_SINCROWS || c->opts.algo == FSTAT_ALGO_SINCPAIRS;
+    // AUTO takes the sinc-polynomial form where the ring applies (731 ms per
+    // workunit launch on GB300 against 1106 ms for near pairs + far polynomial)
+    const int tw = c->opts.tile_warps;
+    // A bank of one spindown row stages a table row per template and SFT: the
+    // ring is then bound by its copies, and AUTO takes the far-field form's
+    // 64-byte positions over the sinc form's 96 (measured on GB300, 2048 sky x
+    // 900 f x 1600 SFTs: 14.4 against 18.6 ms; with two rows they tie)
+    const bool auto_far = c->opts.algo == FSTAT_ALGO_AUTO && L == 2 && c->n_fdot == 1 && tw != 3 && tw != 5;
+    const bool want_sinc = !auto_far && (c->opts.algo == FSTAT_ALGO_SINCPOLY || c->opts.algo == FSTAT_ALGO_AUTO ||
+                                         c->opts.algo == FSTAT_ALGO_SINCROWS || c->opts.algo == FSTAT_ALGO_SINCPAIRS);
     // L = 1 (P = 8) runs the ring in the sinc form only, with plain tables
     const bool ring_l = L == 2 || (L == 1 && want_sinc && !c->have_cov);
-    const int tw = c->opts.tile_warps;
     if (found && ring_l && c->fdot_uniform && (tw == 0 || tw >= 9 || (want_sinc && L == 2 && (tw == 3 || tw == 5)))) {
         // M = 5 with 8 stages measured fastest on GB300 (1105 ms on the workunit; M = 7: 1139 ms).
         // For L = 1, M = 1 competes: narrow banks leave an M = 5 lane-group's lanes idle.
@@ -536,10 +541,10 @@ bool make_far_plan(fstat_ctx* c, int P, int L, bool found, Plan& best) {
         if (nwc0 % P != 0 && !c->opts.tile_warps && 8 % P == 0) nwc0 = 8;
         double best_r = 1e300;
         if (nwc0 % P != 0) Mr.clear();
-        // without a warp count from the caller, blocks of 4 and 2 compute warps
-        // compete: banks with few spindowns fill them with narrower columns
-        std::vector<int> nwcs = {nwc0};
-        if (!c->opts.tile_warps && want_sinc && L == 2 && !c->have_cov) nwcs = {nwc0, 4, 2};
+        // blocks of 4 and 2 compute warps (tile_warps 5 and 3) only on request:
+        // on GB300 the 10-warp block was faster on every bank measured, by 20-60 %
+        // on banks of 1-16 spindowns where the cost model favoured the small ones
+        const std::vector<int> nwcs = {nwc0};
         for (int M_ : Mr)
         for (int nwc : nwcs) {
             if (nwc % P != 0) continue;
@@ -1649,7 +1654,10 @@ int fstat_take_kernel_time(fstat_ctx* c, double* ms_dirichlet, double* ms_total,
 int fstat_autotune(fstat_ctx* c, void* cuda_stream, int32_t* out) {
     if (!c) return FSTAT_EINVAL;
     c->err.clear();
-    // a context holding only workunits tunes on its largest one and applies the choice to all
+    // a context holding only workunits tunes on its largest one and applies its
+    // templates per thread to all; each workunit keeps the planner's stage count,
+    // which follows its own table width and residency (one stage count for all
+    // cost up to 60 % on workunits whose stages then left one block per SM)
     if ((!c->have_sfts || !c->have_templates) && !c->wus.empty()) {
         fstat_ctx* big = c->wus[0];
         for (fstat_ctx* w : c->wus)
@@ -1660,11 +1668,9 @@ int fstat_autotune(fstat_ctx* c, void* cuda_stream, int32_t* out) {
         if (rc != FSTAT_OK) return fail(c, rc, "autotune: %s", big->err.c_str());
         for (fstat_ctx* w : c->wus) {
             w->opts.tile_m = o[0];
-            w->opts.sft_chunk = o[1];
             w->plan_valid = false;
         }
         c->opts.tile_m = o[0];
-        c->opts.sft_chunk = o[1];
         c->graph_valid = false;
         if (out) std::memcpy(out, o, sizeof(o));
         return FSTAT_OK;

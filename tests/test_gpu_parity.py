@@ -164,16 +164,18 @@ def test_row_tiled_forms_on_ragged_row_counts(lib, algo, ids, n_fdot, df_bins):
 @pytest.mark.parametrize("tile_warps,variant", [(3, 130), (5, 129), (0, None)])
 @pytest.mark.parametrize("n_fdot", [1, 2, 3])
 def test_small_block_rings_on_few_spindowns(lib, tile_warps, variant, n_fdot):
-    """The one-row sinc ring with 2 and 4 compute warps (chosen by the
-    planner for banks with few spindowns, or forced by tile_warps = 3 / 5):
-    parity and the toplist on a wide band with a ragged last column."""
+    """The one-row sinc ring with 2 and 4 compute warps (tile_warps = 3 / 5)
+    and the planner's own choice (the 10-warp sinc ring; the far-field ring
+    for one spindown): parity and the toplist on a wide band with a ragged
+    last column."""
     w = config_mid(n_f=410, n_fdot=n_fdot, n_sky=3, n_bins=520)
     bins = _oracle_bins(w)
     ref = O.compute_fstat_freq_band(_dets(w, bins), w.T, w.k_lo, w.dterms, w.bank).ravel()
     out = _gpu(lib, w, bins, tile_warps=tile_warps)
     if variant is not None:
         assert out["plan"]["variant"] == variant
-    assert out["plan"]["variant"] in (112, 129, 130)
+    else:
+        assert out["plan"]["variant"] == (110 if n_fdot == 1 else 112)
     assert out["flags"] == 0
     _assert_parity(out["twoF"], ref, f"tile_warps={tile_warps} n_fdot={n_fdot}")
     _check_toplist(out["top"], out["twoF"], ref, w.topk)
