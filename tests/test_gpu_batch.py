@@ -104,3 +104,36 @@ def test_autotune_picks_a_valid_tiling_and_keeps_parity(lib, algo, chunks):
         assert np.all(np.abs(got - ref) <= REL * ref + ABS)
     finally:
         g.close()
+
+
+def test_batch_autotune_gives_m_and_keeps_each_plans_stages(lib):
+    """A batch context tunes on its largest workunit and gives every workunit
+    that M; each keeps the stage count its own plan chooses (the count a
+    single context with the same M plans for it), and results stay those of
+    the single launches."""
+    specs = config3_specs(3, seed=3300)
+    shapes = [dict(n_sky=40, n_sft_total=160, band=0.05), dict(n_sky=60, n_sft_total=200, band=0.12),
+              dict(n_sky=30, n_sft_total=120, band=0.08)]
+    wus = [config3_workunit(sp, **sh) for sp, sh in zip(specs, shapes)]
+    g = lib.FStat(0, topk=10)
+    try:
+        for w in wus:
+            lib.fstat_batch_add(g.ctx, w)
+        t = lib.fstat_autotune(g.ctx)
+        assert t["M"] in (5, 7, 9)
+        for i, w in enumerate(wus):
+            lib.fstat_batch_compute_one(g.ctx, i)
+            pl = lib.fstat_batch_get_plan(g.ctx, i)
+            got = lib.fstat_batch_get_2f(g.ctx, i, 0, w.n_templates)
+            s = lib.FStat(0, topk=10, tile_m=t["M"])
+            try:
+                s.load_workload(w)
+                s.compute()
+                ps = s.plan()
+                ref = s.twoF()
+            finally:
+                s.close()
+            assert pl["M"] == ps["M"] and pl["sft_chunk"] == ps["sft_chunk"] and pl["variant"] == ps["variant"], (pl, ps)
+            np.testing.assert_array_equal(got, ref)
+    finally:
+        g.close()
