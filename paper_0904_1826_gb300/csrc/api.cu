@@ -1666,8 +1666,9 @@ int fstat_autotune(fstat_ctx* c, void* cuda_stream, int32_t* out) {
         int32_t o[4];
         int rc = fstat_autotune(big, cuda_stream, o);
         if (rc != FSTAT_OK) return fail(c, rc, "autotune: %s", big->err.c_str());
-        for (fstat_ctx* w : c->wus) {
+        for (fstat_ctx* w : c->wus) {   // the tuned workunit too returns to the caller's stage count
             w->opts.tile_m = o[0];
+            w->opts.sft_chunk = c->opts.sft_chunk;
             w->plan_valid = false;
         }
         c->opts.tile_m = o[0];
