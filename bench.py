@@ -112,6 +112,8 @@ def algo_of(variant: int) -> str:
         return "sincpairs"
     if 120 <= variant <= 126:
         return "sincrows"
+    if variant in (117, 132):   # far field with coverage; blocks of 4 sky points
+        return "farpoly"
     return "sincpoly" if variant in (112, 113, 114, 115, 116, 118, 119) or variant >= 129 else "farpoly"
 
 

@@ -49,6 +49,7 @@ struct FarRow {
     bool cov;   // per-SFT frequency coverage compiled in (ring only; single launches)
     int rows;   // rows form: spindown rows per lane (one frequency per lane), 0 = templates along frequency
     int minb;   // two-row tiles (sinc, L = 2): resident blocks per SM the kernel is built for, 0 = one row
+    int sr;     // one-row ring with blocks of `sr` consecutive sky points (0: one)
 };
 const FarRow kFarVariants[] = {{7, 2, 0, false, false, 0},  {5, 2, 0, false, false, 0},  {9, 2, 0, false, false, 0},
                                {7, 1, 0, false, false, 0},  {9, 1, 0, false, false, 0},  {5, 1, 0, false, false, 0},
@@ -65,7 +66,10 @@ const FarRow kFarVariants[] = {{7, 2, 0, false, false, 0},  {5, 2, 0, false, fal
                                {5, 2, 8, true, false, 0, 2},  {3, 2, 10, true, false, 0, 2},
                                // one-row sinc ring with 4 and 2 compute warps (few spindowns: full blocks
                                // with narrow columns), in FS_RING_VARIANTS
-                               {5, 2, 4, true, false, 0, 0},  {5, 2, 2, true, false, 0, 0}};
+                               {5, 2, 4, true, false, 0, 0},  {5, 2, 2, true, false, 0, 0},
+                               // blocks of 4 sky points, in the order of FS_RING_SKY_VARIANTS
+                               {5, 2, 10, true, false, 0, 0, 4}, {5, 2, 10, false, false, 0, 0, 4},
+                               {5, 1, 8, true, false, 0, 0, 4},  {1, 1, 8, true, false, 0, 0, 4}};
 constexpr int kNumFar = sizeof(kFarVariants) / sizeof(kFarVariants[0]);
 constexpr int kFarIdBase = 100;   // variant ids reported for the far-field form
 
@@ -79,6 +83,7 @@ struct Plan {
     bool sinc = false;  // sinc-polynomial form (TMA ring only)
     bool rows = false;  // rows form of the sinc polynomial: M = 1 frequency per lane, R rows (kFarVariants)
     bool two = false;   // two-row tiles of the sinc ring form (L = 2)
+    int sky_rows = 1;   // sky points per block of the one-row ring (meta and bases SFT-major when > 1)
     size_t smem = 0;
     long long grid = 0;
 };
@@ -151,6 +156,7 @@ struct fstat_ctx {
     double* d_fdot = nullptr;
     std::vector<double> h_sky, h_fdot;
     bool fdot_uniform = true;         // spindowns fdot_0 + d * dfdot (compact bases)
+    bool batch_member = false;        // a workunit of a batch (kernels with a persistent form only)
     double dfdot = 0.0;
     // derived per-bank buffers
     size_t cap_meta = 0, cap_kh0 = 0, cap_ph0 = 0, cap_abcd = 0, cap_comb = 0, cap_twoF = 0;
@@ -265,6 +271,29 @@ int pairs_needed(const fstat_ctx* c, int span_templates, int D) {
     tau_max += 500.0;   // Roemer delay bound (AU + R_E)/c < 500 s
     const double spread = (fd_max - fd_min) * tau_max * c->T * tdot_max;
     return (int)std::ceil((span_templates - 1) * dk_max + spread) + 2 * D + 4;
+}
+
+// Bound, in bins, on how far apart the windows of `g` consecutive sky points
+// of the bank can start: khat = f T tdot with tdot - 1 = v.n / c, |v| / c <=
+// 1.1e-4 (orbit and rotation), so two sky points' khat differ by at most
+// f_max T 1.1e-4 |n_1 - n_2| (the Roemer delay's share, fdot T dtau, is below
+// 1e-3 bins); the maximum over all groups of g, plus one bin.
+double sky_spread_bins(const fstat_ctx* c, int g) {
+    const double k_max = (c->f0 + (c->n_f - 1) * c->df) * c->T;
+    double chord = 0.0;
+    for (int s0 = 0; s0 < c->n_sky; s0 += g) {
+        const int s1 = std::min(c->n_sky, s0 + g);
+        for (int a = s0; a < s1; ++a)
+            for (int b = a + 1; b < s1; ++b) {
+                const double aa = c->h_sky[2 * a], da = c->h_sky[2 * a + 1];
+                const double ab = c->h_sky[2 * b], db = c->h_sky[2 * b + 1];
+                const double dx = std::cos(da) * std::cos(aa) - std::cos(db) * std::cos(ab);
+                const double dy = std::cos(da) * std::sin(aa) - std::cos(db) * std::sin(ab);
+                const double dz = std::sin(da) - std::sin(db);
+                chord = std::max(chord, std::sqrt(dx * dx + dy * dy + dz * dz));
+            }
+    }
+    return k_max * 1.1e-4 * chord + 1.0;
 }
 
 // Weights of the far-field form: for each far offset k, the monomial
@@ -520,16 +549,22 @@ bool make_far_plan(fstat_ctx* c, int P, int L, bool found, Plan& best) {
     // AUTO takes the sinc-polynomial form where the ring applies (731 ms per
     // workunit launch on GB300 against 1106 ms for near pairs + far polynomial)
     const int tw = c->opts.tile_warps;
-    // A bank of one spindown row stages a table row per template and SFT: the
-    // ring is then bound by its copies, and AUTO takes the far-field form's
-    // 64-byte positions over the sinc form's 96 (measured on GB300, 2048 sky x
-    // 900 f x 1600 SFTs: 14.4 against 18.6 ms; with two rows they tie)
-    const bool auto_far = c->opts.algo == FSTAT_ALGO_AUTO && L == 2 && c->n_fdot == 1 && tw != 3 && tw != 5;
-    const bool want_sinc = !auto_far && (c->opts.algo == FSTAT_ALGO_SINCPOLY || c->opts.algo == FSTAT_ALGO_AUTO ||
-                                         c->opts.algo == FSTAT_ALGO_SINCROWS || c->opts.algo == FSTAT_ALGO_SINCPAIRS);
+    const bool sinc_ok = c->opts.algo == FSTAT_ALGO_SINCPOLY || c->opts.algo == FSTAT_ALGO_AUTO ||
+                         c->opts.algo == FSTAT_ALGO_SINCROWS || c->opts.algo == FSTAT_ALGO_SINCPAIRS;
+    // With few spindown rows a block's table row serves few templates, and the
+    // ring can be bound by its copies: AUTO then also weighs the far-field form
+    // (64-byte positions against the sinc form's 96) and blocks of 4 close sky
+    // points (one window for all four).  Measured on GB300, 2048 sky x 900 f x
+    // 1600 SFTs, one spindown, one sky point a block: sinc 18.6 ms, far field
+    // 14.4 ms; with two spindowns they tie.
+    const bool few_rows = c->n_fdot <= 2;
+    std::vector<bool> forms;
+    if (sinc_ok) forms.push_back(true);
+    if (!sinc_ok || (c->opts.algo == FSTAT_ALGO_AUTO && L == 2 && few_rows && tw != 3 && tw != 5))
+        forms.push_back(false);
     // L = 1 (P = 8) runs the ring in the sinc form only, with plain tables
-    const bool ring_l = L == 2 || (L == 1 && want_sinc && !c->have_cov);
-    if (found && ring_l && c->fdot_uniform && (tw == 0 || tw >= 9 || (want_sinc && L == 2 && (tw == 3 || tw == 5)))) {
+    const bool ring_l = L == 2 || (L == 1 && sinc_ok && !c->have_cov);
+    if (found && ring_l && c->fdot_uniform && (tw == 0 || tw >= 9 || (sinc_ok && L == 2 && (tw == 3 || tw == 5)))) {
         // M = 5 with 8 stages measured fastest on GB300 (1105 ms on the workunit; M = 7: 1139 ms).
         // For L = 1, M = 1 competes: narrow banks leave an M = 5 lane-group's lanes idle.
         std::vector<int> Mr = {5};
@@ -545,37 +580,54 @@ bool make_far_plan(fstat_ctx* c, int P, int L, bool found, Plan& best) {
         // on GB300 the 10-warp block was faster on every bank measured, by 20-60 %
         // on banks of 1-16 spindowns where the cost model favoured the small ones
         const std::vector<int> nwcs = {nwc0};
+        // blocks of 4 consecutive sky points where their windows lie within 24 bins
+        // (the window widens by that much; the cost model weighs it)
+        std::vector<int> SRs = {1};
+        double spread4 = 0.0;
+        if (few_rows && !c->have_cov && !c->batch_member && c->n_sky >= 8) {
+            spread4 = sky_spread_bins(c, 4);
+            if (spread4 <= 24.0) SRs.push_back(4);
+        }
+        // one spindown and one sky point a block: the far-field form (measured; the
+        // compute model overrates the idle warps of its wide blocks)
+        const bool one_row_far = forms.size() > 1 && c->n_fdot == 1;
+        for (const bool sinc : forms)
+        for (const int SR : SRs)
         for (int M_ : Mr)
         for (int nwc : nwcs) {
             if (nwc % P != 0) continue;
+            if (sinc && SR == 1 && one_row_far) continue;
             int fid = -1;
             for (int i = 0; i < kNumFar; ++i)
                 if (kFarVariants[i].ring == nwc && kFarVariants[i].M == M_ && kFarVariants[i].L == L &&
-                    kFarVariants[i].sinc == want_sinc && kFarVariants[i].cov == c->have_cov && !kFarVariants[i].rows &&
-                    !kFarVariants[i].minb)
+                    kFarVariants[i].sinc == sinc && kFarVariants[i].cov == c->have_cov && !kFarVariants[i].rows &&
+                    !kFarVariants[i].minb && std::max(1, kFarVariants[i].sr) == SR)
                     fid = i;
             if (fid < 0) continue;
             const int PM = P * M_;
             const int lg_cta = 32 * nwc / P;
             const int lg_max = std::min((c->n_f + PM - 1) / PM, lg_cta);
+            const int rows = SR * c->n_fdot;   // rows of a block: (sky point, spindown)
             for (int lg_row = 1; lg_row <= lg_max; ++lg_row) {
-                // a quarter-warp (8 lane-groups) must not straddle two spindown rows:
+                // a quarter-warp (8 lane-groups) must not straddle two rows:
                 // its lanes' records then sit 5 positions apart and read conflict-free
                 // (a straddling layout measured 23 % slower on the workunit)
-                if (c->n_fdot > 1 && lg_row % 8 != 0 && lg_row < lg_max) continue;
+                if (rows > 1 && lg_row % 8 != 0 && lg_row < lg_max) continue;
                 const int col_w = lg_row * PM;
                 const int n_col = (c->n_f + col_w - 1) / col_w;
-                const int w_pairs = std::max(pairs_needed(c, col_w, 8), (M_ - 1) * L + 2 * 8 + 2);
+                const int w_pairs = std::max(pairs_needed(c, col_w, 8) + (SR > 1 ? (int)std::ceil(spread4) : 0),
+                                             (M_ - 1) * L + 2 * 8 + 2);
                 int hf = (w_pairs + 1) / 2;
                 hf += ((4 - hf % 8) + 8) % 8;
                 const int w_tab = L == 2 ? 2 * hf : w_pairs;
-                // live warps of every block (a block's idle warps still hold its place on the SM)
+                // live warps of every block (a block's idle warps still hold its place on
+                // the SM), for one block row of SR sky points
                 double live = 0.0, blocks = 0.0;
                 int chunks_max = 0;
                 for (int col = 0; col < n_col; ++col) {
                     const int width = std::min(col_w, c->n_f - col * col_w);
                     const int Gc = (width + PM - 1) / PM;
-                    const long long LG = (long long)c->n_fdot * Gc;
+                    const long long LG = (long long)rows * Gc;
                     const int chunks = (int)((LG + lg_cta - 1) / lg_cta);
                     chunks_max = std::max(chunks_max, chunks);
                     for (int k = 0; k < chunks; ++k) {
@@ -587,23 +639,29 @@ bool make_far_plan(fstat_ctx* c, int P, int L, bool found, Plan& best) {
                 const int S_hi = c->opts.sft_chunk > 0 ? c->opts.sft_chunk : 8;
                 const int S_lo = c->opts.sft_chunk > 0 ? c->opts.sft_chunk : 3;
                 for (int S = S_hi; S >= S_lo; --S) {
-                    const size_t smem = ring_smem(S, w_tab, want_sinc).total;
+                    const size_t smem = ring_smem(S, w_tab, sinc, SR).total;
                     if (smem > 220 * 1024) continue;
-                    // Time ~ work / concurrency: the kernel saturates its SM (shared-memory
-                    // loads) at about 20 live compute warps; fewer resident live warps
-                    // (blocks per SM limited by shared memory, threads or ~80 registers
-                    // a thread) leave it latency-bound.  Per live warp and SFT ~40
-                    // instructions of set-up and ~50 per template; staging ~0.05 per
-                    // staged byte; fewer stages leave less slack between warps.
+                    // Compute ~ work / concurrency: the kernel saturates its SM at
+                    // about 20 live compute warps; fewer resident live warps (blocks
+                    // per SM limited by shared memory, threads or ~80 registers a
+                    // thread) leave it latency-bound.  Per live warp and SFT ~40
+                    // instructions of set-up and ~50 per template; fewer stages
+                    // leave less slack between warps; the far-field form takes 1.5x
+                    // the sinc form's time per template (1106 against 731 ms on the
+                    // workunit).  Staging: the table rows copied per SFT at ~17.7 TB/s
+                    // (L2 to shared memory, measured with one spindown).  The time
+                    // is the larger of the two, in ms per sky point and SFT (compute
+                    // calibrated on the workunit: 731 ms for 10 000 x 2400).
                     const int threads = 32 * (nwc + 1);
                     int resident = (int)((227 * 1024) / (smem + 1024));
                     resident = std::min(resident, 2048 / threads);
                     resident = std::min(resident, 65536 / (80 * threads));
                     if (resident < 1) continue;
                     const double conc = std::min(20.0, resident * live / blocks);
-                    const double work = live * 32.0 * (40.0 + 50.0 * M_) * (1.0 + 0.2 / S) +
-                                        blocks * 0.05 * w_pairs * (want_sinc ? 96.0 : 64.0);
-                    const double cost = work / conc;
+                    const double work = live * 32.0 * (40.0 + 50.0 * M_) * (1.0 + 0.2 / S);
+                    const double t_comp = work / conc * 5.26e-10 * (sinc ? 1.0 : 1.5) / SR;
+                    const double t_copy = blocks * w_pairs * (sinc ? 96.0 : 64.0) / 17.7e9 / SR;
+                    const double cost = std::max(t_comp, t_copy);
                     if (cost < best_r * 0.999) {
                         best_r = cost;
                         best = Plan{};
@@ -621,9 +679,10 @@ bool make_far_plan(fstat_ctx* c, int P, int L, bool found, Plan& best) {
                         best.variant = fid;
                         best.far = true;
                         best.ring = true;
-                        best.sinc = want_sinc;
+                        best.sinc = sinc;
+                        best.sky_rows = SR;
                         best.smem = smem;
-                        best.grid = (long long)c->n_sky * n_col * chunks_max;
+                        best.grid = (long long)((c->n_sky + SR - 1) / SR) * n_col * chunks_max;
                         have_ring = true;
                     }
                 }
@@ -1348,6 +1407,7 @@ TimingParams timing_params(const fstat_ctx* c, int n_sky) {
     tp.dfdot = c->dfdot;
     tp.meta = c->d_meta;
     tp.base = c->fdot_uniform ? c->d_base : nullptr;
+    tp.sft_major = c->plan.sky_rows > 1 ? 1 : 0;   // blocks of several sky points read them SFT-major
     tp.kh0 = c->fdot_uniform ? nullptr : c->d_kh0;
     tp.ph0 = c->fdot_uniform ? nullptr : c->d_ph0;
     tp.abcd = c->d_abcd;
@@ -1722,7 +1782,8 @@ int fstat_autotune(fstat_ctx* c, void* cuda_stream, int32_t* out) {
             if (launch_timing(timing_params(c, n_sky_sub), s) != cudaSuccess) continue;
             DirichletParams dp = dirichlet_params(c);
             dp.n_sky = n_sky_sub;   // the far-field form orders blocks sky-fastest
-            const long long grid = (long long)n_sky_sub * per_sky;
+            const int sr = c->plan.sky_rows;
+            const long long grid = (long long)((n_sky_sub + sr - 1) / sr) * per_sky;
             float t = 1e30f;
             for (int rep = 0; rep < 3; ++rep) {
                 cudaEventRecord(e0, s);
@@ -1768,6 +1829,7 @@ int fstat_batch_add(fstat_ctx* c, const fstat_workunit* wu, int32_t* wu_id) {
     fstat_ctx* w = nullptr;
     int rc = fstat_create(&w, c->device, &c->opts);
     if (rc != FSTAT_OK) return fail(c, rc, "workunit context creation failed");
+    w->batch_member = true;
     for (int d = 0; d < wu->n_det; ++d) {
         rc = fstat_set_sfts(w, d, &wu->det[d], wu->Tsft, wu->k_lo, wu->n_bins, wu->n_sft[d], wu->t_start[d],
                             wu->bins[d], FSTAT_MEM_HOST);

@@ -544,9 +544,13 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
 // stage to be free, writes its window base and coverage, and copies its
 // constants and table rows into the stage with bulk copies under the stage's
 // full barrier.  Returns (lane 0) the number of stages issued.
-template <bool SINC, bool COV, int L>
+// SR > 1: the block holds n_in <= SR consecutive sky points starting at sky
+// meta0 (meta and bases SFT-major, one copy of each for all of them); the
+// window base is the lowest of theirs.
+template <bool SINC, bool COV, int L, int SR = 1>
 __device__ __forceinline__ int ring_produce(const DirichletParams& p, const RingSmem& lay, int S, unsigned char* smem,
-                                            uint32_t sb, volatile int* ctrl, size_t meta0, int j_col0, int lane) {
+                                            uint32_t sb, volatile int* ctrl, size_t meta0, int j_col0, int lane,
+                                            int n_in = 1) {
     constexpr int D = 8;
     auto full_bar = [&](int s) { return sb + (uint32_t)(lay.bars + 16 * (size_t)s); };
     auto empty_bar = [&](int s) { return sb + (uint32_t)(lay.bars + 16 * (size_t)s + 8); };
@@ -556,7 +560,7 @@ __device__ __forceinline__ int ring_produce(const DirichletParams& p, const Ring
     const int half = p.w_tab >> 1;
     const int n0 = (p.w_pairs + 1) >> 1, n1 = p.w_pairs >> 1;
     // per position 16 + 48 bytes (far field) or 2 x 48 bytes (sinc)
-    const uint32_t bytes = 48u + 32u + (uint32_t)(n0 + n1) * (SINC ? 96u : 64u);
+    const uint32_t bytes = 80u * (uint32_t)n_in + (uint32_t)(n0 + n1) * (SINC ? 96u : 64u);
     int a = 0;
     bool stop = false;
     int pslot = 0;            // slot of SFT a
@@ -567,8 +571,15 @@ __device__ __forceinline__ int ring_produce(const DirichletParams& p, const Ring
         int2 cv_lane = make_int2(0, 0x7fffffff);
         if (COV && a0 + lane < p.n_sft) cv_lane = p.cov[a0 + lane];
         if (a0 + lane < p.n_sft) {
-            const SkySftMeta* gm = p.meta + meta0 + a0 + lane;
-            x_lane = (int)(((gm->khmin + (long long)j_col0 * gm->dk) >> 32) - p.k_lo) - (D - 1) + p.xoff;
+            if (SR == 1) {
+                const SkySftMeta* gm = p.meta + meta0 + a0 + lane;
+                x_lane = (int)(((gm->khmin + (long long)j_col0 * gm->dk) >> 32) - p.k_lo) - (D - 1) + p.xoff;
+            } else {
+                const SkySftMeta* gm = p.meta + (size_t)(a0 + lane) * p.n_sky + meta0;
+                long long kmin = gm->khmin + (long long)j_col0 * gm->dk;
+                for (int q = 1; q < n_in; ++q) kmin = min(kmin, gm[q].khmin + (long long)j_col0 * gm[q].dk);
+                x_lane = (int)((kmin >> 32) - p.k_lo) - (D - 1) + p.xoff;
+            }
         }
         const int n_here = min(32, n_issue - a0);
         for (int j = 0; j < n_here; ++j) {
@@ -593,8 +604,13 @@ __device__ __forceinline__ int ring_produce(const DirichletParams& p, const Ring
                     const uint32_t ss = sb + (uint32_t)((size_t)pslot * lay.stage);
                     const uint32_t fb = full_bar(pslot);
                     mbar_expect_tx(fb, bytes);
-                    bulk_g2s(ss + (uint32_t)lay.meta, p.meta + meta0 + a, 48, fb);
-                    bulk_g2s(ss + (uint32_t)lay.base, p.base + meta0 + a, 32, fb);
+                    if (SR == 1) {
+                        bulk_g2s(ss + (uint32_t)lay.meta, p.meta + meta0 + a, 48, fb);
+                        bulk_g2s(ss + (uint32_t)lay.base, p.base + meta0 + a, 32, fb);
+                    } else {
+                        bulk_g2s(ss + (uint32_t)lay.meta, p.meta + (size_t)a * p.n_sky + meta0, 48u * n_in, fb);
+                        bulk_g2s(ss + (uint32_t)lay.base, p.base + (size_t)a * p.n_sky + meta0, 32u * n_in, fb);
+                    }
                     if (L == 1) {   // plain tables: one run of w_pairs positions per plane
 #pragma unroll
                         for (int hb = 0; hb < 2; ++hb)
@@ -637,25 +653,31 @@ __device__ __forceinline__ int ring_produce(const DirichletParams& p, const Ring
 // Uniform spindown grid; L = 2 (tables split by position parity, two runs
 // per table and SFT) or L = 1 (sinc form only: plain tables, one run).
 // Warps 0..NW-1 compute, warp NW produces.
+// SR > 1: a block holds SR consecutive sky points (the last block of a column
+// fewer); its rows are (sky point, spindown), sky-major, and its window
+// covers all of them (close sky points: their windows differ by a few bins).
 // Error flag bit 2: a pipeline wait gave up (results of the block invalid).
-template <int M, bool SINC, bool COV, int L>
+template <int M, bool SINC, bool COV, int L, int SR = 1>
 __device__ __forceinline__ void far_ring_block(const DirichletParams& p, long long bid, unsigned char* smem) {
     static_assert(L == 2 || (L == 1 && SINC), "the L = 1 ring is built for the sinc tables");
+    static_assert(SR == 1 || !COV, "blocks of several sky points have no coverage path");
     constexpr int D = 8;
     const int S = p.sft_chunk;
-    const RingSmem lay = ring_smem(S, p.w_tab, SINC);
+    const RingSmem lay = ring_smem(S, p.w_tab, SINC, SR);
     const int NW = (int)(blockDim.x >> 5) - 1;
 
     const int chunk = (int)(bid % p.chunks_per_col);
     bid /= p.chunks_per_col;
-    const int sky = (int)(bid % p.n_sky);
-    const int col = (int)(bid / p.n_sky);
+    const int n_grp = SR == 1 ? p.n_sky : (p.n_sky + SR - 1) / SR;
+    const int sky0 = (int)(bid % n_grp) * SR;
+    const int col = (int)(bid / n_grp);
+    const int n_in = SR == 1 ? 1 : min(SR, p.n_sky - sky0);
     const int PM = p.P * M;
     const int col_w = p.lg_row * PM;
     const int j_col0 = col * col_w;
     const int width = min(col_w, p.n_f - j_col0);
     const int Gc = (width + PM - 1) / PM;
-    const int LG = p.n_fdot * Gc;
+    const int LG = n_in * p.n_fdot * Gc;
     const int u0 = chunk * p.lg_cta;
     if (u0 >= LG) return;   // block-uniform, before any barrier exists
     const int u_end = min(u0 + p.lg_cta, LG);
@@ -667,8 +689,11 @@ __device__ __forceinline__ void far_ring_block(const DirichletParams& p, long lo
     const int u = u0 + ul;
     const bool active = !producer && (ul < p.lg_cta) && (u < u_end);
     const int uu = active ? u : u0;
-    const int drow = uu / Gc;
-    const int g = uu - drow * Gc;
+    const int row = uu / Gc;
+    const int g = uu - row * Gc;
+    const int sky_l = SR == 1 ? 0 : row / p.n_fdot;   // sky point of the block
+    const int drow = SR == 1 ? row : row - sky_l * p.n_fdot;
+    const int sky = sky0 + sky_l;
     const int j_t = j_col0 + g * PM + r;
     const bool warp_live = __any_sync(0xffffffffu, active);
 
@@ -687,9 +712,9 @@ __device__ __forceinline__ void far_ring_block(const DirichletParams& p, long lo
     }
     __syncthreads();
 
-    const size_t meta0 = (size_t)sky * p.n_sft;
+    const size_t meta0 = SR == 1 ? (size_t)sky0 * p.n_sft : (size_t)sky0;
     if (producer) {
-        const int issued = ring_produce<SINC, COV, L>(p, lay, S, smem, sb, ctrl, meta0, j_col0, lane);
+        const int issued = ring_produce<SINC, COV, L, SR>(p, lay, S, smem, sb, ctrl, meta0, j_col0, lane, n_in);
         if (lane == 0) ctrl[0] = issued;   // stages issued
     } else {
         float2 fa[M], fb[M];
@@ -713,8 +738,8 @@ __device__ __forceinline__ void far_ring_block(const DirichletParams& p, long lo
                                      : make_int4(*reinterpret_cast<const int*>(st + lay.lo), 0, 0, 0x7fffffff);
                 // skip an SFT whose coverage holds none of the thread's templates
                 if (!COV || (j_t + (M - 1) * p.P >= lo4.z && j_t < lo4.w)) {
-                    const SkySftMeta m = *reinterpret_cast<const SkySftMeta*>(st + lay.meta);
-                    const SkySftBase bs = *reinterpret_cast<const SkySftBase*>(st + lay.base);
+                    const SkySftMeta m = *reinterpret_cast<const SkySftMeta*>(st + lay.meta + 48 * sky_l);
+                    const SkySftBase bs = *reinterpret_cast<const SkySftBase*>(st + lay.base + 32 * sky_l);
                     if (SINC)
                         sinc_sft<M, L, COV>(p, m, bs.kh0 + (long long)drow * bs.dkh,
                                             bs.ph0 + (unsigned int)drow * bs.dph, lo4.x,
@@ -754,11 +779,12 @@ __device__ __forceinline__ void far_ring_block(const DirichletParams& p, long lo
     }
 }
 
-// NWC compute warps plus the producer; two resident blocks per SM.
-template <int M, int NWC, bool SINC, bool COV, int L>
+// NWC compute warps plus the producer; two resident blocks per SM; SR sky
+// points per block.
+template <int M, int NWC, bool SINC, bool COV, int L, int SR = 1>
 __global__ void __launch_bounds__(32 * (NWC + 1), 2) dirichlet_far_ring_kernel(const DirichletParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
-    far_ring_block<M, SINC, COV, L>(p, (long long)blockIdx.x, smem);
+    far_ring_block<M, SINC, COV, L, SR>(p, (long long)blockIdx.x, smem);
 }
 
 // Rows form of the sinc polynomial (uniform spindown grid, plain tables).
@@ -1229,6 +1255,12 @@ __global__ void __launch_bounds__(32 * (NWC + 1), 2)
 #define FS_RING_COV_VARIANTS(X) \
     X(16, 5, 10, true)          \
     X(17, 5, 10, false)
+// blocks of 4 sky points (single launches only): (ID, M, NWC, sinc, L)
+#define FS_RING_SKY_VARIANTS(X) \
+    X(31, 5, 10, true, 2)       \
+    X(32, 5, 10, false, 2)      \
+    X(33, 5, 8, true, 1)        \
+    X(34, 1, 8, true, 1)
 // sinc form for L = 1 banks (P = 8 threads per lane-group; single launches only)
 #define FS_RING_L1_VARIANTS(X) \
     X(18, 5, 8, true)          \
@@ -1260,9 +1292,9 @@ cudaError_t launch_dirichlet_far(int v, const DirichletParams& p, int threads, s
     }
         FS_FAR_VARIANTS(FS_FCASE)
 #undef FS_FCASE
-#define FS_RCASE(ID, M_, W_, S_, C_, L_)                                                                  \
+#define FS_RCASE(ID, M_, W_, S_, C_, L_, ...)                                                             \
     case ID: {                                                                                            \
-        auto fn = dirichlet_far_ring_kernel<M_, W_, S_, C_, L_>;                                          \
+        auto fn = dirichlet_far_ring_kernel<M_, W_, S_, C_, L_, ##__VA_ARGS__>;                           \
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
         if (e != cudaSuccess) return e;                                                                   \
         fn<<<(unsigned)grid, threads, smem, s>>>(p);                                                      \
@@ -1271,9 +1303,11 @@ cudaError_t launch_dirichlet_far(int v, const DirichletParams& p, int threads, s
 #define FS_RCASE_PLAIN(ID, M_, W_, S_) FS_RCASE(ID, M_, W_, S_, false, 2)
 #define FS_RCASE_COV(ID, M_, W_, S_) FS_RCASE(ID, M_, W_, S_, true, 2)
 #define FS_RCASE_L1(ID, M_, W_, S_) FS_RCASE(ID, M_, W_, S_, false, 1)
+#define FS_RCASE_SKY(ID, M_, W_, S_, L_) FS_RCASE(ID, M_, W_, S_, false, L_, 4)
         FS_RING_VARIANTS(FS_RCASE_PLAIN)
         FS_RING_COV_VARIANTS(FS_RCASE_COV)
         FS_RING_L1_VARIANTS(FS_RCASE_L1)
+        FS_RING_SKY_VARIANTS(FS_RCASE_SKY)
 #define FS_ROWCASE(ID, R_, W_)                                                                            \
     case ID: {                                                                                            \
         auto fn = dirichlet_rows_kernel<R_, W_>;                                                          \
@@ -1294,6 +1328,7 @@ cudaError_t launch_dirichlet_far(int v, const DirichletParams& p, int threads, s
     }
         FS_RING2_VARIANTS(FS_R2CASE)
 #undef FS_R2CASE
+#undef FS_RCASE_SKY
 #undef FS_RCASE_L1
 #undef FS_RCASE_COV
 #undef FS_RCASE_PLAIN

@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(kTimingBlock) timing_kernel(const TimingParams
             sincos((double)(int)bs.dph / kTwo32 * kTwoPi, &rs, &rc);
             bs.rot_re = (float)rc;
             bs.rot_im = (float)(-rs);
-            p.base[(size_t)sky * p.n_sft + i] = bs;
+            p.base[p.sft_major ? (size_t)i * p.n_sky + sky : (size_t)sky * p.n_sft + i] = bs;
             const long long last = bs.kh0 + (long long)(p.n_fdot - 1) * bs.dkh;
             khmin = bs.kh0 < last ? bs.kh0 : last;
         } else {
@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(kTimingBlock) timing_kernel(const TimingParams
             }
         }
         m.khmin = khmin;
-        p.meta[(size_t)sky * p.n_sft + i] = m;
+        p.meta[p.sft_major ? (size_t)i * p.n_sky + sky : (size_t)sky * p.n_sft + i] = m;
     }
     const double A = block_sum<kTimingBlock>(sAA, red[0]);
     const double B = block_sum<kTimingBlock>(sBB, red[1]);

@@ -168,7 +168,8 @@ __host__ __device__ inline PolySmem farpoly_smem(int sft_chunk, int w_tab, int n
 // Shared-memory layout of the ring kernel: S stages of
 // [pairs w_tab x 16 B][coefficient records w_tab x 48 B] (far field) or
 // [half-bin plane 0][half-bin plane 1] (sinc), then [meta 48 B][base 32 B]
-// [window base 16 B] (128-byte aligned), then a full and an empty mbarrier
+// (one of each per sky point of the block) [window base 16 B] (128-byte
+// aligned), then a full and an empty mbarrier
 // per stage, then two control words (stages issued, abort).
 struct RingSmem {
     size_t stage, pairs, coef, plane, meta, base, lo, bars, ctrl, total;
@@ -177,14 +178,14 @@ struct RingSmem {
 // per position; the sinc form two 48-byte records (one per half bin) in two
 // planes whose distance is a multiple of 128 bytes, so that the half a
 // template picks does not change its shared-memory bank.
-__host__ __device__ inline RingSmem ring_smem(int stages, int w_tab, bool sinc = false) {
+__host__ __device__ inline RingSmem ring_smem(int stages, int w_tab, bool sinc = false, int sky_rows = 1) {
     RingSmem r;
     r.pairs = 0;
     r.plane = ((size_t)w_tab * 48 + 127) & ~(size_t)127;
     r.coef = sinc ? 0 : (size_t)w_tab * 16;
     r.meta = sinc ? 2 * r.plane : r.coef + (size_t)w_tab * 48;
-    r.base = r.meta + 48;
-    r.lo = r.base + 32;
+    r.base = r.meta + 48 * (size_t)sky_rows;   // one meta and one base per sky point of the block
+    r.lo = r.base + 32 * (size_t)sky_rows;
     r.stage = (r.lo + 16 + 127) & ~(size_t)127;
     r.bars = (size_t)stages * r.stage;
     r.ctrl = r.bars + 16 * (size_t)stages;
@@ -213,8 +214,9 @@ struct TimingParams {
     int P, L, M;
     int uniform;               // spindowns fdot_0 + d * dfdot: write `base`, else kh0 / ph0
     double dfdot;
-    SkySftMeta* meta;          // out [n_sky][n_sft]
-    SkySftBase* base;          // out [n_sky][n_sft] (uniform)
+    SkySftMeta* meta;          // out [n_sky][n_sft], or [n_sft][n_sky] when sft_major
+    SkySftBase* base;          // out [n_sky][n_sft] (uniform), or [n_sft][n_sky] when sft_major
+    int sft_major;             // SFT-major meta and bases (blocks of several sky points)
     long long* kh0;            // out [n_sky][n_fdot][n_sft] (not uniform)
     unsigned int* ph0;         // out [n_sky][n_fdot][n_sft] (not uniform)
     double* abcd;              // out [n_sky][4]

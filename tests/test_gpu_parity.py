@@ -4,6 +4,7 @@ Tolerance of the FP32 path: |d2F| <= 1e-4 * 2F + 1e-3, element by element.
 Inputs are the seeded workloads of `workload`; signals are added by the
 oracle (never by the GPU) before both sides compute.
 """
+import dataclasses
 import math
 
 import numpy as np
@@ -165,17 +166,17 @@ def test_row_tiled_forms_on_ragged_row_counts(lib, algo, ids, n_fdot, df_bins):
 @pytest.mark.parametrize("n_fdot", [1, 2, 3])
 def test_small_block_rings_on_few_spindowns(lib, tile_warps, variant, n_fdot):
     """The one-row sinc ring with 2 and 4 compute warps (tile_warps = 3 / 5)
-    and the planner's own choice (the 10-warp sinc ring; the far-field ring
-    for one spindown): parity and the toplist on a wide band with a ragged
-    last column."""
+    and the planner's own choice (the 10-warp sinc ring; for one or two
+    spindowns possibly the far-field ring): parity and the toplist on a wide
+    band with a ragged last column."""
     w = config_mid(n_f=410, n_fdot=n_fdot, n_sky=3, n_bins=520)
     bins = _oracle_bins(w)
     ref = O.compute_fstat_freq_band(_dets(w, bins), w.T, w.k_lo, w.dterms, w.bank).ravel()
     out = _gpu(lib, w, bins, tile_warps=tile_warps)
     if variant is not None:
         assert out["plan"]["variant"] == variant
-    else:
-        assert out["plan"]["variant"] == (110 if n_fdot == 1 else 112)
+    else:   # one or two spindowns: the sinc or the far-field ring by the planner's copy model
+        assert out["plan"]["variant"] in ((110, 112) if n_fdot <= 2 else (112,))
     assert out["flags"] == 0
     _assert_parity(out["twoF"], ref, f"tile_warps={tile_warps} n_fdot={n_fdot}")
     _check_toplist(out["top"], out["twoF"], ref, w.topk)
@@ -429,3 +430,39 @@ def test_size_limits_are_errors_not_allocations(lib):
         assert g.error_flags() == 0
     finally:
         g.close()
+
+
+def _close_sky(w, n_a, n_d, step):
+    """The bank's sky replaced by a small regular grid around its first
+    point (the signal's), delta fastest: consecutive points are neighbours,
+    as in the learned proposal's maps."""
+    a0, d0 = w.bank.sky[0]
+    a = a0 + step * (np.arange(n_a) - n_a // 2)
+    d = d0 + step * (np.arange(n_d) - n_d // 2)
+    A, Dd = np.meshgrid(a, d, indexing="ij")
+    sky = np.stack([A.ravel(), Dd.ravel()], axis=1)
+    return dataclasses.replace(w, bank=dataclasses.replace(w.bank, sky=sky))
+
+
+@pytest.mark.parametrize("n_fdot,df_bins,ids", [(1, 1.0, (131, 132)), (2, 1.0, (131, 132)),
+                                                 (1, 0.125, (133, 134))])
+def test_blocks_of_four_sky_points(lib, n_fdot, df_bins, ids):
+    """The one-row ring with blocks of 4 consecutive sky points (one window for
+    the four, meta and bases SFT-major), chosen by the planner for a bank of
+    few spindowns on a grid of close sky points (18 points: a ragged last
+    block of 2): parity, the toplist, and bit-identical 2F against the
+    one-sky-point block of the same form where one exists (8 compute warps)."""
+    n_f = 210 if df_bins == 1.0 else 256
+    w = _close_sky(config_mid(n_f=n_f, n_fdot=n_fdot, n_sky=3, df_bins=df_bins, n_bins=300), 3, 6, 0.01)
+    bins = _oracle_bins(w)
+    ref = O.compute_fstat_freq_band(_dets(w, bins), w.T, w.k_lo, w.dterms, w.bank).ravel()
+    out = _gpu(lib, w, bins)
+    assert out["plan"]["variant"] in ids, out["plan"]
+    assert out["flags"] == 0
+    _assert_parity(out["twoF"], ref, f"sky blocks n_fdot={n_fdot} df={df_bins}")
+    _check_toplist(out["top"], out["twoF"], ref, w.topk)
+    if df_bins == 1.0:
+        algo = "sincpoly" if out["plan"]["variant"] == 131 else "farpoly"
+        one = _gpu(lib, w, bins, tile_warps=9, algo=algo)
+        assert one["plan"]["variant"] in (114, 107), one["plan"]
+        np.testing.assert_array_equal(out["twoF"], one["twoF"])
