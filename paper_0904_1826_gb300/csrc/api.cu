@@ -1408,6 +1408,7 @@ TimingParams timing_params(const fstat_ctx* c, int n_sky) {
     tp.meta = c->d_meta;
     tp.base = c->fdot_uniform ? c->d_base : nullptr;
     tp.sft_major = c->plan.sky_rows > 1 ? 1 : 0;   // blocks of several sky points read them SFT-major
+    tp.row_rot = (c->plan.rows || c->plan.two) ? 1 : 0;   // the row-tiled forms step the twiddle across rows
     tp.kh0 = c->fdot_uniform ? nullptr : c->d_kh0;
     tp.ph0 = c->fdot_uniform ? nullptr : c->d_ph0;
     tp.abcd = c->d_abcd;

@@ -167,13 +167,16 @@ __global__ void __launch_bounds__(kTimingBlock) timing_kernel(const TimingParams
         const unsigned int dphi = frac_fx32(p.df * dtau);
         m.dphi = dphi;
         m.eps = (float)((double)(pdk - ((long long)p.L << 32)) / kTwo32);
-        // twiddle step e^{-2 pi i (P dphi + L/2)} from the same fixed-point step
+        // twiddle step e^{-2 pi i (P dphi + L/2)} from the same fixed-point step:
+        // a reduced angle (the step in [-1/2, 1/2) cycle) whose sine and cosine
+        // are stored in FP32, so they are taken in FP32 (error ~2e-7 rad from
+        // rounding the 32-bit step to 24 bits; the kernels' own twiddles are
+        // FP32 too)
         const unsigned int step = (unsigned int)p.P * dphi + ((unsigned int)p.L << 31);
-        const double ang = (double)(int)step / kTwo32 * kTwoPi;
-        double sn, cs;
-        sincos(ang, &sn, &cs);
-        m.rot_re = (float)cs;
-        m.rot_im = (float)(-sn);
+        float sn, cs;
+        sincospif((float)(int)step * 4.656612873077393e-10f, &sn, &cs);   // x 2^-31: half cycles
+        m.rot_re = cs;
+        m.rot_im = -sn;
         const double sc = (double)p.scale[i] * kconst;
         m.a = (float)(a * sc);
         m.b = (float)(b * sc);
@@ -186,10 +189,11 @@ __global__ void __launch_bounds__(kTimingBlock) timing_kernel(const TimingParams
             bs.ph0 = frac_fx32(p.f0 * dtau + 0.5 * fd * dtau * dtau);
             bs.dph = frac_fx32(0.5 * p.dfdot * dtau * dtau);
             // twiddle step from one spindown row to the next, e^{-2 pi i dph}
-            double rs, rc;
-            sincos((double)(int)bs.dph / kTwo32 * kTwoPi, &rs, &rc);
-            bs.rot_re = (float)rc;
-            bs.rot_im = (float)(-rs);
+            // (read by the row-tiled forms only)
+            float rs = 0.f, rc = 1.f;
+            if (p.row_rot) sincospif((float)(int)bs.dph * 4.656612873077393e-10f, &rs, &rc);
+            bs.rot_re = rc;
+            bs.rot_im = -rs;
             p.base[p.sft_major ? (size_t)i * p.n_sky + sky : (size_t)sky * p.n_sft + i] = bs;
             const long long last = bs.kh0 + (long long)(p.n_fdot - 1) * bs.dkh;
             khmin = bs.kh0 < last ? bs.kh0 : last;

@@ -217,6 +217,7 @@ struct TimingParams {
     SkySftMeta* meta;          // out [n_sky][n_sft], or [n_sft][n_sky] when sft_major
     SkySftBase* base;          // out [n_sky][n_sft] (uniform), or [n_sft][n_sky] when sft_major
     int sft_major;             // SFT-major meta and bases (blocks of several sky points)
+    int row_rot;               // write the bases' row twiddle step (row-tiled forms)
     long long* kh0;            // out [n_sky][n_fdot][n_sft] (not uniform)
     unsigned int* ph0;         // out [n_sky][n_fdot][n_sft] (not uniform)
     double* abcd;              // out [n_sky][4]
