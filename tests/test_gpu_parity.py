@@ -444,9 +444,12 @@ def _close_sky(w, n_a, n_d, step):
     return dataclasses.replace(w, bank=dataclasses.replace(w.bank, sky=sky))
 
 
-@pytest.mark.parametrize("n_fdot,df_bins,ids,tile_m", [(1, 1.0, (131, 132), 0), (2, 1.0, (131, 132), 0),
-                                                        (1, 0.125, (133, 134), 0), (1, 0.125, (134,), 1)])
-def test_blocks_of_four_sky_points(lib, n_fdot, df_bins, ids, tile_m):
+@pytest.mark.parametrize("n_fdot,df_bins,ids,tile_m,algo", [(1, 1.0, (131, 132), 0, "auto"),
+                                                             (2, 1.0, (131, 132), 0, "auto"),
+                                                             (1, 1.0, (132,), 0, "farpoly"),
+                                                             (1, 0.125, (133, 134), 0, "auto"),
+                                                             (1, 0.125, (134,), 1, "auto")])
+def test_blocks_of_four_sky_points(lib, n_fdot, df_bins, ids, tile_m, algo):
     """The one-row ring with blocks of 4 consecutive sky points (one window for
     the four, meta and bases SFT-major), chosen by the planner for a bank of
     few spindowns on a grid of close sky points (18 points: a ragged last
@@ -456,7 +459,7 @@ def test_blocks_of_four_sky_points(lib, n_fdot, df_bins, ids, tile_m):
     w = _close_sky(config_mid(n_f=n_f, n_fdot=n_fdot, n_sky=3, df_bins=df_bins, n_bins=300), 3, 6, 0.01)
     bins = _oracle_bins(w)
     ref = O.compute_fstat_freq_band(_dets(w, bins), w.T, w.k_lo, w.dterms, w.bank).ravel()
-    out = _gpu(lib, w, bins, tile_m=tile_m)
+    out = _gpu(lib, w, bins, tile_m=tile_m, algo=algo)
     assert out["plan"]["variant"] in ids, out["plan"]
     assert out["flags"] == 0
     _assert_parity(out["twoF"], ref, f"sky blocks n_fdot={n_fdot} df={df_bins}")
