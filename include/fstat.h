@@ -112,10 +112,12 @@ typedef struct {
  *   and are slower than SINCPOLY on the workunit-sized bank; they are kept as
  *   options.  Batched workunits use the TMA-ring form where it applies, else
  *   DIRECT.
- * AUTO: SINCPOLY where the TMA ring applies, except on a bank of one
- *   spindown with L = 2, where the ring is bound by its table copies and
- *   FARPOLY's smaller records are faster; else FARPOLY where it applies,
- *   else DIRECT. */
+ * AUTO: the TMA ring where it applies: SINCPOLY, or on banks of one or two
+ *   spindowns with L = 2 (where the ring can be bound by its table copies)
+ *   whichever of SINCPOLY and FARPOLY's smaller records the planner's model
+ *   finds faster; banks of one or two spindowns whose consecutive sky points
+ *   are neighbours run blocks of 4 sky points sharing one staged window;
+ *   else FARPOLY where it applies, else DIRECT. */
 typedef enum {
     FSTAT_ALGO_AUTO = 0,
     FSTAT_ALGO_DIRECT = 1,
