@@ -84,6 +84,7 @@ struct Plan {
     bool rows = false;  // rows form of the sinc polynomial: M = 1 frequency per lane, R rows (kFarVariants)
     bool two = false;   // two-row tiles of the sinc ring form (L = 2)
     int sky_rows = 1;   // sky points per block of the one-row ring (meta and bases SFT-major when > 1)
+    bool sky_perm = false;   // blocks group the sky points in the context's neighbour order
     size_t smem = 0;
     long long grid = 0;
 };
@@ -157,6 +158,11 @@ struct fstat_ctx {
     std::vector<double> h_sky, h_fdot;
     bool fdot_uniform = true;         // spindowns fdot_0 + d * dfdot (compact bases)
     bool batch_member = false;        // a workunit of a batch (kernels with a persistent form only)
+    std::vector<int> h_order;         // sky points in neighbour order (empty: not computed yet)
+    double order_spread4 = -1.0;      // window spread bound of 4 consecutive points of h_order (bins)
+    int* d_perm = nullptr;            // [n_sky] h_order on the device
+    int* d_rank = nullptr;            // [n_sky] each sky point's place in h_order
+    bool perm_on_device = false;
     double dfdot = 0.0;
     // derived per-bank buffers
     size_t cap_meta = 0, cap_kh0 = 0, cap_ph0 = 0, cap_abcd = 0, cap_comb = 0, cap_twoF = 0;
@@ -278,13 +284,14 @@ int pairs_needed(const fstat_ctx* c, int span_templates, int D) {
 // 1.1e-4 (orbit and rotation), so two sky points' khat differ by at most
 // f_max T 1.1e-4 |n_1 - n_2| (the Roemer delay's share, fdot T dtau, is below
 // 1e-3 bins); the maximum over all groups of g, plus one bin.
-double sky_spread_bins(const fstat_ctx* c, int g) {
+double sky_spread_bins(const fstat_ctx* c, int g, const std::vector<int>* order = nullptr) {
     const double k_max = (c->f0 + (c->n_f - 1) * c->df) * c->T;
     double chord = 0.0;
     for (int s0 = 0; s0 < c->n_sky; s0 += g) {
         const int s1 = std::min(c->n_sky, s0 + g);
-        for (int a = s0; a < s1; ++a)
-            for (int b = a + 1; b < s1; ++b) {
+        for (int ia = s0; ia < s1; ++ia)
+            for (int ib = ia + 1; ib < s1; ++ib) {
+                const int a = order ? (*order)[ia] : ia, b = order ? (*order)[ib] : ib;
                 const double aa = c->h_sky[2 * a], da = c->h_sky[2 * a + 1];
                 const double ab = c->h_sky[2 * b], db = c->h_sky[2 * b + 1];
                 const double dx = std::cos(da) * std::cos(aa) - std::cos(db) * std::cos(ab);
@@ -294,6 +301,27 @@ double sky_spread_bins(const fstat_ctx* c, int g) {
             }
     }
     return k_max * 1.1e-4 * chord + 1.0;
+}
+
+// An order of the sky points in which consecutive ones are neighbours: bands
+// of equal width in delta (0.6 sqrt(n) of them: on a near-uniform sky this
+// gave the smallest largest chord within groups of 4, e.g. 0.21 for 3000
+// points and 0.09 for 16 435), alpha ascending in even bands and descending
+// in odd ones.
+std::vector<int> sky_neighbour_order(const fstat_ctx* c) {
+    const int n = c->n_sky;
+    const int nb = std::max(1, (int)std::lround(0.6 * std::sqrt((double)n)));
+    std::vector<std::pair<double, int>> key(n);
+    for (int i = 0; i < n; ++i) {
+        double a = std::fmod(c->h_sky[2 * i], 2.0 * kPi);
+        if (a < 0) a += 2.0 * kPi;
+        const int band = std::min(nb - 1, std::max(0, (int)std::floor((c->h_sky[2 * i + 1] + 0.5 * kPi) / kPi * nb)));
+        key[i] = {band * 10.0 + ((band & 1) ? 2.0 * kPi - a : a), i};
+    }
+    std::sort(key.begin(), key.end());
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = key[i].second;
+    return order;
 }
 
 // Weights of the far-field form: for each far offset k, the monomial
@@ -580,12 +608,26 @@ bool make_far_plan(fstat_ctx* c, int P, int L, bool found, Plan& best) {
         // on GB300 the 10-warp block was faster on every bank measured, by 20-60 %
         // on banks of 1-16 spindowns where the cost model favoured the small ones
         const std::vector<int> nwcs = {nwc0};
-        // blocks of 4 consecutive sky points where their windows lie within 24 bins
-        // (the window widens by that much; the cost model weighs it)
+        // blocks of 4 sky points whose windows lie within 24 bins (the window widens
+        // by that much; the cost model weighs it): 4 consecutive ones of the bank,
+        // else 4 consecutive ones of a neighbour order (meta and bases are then
+        // written in that order); batched workunits only where a persistent form
+        // exists (L = 2)
         std::vector<int> SRs = {1};
         double spread4 = 0.0;
-        if (few_rows && !c->have_cov && !c->batch_member && c->n_sky >= 8) {
+        bool use_perm = false;
+        if (few_rows && !c->have_cov && (!c->batch_member || L == 2) && c->n_sky >= 8) {
             spread4 = sky_spread_bins(c, 4);
+            if (spread4 > 24.0) {
+                if (c->h_order.empty()) {
+                    c->h_order = sky_neighbour_order(c);
+                    c->order_spread4 = sky_spread_bins(c, 4, &c->h_order);
+                }
+                if (c->order_spread4 <= 24.0) {
+                    spread4 = c->order_spread4;
+                    use_perm = true;
+                }
+            }
             if (spread4 <= 24.0) SRs.push_back(4);
         }
         // one spindown and one sky point a block: the far-field form (measured; the
@@ -681,6 +723,7 @@ bool make_far_plan(fstat_ctx* c, int P, int L, bool found, Plan& best) {
                         best.ring = true;
                         best.sinc = sinc;
                         best.sky_rows = SR;
+                        best.sky_perm = SR > 1 && use_perm;
                         best.smem = smem;
                         best.grid = (long long)((c->n_sky + SR - 1) / SR) * n_col * chunks_max;
                         have_ring = true;
@@ -1066,7 +1109,7 @@ void fstat_destroy(fstat_ctx* c) {
                     c->tw.hist, c->tw.state, c->tw.tie_count, c->tw.cand_idx, c->tw.cand_val, c->tw.n_cand,
                     c->tw.out_idx, c->tw.out_val, c->d_inj_work, c->d_sig, c->d_ptab, c->d_pcoef,
                     c->d_bins_w, c->d_floor, c->d_sbar, c->d_weight, c->d_cov, c->d_comb_j, c->d_slide_seg, c->d_slide_A,
-                    c->d_slide_B, c->d_slide_out};
+                    c->d_slide_B, c->d_slide_out, c->d_perm, c->d_rank};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (int i = 0; i < kTimedRing; ++i) {
@@ -1296,6 +1339,9 @@ int fstat_set_templates(fstat_ctx* c, const double* sky, int32_t n_sky, double f
     if (set_device(c) != FSTAT_OK) return FSTAT_ECUDA;
     c->h_sky.assign(sky, sky + 2 * (size_t)n_sky);
     c->h_fdot.assign(fdot, fdot + n_fdot);
+    c->h_order.clear();
+    c->order_spread4 = -1.0;
+    c->perm_on_device = false;
     if (c->d_sky) cudaFree(c->d_sky);
     if (c->d_fdot) cudaFree(c->d_fdot);
     c->d_sky = nullptr;
@@ -1360,6 +1406,19 @@ int prepare(fstat_ctx* c, cudaStream_t s) {
 // follow the plan (form, window width), so a new plan may need a rebuild.
 int ensure_tables(fstat_ctx* c, cudaStream_t s) {
     int rc;
+    if (c->plan.sky_perm && !c->perm_on_device) {   // the neighbour order and its inverse
+        const int n = c->n_sky;
+        std::vector<int> rank(n);
+        for (int i = 0; i < n; ++i) rank[c->h_order[i]] = i;
+        if (c->d_perm) cudaFree(c->d_perm);
+        if (c->d_rank) cudaFree(c->d_rank);
+        c->d_perm = c->d_rank = nullptr;
+        CUDA_TRY(c, cudaMalloc(&c->d_perm, (size_t)n * sizeof(int)));
+        CUDA_TRY(c, cudaMalloc(&c->d_rank, (size_t)n * sizeof(int)));
+        CUDA_TRY(c, cudaMemcpy(c->d_perm, c->h_order.data(), (size_t)n * sizeof(int), cudaMemcpyHostToDevice));
+        CUDA_TRY(c, cudaMemcpy(c->d_rank, rank.data(), (size_t)n * sizeof(int), cudaMemcpyHostToDevice));
+        c->perm_on_device = true;
+    }
     if (c->plan.far) far_extent(c, c->plan.w_pairs, &c->far_xoff, &c->n_pos);
     if (c->plan.far &&
         (c->tab_dirty || c->tab_npos != c->n_pos || c->tab_xoff != c->far_xoff || c->tab_sinc != c->plan.sinc ||
@@ -1408,6 +1467,7 @@ TimingParams timing_params(const fstat_ctx* c, int n_sky) {
     tp.meta = c->d_meta;
     tp.base = c->fdot_uniform ? c->d_base : nullptr;
     tp.sft_major = c->plan.sky_rows > 1 ? 1 : 0;   // blocks of several sky points read them SFT-major
+    tp.sky_rank = c->plan.sky_perm ? c->d_rank : nullptr;
     tp.row_rot = (c->plan.rows || c->plan.two) ? 1 : 0;   // the row-tiled forms step the twiddle across rows
     tp.kh0 = c->fdot_uniform ? nullptr : c->d_kh0;
     tp.ph0 = c->fdot_uniform ? nullptr : c->d_ph0;
@@ -1430,6 +1490,7 @@ DirichletParams dirichlet_params(const fstat_ctx* c) {
     dp.kh0 = c->fdot_uniform ? nullptr : c->d_kh0;
     dp.ph0 = c->fdot_uniform ? nullptr : c->d_ph0;
     dp.comb = c->d_comb;
+    dp.sky_perm = pl.sky_perm ? c->d_perm : nullptr;
     dp.twoF = c->d_twoF;
     dp.n_sky = c->n_sky;
     dp.n_fdot = c->n_fdot;
@@ -1774,6 +1835,7 @@ int fstat_autotune(fstat_ctx* c, void* cuda_stream, int32_t* out) {
             if (make_plan(c, c->plan) != FSTAT_OK) continue;
             c->plan_valid = true;
             if (c->plan.C != C) continue;   // round size capped by shared memory
+            if (c->plan.sky_perm) continue;   // the slice takes the first sky points, not an order's groups
             if (ensure_tables(c, s) != FSTAT_OK) continue;   // tables for this plan's form and width
             // a slice of the bank: the first sky points, about four waves of blocks
             const long long per_sky = (long long)c->plan.n_col * c->plan.chunks_per_col;

@@ -693,7 +693,8 @@ __device__ __forceinline__ void far_ring_block(const DirichletParams& p, long lo
     const int g = uu - row * Gc;
     const int sky_l = SR == 1 ? 0 : row / p.n_fdot;   // sky point of the block
     const int drow = SR == 1 ? row : row - sky_l * p.n_fdot;
-    const int sky = sky0 + sky_l;
+    // SR > 1: the block's places in the grouping order, the sky point at each
+    const int sky = SR == 1 || !p.sky_perm ? sky0 + sky_l : p.sky_perm[sky0 + sky_l];
     const int j_t = j_col0 + g * PM + r;
     const bool warp_live = __any_sync(0xffffffffu, active);
 
@@ -1192,7 +1193,7 @@ __global__ void __launch_bounds__(32 * (NWC + 1), MINB) dirichlet_ring2_kernel(c
 // all banks are done, runs it as far_ring_block (whose barriers it sets up and
 // invalidates), and the block that completes a bank's last item stamps its
 // completion time.  At most `total` items per block; no block waits on another.
-template <int M, int NWC, bool SINC>
+template <int M, int NWC, bool SINC, int SR = 1>
 __global__ void __launch_bounds__(32 * (NWC + 1), 2)
     dirichlet_far_ring_batch_kernel(const DirichletParams* __restrict__ banks,
                                     const long long* __restrict__ item_prefix, int n_wu,
@@ -1219,7 +1220,7 @@ __global__ void __launch_bounds__(32 * (NWC + 1), 2)
         if (it >= total) break;
         const int w = s_wu;
         const DirichletParams p = banks[w];
-        far_ring_block<M, SINC, false, 2>(p, it - item_prefix[w], smem);
+        far_ring_block<M, SINC, false, 2, SR>(p, it - item_prefix[w], smem);
         __syncthreads();
         if (threadIdx.x == 0) {
             __threadfence();
@@ -1255,12 +1256,18 @@ __global__ void __launch_bounds__(32 * (NWC + 1), 2)
 #define FS_RING_COV_VARIANTS(X) \
     X(16, 5, 10, true)          \
     X(17, 5, 10, false)
-// blocks of 4 sky points (single launches only): (ID, M, NWC, sinc, L)
+// blocks of 4 sky points: (ID, M, NWC, sinc, L)
 #define FS_RING_SKY_VARIANTS(X) \
     X(31, 5, 10, true, 2)       \
     X(32, 5, 10, false, 2)      \
     X(33, 5, 8, true, 1)        \
     X(34, 1, 8, true, 1)
+// the L = 2 ones also in the persistent batch kernel: (ID, M, NWC, sinc)
+#define FS_RING_SKY2_VARIANTS(X) \
+    X(31, 5, 10, true)           \
+    X(32, 5, 10, false)
+#define FS_BRCASE_SKY(ID, M_, W_, S_) FS_BRCASE(ID, M_, W_, S_, 4)
+#define FS_BOCASE_SKY(ID, M_, W_, S_) FS_BOCASE(ID, M_, W_, S_, 4)
 // sinc form for L = 1 banks (P = 8 threads per lane-group; single launches only)
 #define FS_RING_L1_VARIANTS(X) \
     X(18, 5, 8, true)          \
@@ -1341,15 +1348,16 @@ cudaError_t launch_dirichlet_far(int v, const DirichletParams& p, int threads, s
 cudaError_t launch_dirichlet_far_batch(int v, const DirichletBatch& b, int threads, size_t smem, int grid,
                                        cudaStream_t s) {
     switch (v) {
-#define FS_BRCASE(ID, M_, W_, S_)                                                                         \
+#define FS_BRCASE(ID, M_, W_, S_, ...)                                                                    \
     case ID: {                                                                                            \
-        auto fn = dirichlet_far_ring_batch_kernel<M_, W_, S_>;                                            \
+        auto fn = dirichlet_far_ring_batch_kernel<M_, W_, S_, ##__VA_ARGS__>;                             \
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
         if (e != cudaSuccess) return e;                                                                   \
         fn<<<grid, threads, smem, s>>>(b.banks, b.item_prefix, b.n_wu, b.queue, b.remaining, b.done_ns);  \
         return cudaGetLastError();                                                                        \
     }
         FS_RING_VARIANTS(FS_BRCASE)
+        FS_RING_SKY2_VARIANTS(FS_BRCASE_SKY)
 #undef FS_BRCASE
         default:
             return cudaErrorInvalidValue;
@@ -1358,14 +1366,15 @@ cudaError_t launch_dirichlet_far_batch(int v, const DirichletBatch& b, int threa
 
 cudaError_t dirichlet_far_batch_occupancy(int v, int threads, size_t smem, int* blocks_per_sm) {
     switch (v) {
-#define FS_BOCASE(ID, M_, W_, S_)                                                                         \
+#define FS_BOCASE(ID, M_, W_, S_, ...)                                                                    \
     case ID: {                                                                                            \
-        auto fn = dirichlet_far_ring_batch_kernel<M_, W_, S_>;                                            \
+        auto fn = dirichlet_far_ring_batch_kernel<M_, W_, S_, ##__VA_ARGS__>;                             \
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
         if (e != cudaSuccess) return e;                                                                   \
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, threads, smem);           \
     }
         FS_RING_VARIANTS(FS_BOCASE)
+        FS_RING_SKY2_VARIANTS(FS_BOCASE_SKY)
 #undef FS_BOCASE
         default:
             return cudaErrorInvalidValue;

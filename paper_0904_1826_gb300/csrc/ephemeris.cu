@@ -194,7 +194,8 @@ __global__ void __launch_bounds__(kTimingBlock) timing_kernel(const TimingParams
             if (p.row_rot) sincospif((float)(int)bs.dph * 4.656612873077393e-10f, &rs, &rc);
             bs.rot_re = rc;
             bs.rot_im = -rs;
-            p.base[p.sft_major ? (size_t)i * p.n_sky + sky : (size_t)sky * p.n_sft + i] = bs;
+            p.base[p.sft_major ? (size_t)i * p.n_sky + (p.sky_rank ? p.sky_rank[sky] : sky)
+                               : (size_t)sky * p.n_sft + i] = bs;
             const long long last = bs.kh0 + (long long)(p.n_fdot - 1) * bs.dkh;
             khmin = bs.kh0 < last ? bs.kh0 : last;
         } else {
@@ -210,7 +211,8 @@ __global__ void __launch_bounds__(kTimingBlock) timing_kernel(const TimingParams
             }
         }
         m.khmin = khmin;
-        p.meta[p.sft_major ? (size_t)i * p.n_sky + sky : (size_t)sky * p.n_sft + i] = m;
+        p.meta[p.sft_major ? (size_t)i * p.n_sky + (p.sky_rank ? p.sky_rank[sky] : sky)
+                           : (size_t)sky * p.n_sft + i] = m;
     }
     const double A = block_sum<kTimingBlock>(sAA, red[0]);
     const double B = block_sum<kTimingBlock>(sBB, red[1]);

@@ -95,6 +95,8 @@ struct DirichletParams {
     int ring_stop;             // testing aid: the ring's copy warp stops after this many SFTs (< 0: never)
     const int2* cov;           // [n_sft] frequency-index range [x, y) each SFT contributes to, or null (all)
     const float4* comb_j;      // [n_sky][n_f] per-frequency combine weights with coverage, or null
+    const int* sky_perm;       // blocks of several sky points: the sky point at each place of the
+                               // grouping order (meta and bases SFT-major in that order), or null
 };
 
 // Far-field polynomial form (D = 8): the window's 12 bins at offsets -7..-2
@@ -217,6 +219,7 @@ struct TimingParams {
     SkySftMeta* meta;          // out [n_sky][n_sft], or [n_sft][n_sky] when sft_major
     SkySftBase* base;          // out [n_sky][n_sft] (uniform), or [n_sft][n_sky] when sft_major
     int sft_major;             // SFT-major meta and bases (blocks of several sky points)
+    const int* sky_rank;       // with sft_major: each sky point's place in the grouping order, or null
     int row_rot;               // write the bases' row twiddle step (row-tiled forms)
     long long* kh0;            // out [n_sky][n_fdot][n_sft] (not uniform)
     unsigned int* ph0;         // out [n_sky][n_fdot][n_sft] (not uniform)

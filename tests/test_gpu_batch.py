@@ -137,3 +137,29 @@ def test_batch_autotune_gives_m_and_keeps_each_plans_stages(lib):
             np.testing.assert_array_equal(got, ref)
     finally:
         g.close()
+
+
+def test_batch_with_blocks_of_sky_points(lib):
+    """Workunits of one and two spindowns on Fibonacci skies run the ring with
+    blocks of 4 neighbouring sky points in the persistent kernel: bit-exact
+    against their single launches."""
+    specs = config3_specs(2, seed=3400)
+    wus = []
+    for sp, nfd in zip(specs, (1, 2)):
+        sp = dict(sp, n_fdot=nfd)
+        wus.append(config3_workunit(sp, n_sky=3000, n_sft_total=160, band=0.1))
+    g = lib.FStat(0, topk=10)
+    try:
+        for w in wus:
+            lib.fstat_batch_add(g.ctx, w)
+        ref = []
+        for i, w in enumerate(wus):
+            lib.fstat_batch_compute_one(g.ctx, i)
+            assert lib.fstat_batch_get_plan(g.ctx, i)["variant"] in (131, 132)
+            ref.append(lib.fstat_batch_get_2f(g.ctx, i, 0, w.n_templates))
+        for rep in range(2):
+            lib.fstat_batch_compute(g.ctx)
+            for i, w in enumerate(wus):
+                np.testing.assert_array_equal(lib.fstat_batch_get_2f(g.ctx, i, 0, w.n_templates), ref[i])
+    finally:
+        g.close()

@@ -469,3 +469,24 @@ def test_blocks_of_four_sky_points(lib, n_fdot, df_bins, ids, tile_m, algo):
         one = _gpu(lib, w, bins, tile_warps=9, algo=algo)
         assert one["plan"]["variant"] in (114, 107), one["plan"]
         np.testing.assert_array_equal(out["twoF"], one["twoF"])
+
+
+@pytest.mark.parametrize("n_fdot", [1, 2])
+def test_blocks_of_four_sky_points_in_neighbour_order(lib, n_fdot):
+    """A sky list whose consecutive points are far apart (Fibonacci lattice):
+    the blocks group 4 neighbours of a neighbour order instead (meta and bases
+    written in that order); parity, and 2F bit-identical to blocks of one sky
+    point of the same form."""
+    from workload import fibonacci_sky
+    w = config_mid(n_f=210, n_fdot=n_fdot, n_sky=3, n_bins=300)
+    w = dataclasses.replace(w, bank=dataclasses.replace(w.bank, sky=fibonacci_sky(150)))
+    bins = _oracle_bins(w)
+    ref = O.compute_fstat_freq_band(_dets(w, bins), w.T, w.k_lo, w.dterms, w.bank).ravel()
+    out = _gpu(lib, w, bins)
+    assert out["plan"]["variant"] in (131, 132), out["plan"]
+    assert out["flags"] == 0
+    _assert_parity(out["twoF"], ref, f"neighbour-order sky blocks n_fdot={n_fdot}")
+    _check_toplist(out["top"], out["twoF"], ref, w.topk)
+    algo = "sincpoly" if out["plan"]["variant"] == 131 else "farpoly"
+    one = _gpu(lib, w, bins, tile_warps=9, algo=algo)
+    np.testing.assert_array_equal(out["twoF"], one["twoF"])
