@@ -115,9 +115,10 @@ typedef struct {
  * AUTO: the TMA ring where it applies: SINCPOLY, or on banks of one or two
  *   spindowns with L = 2 (where the ring can be bound by its table copies)
  *   whichever of SINCPOLY and FARPOLY's smaller records the planner's model
- *   finds faster; banks of one or two spindowns whose consecutive sky points
- *   are neighbours run blocks of 4 sky points sharing one staged window;
- *   else FARPOLY where it applies, else DIRECT. */
+ *   finds faster; banks of one or two spindowns run blocks of 4 neighbouring
+ *   sky points (consecutive ones of the bank, or of a neighbour order of its
+ *   sky list) sharing one staged window; else FARPOLY where it applies, else
+ *   DIRECT.  Results do not depend on the grouping. */
 typedef enum {
     FSTAT_ALGO_AUTO = 0,
     FSTAT_ALGO_DIRECT = 1,
