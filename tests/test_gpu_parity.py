@@ -490,3 +490,27 @@ def test_blocks_of_four_sky_points_in_neighbour_order(lib, n_fdot):
     algo = "sincpoly" if out["plan"]["variant"] == 131 else "farpoly"
     one = _gpu(lib, w, bins, tile_warps=9, algo=algo)
     np.testing.assert_array_equal(out["twoF"], one["twoF"])
+
+
+@pytest.mark.parametrize("form", ["f16", "bf16"])
+def test_sky_blocks_with_16_bit_storage_and_noise_weights(lib, form):
+    """Blocks of 4 sky points (neighbour order) with 16-bit SFT storage and
+    noise weights (a and b scaled per SFT before the SFT-major write): 2F
+    bit-identical to blocks of one sky point of the same form."""
+    from workload import fibonacci_sky
+    w = config_mid(n_f=210, n_fdot=1, n_sky=3, n_bins=300)
+    w = dataclasses.replace(w, bank=dataclasses.replace(w.bank, sky=fibonacci_sky(150)))
+    bins = _oracle_bins(w)
+    outs = []
+    for tw in (0, 9):
+        g = lib.FStat(0, dterms=w.dterms, topk=10, bins_form=form, tile_warps=tw, algo="sincpoly")
+        try:
+            g.load_workload(w, bins_override=bins)
+            lib.fstat_set_noise_floor(g.ctx, 9)
+            g.compute()
+            outs.append((g.twoF(), g.plan()["variant"], g.error_flags()))
+        finally:
+            g.close()
+    assert outs[0][1] == 131 and outs[1][1] == 114, (outs[0][1], outs[1][1])
+    assert outs[0][2] == 0 and outs[1][2] == 0
+    np.testing.assert_array_equal(outs[0][0], outs[1][0])
